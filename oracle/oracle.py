@@ -1,0 +1,350 @@
+"""ORACLE -- test infrastructure only.
+
+Plain, slow CPU restatement of the QQMC estimator for the charge coefficients
+Q_n of the Anderson single-level dot (wide-band leads, T = 0, zero bias).
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It shares no code with the CUDA path
+and imports nothing from the product package; inputs (shift words, synthetic
+tables) are passed in by the caller.
+
+Pieces and the passages they follow:
+
+* ``gf_exact`` / ``gf_tables`` -- the non-interacting lesser/greater Green
+  functions of the dot in the time domain, App. E Eq. (lesser_greater_freq)
+  specialised to V = 0, T = 0 and the flat band Delta = -i Gamma (App. E,
+  "universal regime"), Fourier transformed.  The convention is the textbook
+  one, g^<(0) = i<n>, with the Lorentzian spectral function
+  A(w) = 2 Gamma / ((w - eps_d)^2 + Gamma^2):
+
+      g^<(tau) =  i Int dw/2pi e^{-i w tau} A(w) theta(-w)
+      g^>(tau) = -i Int dw/2pi e^{-i w tau} A(w) theta(+w)
+
+  Each half-line Fourier integral is written in closed form with the
+  exponential integral E1 (partial fractions of the Lorentzian, then the
+  Laplace-transform identity Int_0^inf e^{-p s}/(s+b) ds = e^{pb} E1(pb)),
+  continued onto the sheet the integration path selects.  The App. E
+  contour-deformation quadrature is a different route to the same numbers;
+  this closed form is pinned against 30-digit quadrature in the tests.
+* ``sobol_direction_numbers`` -- direction words of the unscrambled Sobol'
+  sequence (main text below Eq. (warped_int2)), read off scipy's generator.
+* ``sobol_points`` / ``warp`` / ``estimate`` -- C routines in qqmc_oracle.c
+  (Gray-code Sobol' with a digital shift, App. H; product-model warp,
+  Eq. (warper1d) with App. F Eq. (hi_expo); estimator Eq. (warped_int2)).
+* ``integrand`` -- App. E Eq. (integral_gf): naive sum over all 2^n Keldysh
+  index vectors of det M_up * det M_down, each by pivoted LU.
+* ``q_from_sums`` / ``shift_statistics`` -- readout Q_n = -2i c_n and the
+  randomised-QMC error bar (App. G, App. H: standard deviation over the K
+  shifted sequences divided by sqrt(K)).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qqmc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        i64 = ctypes.c_int64
+        L.oracle_integrand.argtypes = [ctypes.c_int, i64, dp, ctypes.c_double, dp, dp, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.oracle_sobol.argtypes = [ctypes.c_int, i64, i64, u32p, u32p]
+        L.oracle_estimate.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
+                                      ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64)]
+        L.oracle_warp.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
+                                  ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int32)]
+        L.oracle_det.argtypes = [ctypes.c_int, dp, dp]
+        L.oracle_table_at.argtypes = [dp, ctypes.c_int, ctypes.c_double, i64, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+# --------------------------------------------------------------------------
+# Green functions (App. E)
+# --------------------------------------------------------------------------
+
+def _half_line_ft(eps: float, gamma: float, tau: np.ndarray) -> np.ndarray:
+    """I(tau) = Int_0^inf e^{i s tau} 2Gamma/((s+eps)^2+Gamma^2) ds for tau > 0.
+
+    With beta = eps + i Gamma the Lorentzian is -i [1/(s+beta*) - 1/(s+beta)],
+    and F(b) = Int_0^inf e^{i s tau}/(s+b) ds = e^{w} E1(w) with w = -i b tau.
+    For b = beta the argument has Re w = Gamma tau > 0 (principal E1).  For
+    b = beta* it is w = -Gamma tau - i eps tau, reached from the lower half
+    plane (eps > 0); for eps <= 0 the path crosses the negative real axis
+    and E1 is continued past its cut: E1 + 2 pi i above the axis, the lower
+    boundary value on it.
+    """
+    from scipy.special import exp1
+
+    tau = np.asarray(tau, dtype=np.float64)
+    beta = complex(eps, gamma)
+    w_plus = -1j * beta * tau
+    w_minus = -1j * np.conj(beta) * tau
+    F_plus = np.exp(w_plus) * exp1(w_plus)
+    if eps > 0:
+        E = exp1(w_minus)
+    else:
+        on_axis = np.imag(w_minus) == 0.0
+        wm = np.where(on_axis, np.real(w_minus) + 0j, w_minus)
+        E = exp1(wm) + 2j * np.pi
+        # on the axis itself take the boundary value from below
+        below = np.conj(exp1(np.real(w_minus) + 0j))
+        E = np.where(on_axis, below, E)
+    F_minus = np.exp(w_minus) * E
+    return -1j * (F_minus - F_plus)
+
+
+def gf_exact(tau, gamma: float, eps_d: float):
+    """Exact g^<(tau), g^>(tau) of the wide-band dot at T = 0, V = 0.
+
+    tau = 0 gives g^<(0) = i(1/2 - arctan(eps_d/Gamma)/pi) and
+    g^>(0) = g^<(0) - i.  Negative tau uses g(-tau) = -conj g(tau).
+    """
+    tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
+    a = np.abs(tau)
+    pos = a > 0
+    gl = np.empty(tau.shape, dtype=np.complex128)
+    gg = np.empty(tau.shape, dtype=np.complex128)
+    gl0 = 1j * (0.5 - math.atan(eps_d / gamma) / math.pi)
+    gl[~pos] = gl0
+    gg[~pos] = gl0 - 1j
+    if np.any(pos):
+        ap = a[pos]
+        # g^<(tau) = (i/2pi) Int_0^inf e^{i s tau} A(-s) ds      (w = -s)
+        gl_p = 1j / (2 * math.pi) * _half_line_ft(eps_d, gamma, ap)
+        # g^>(tau) = (-i/2pi) Int_0^inf e^{-i w tau} A(w) dw = (-i/2pi) conj(I_{-eps})
+        gg_p = -1j / (2 * math.pi) * np.conj(_half_line_ft(-eps_d, gamma, ap))
+        neg = tau[pos] < 0
+        gl_p = np.where(neg, -np.conj(gl_p), gl_p)
+        gg_p = np.where(neg, -np.conj(gg_p), gg_p)
+        gl[pos] = gl_p
+        gg[pos] = gg_p
+    return gl, gg
+
+
+def table_nodes(T: float, L: int) -> np.ndarray:
+    """Uniform nodes tau_k = -T + k * 2T/(L-1), k = 0..L-1 (both ends included)."""
+    h = 2.0 * T / (L - 1)
+    return -T + np.arange(L, dtype=np.float64) * h
+
+
+def gf_tables(gamma: float, eps_d: float, T: float, L: int = 4096):
+    """(g^< table, g^> table, g^<(0)) on ``table_nodes(T, L)``."""
+    gl, gg = gf_exact(table_nodes(T, L), gamma, eps_d)
+    gl0 = 1j * (0.5 - math.atan(eps_d / gamma) / math.pi)
+    return gl, gg, gl0
+
+
+# --------------------------------------------------------------------------
+# Sobol' direction numbers (library primitive: scipy's unscrambled generator)
+# --------------------------------------------------------------------------
+
+_V_CACHE: dict = {}
+
+
+def sobol_direction_numbers(n_dims: int, n_bits: int = 26) -> np.ndarray:
+    """uint32 [n_dims, 32]: V[d, j] = X_{2^j, d}, the natural-order point 2^j.
+
+    scipy emits points in Gray-code order, where consecutive outputs differ
+    by one direction word: output p XOR output p+1 = V[ctz(p+1)].  So
+    V[:, j] = out[2^j - 1] XOR out[2^j].  Words j >= n_bits are left zero
+    (the callers never index points at or beyond 2^n_bits).
+    """
+    key = (n_dims, n_bits)
+    if key in _V_CACHE:
+        return _V_CACHE[key]
+    from scipy.stats import qmc
+
+    V = np.zeros((n_dims, 32), dtype=np.uint32)
+    eng = qmc.Sobol(n_dims, scramble=False, bits=32)
+    pos = 0
+    for j in range(n_bits):
+        target = (1 << j) - 1
+        if target < pos:
+            eng = qmc.Sobol(n_dims, scramble=False, bits=32)
+            pos = 0
+        if target > pos:
+            eng.fast_forward(target - pos)
+        pts = np.rint(eng.random(2) * 2.0 ** 32).astype(np.uint64)
+        pos = target + 2
+        V[:, j] = (pts[0] ^ pts[1]).astype(np.uint32)
+    _V_CACHE[key] = V
+    return V
+
+
+def sobol_points(n: int, i0: int, count: int, V: np.ndarray) -> np.ndarray:
+    """Unshifted Sobol' integers, Gray-code order: uint32 [count, n]."""
+    Vc = np.ascontiguousarray(V[:n], dtype=np.uint32)
+    out = np.zeros((count, n), dtype=np.uint32)
+    lib().oracle_sobol(n, i0, count, _u32p(Vc), _u32p(out))
+    return out
+
+
+def warp(n: int, i0: int, count: int, V: np.ndarray, shift: np.ndarray, t: float, tau: float):
+    """Warped points: (u [count, n], weight C/p_n [count], in-domain flag [count])."""
+    Vc = np.ascontiguousarray(V[:n], dtype=np.uint32)
+    S = np.ascontiguousarray(shift[:n], dtype=np.uint32)
+    u = np.zeros((count, n))
+    w = np.zeros(count)
+    ins = np.zeros(count, dtype=np.int32)
+    lib().oracle_warp(n, i0, count, _u32p(Vc), _u32p(S), t, tau, _dp(u), _dp(w),
+                      ins.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return u, w, ins.astype(bool)
+
+
+# --------------------------------------------------------------------------
+# Integrand and estimator
+# --------------------------------------------------------------------------
+
+def _tab(a: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
+
+
+def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: bool = False):
+    """c(u) of App. E Eq. (integral_gf) at each row of u ([count, n], any time order)."""
+    gl, gg, gl0 = tables
+    u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)).reshape(-1, n))
+    count = u.shape[0]
+    gl_t, gg_t = _tab(gl), _tab(gg)
+    L = gl_t.size // 2
+    out = np.zeros(2 * count)
+    ab = np.zeros(count)
+    rc = lib().oracle_integrand(n, count, _dp(u), t, _dp(gl_t), _dp(gg_t), L, T,
+                                float(np.real(gl0)), float(np.imag(gl0)), _dp(out), _dp(ab))
+    if rc != 0:
+        raise ValueError("oracle_integrand rejected its arguments")
+    val = out[0::2] + 1j * out[1::2]
+    return (val, ab) if return_abs else val
+
+
+def det(A: np.ndarray) -> complex:
+    """Determinant by the oracle's pivoted LU (for the pins)."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
+    out = np.zeros(2)
+    if lib().oracle_det(A.shape[0], _dp(A.view(np.float64)), _dp(out)) != 0:
+        raise ValueError("matrix too large for the oracle")
+    return complex(out[0], out[1])
+
+
+def table_at(table: np.ndarray, T: float, tau: np.ndarray) -> np.ndarray:
+    """Linear interpolation of a table on ``table_nodes(T, L)`` at tau."""
+    tab = _tab(table)
+    tau = np.ascontiguousarray(np.atleast_1d(np.asarray(tau, dtype=np.float64)))
+    out = np.zeros(2 * tau.size)
+    lib().oracle_table_at(_dp(tab), tab.size // 2, T, tau.size, _dp(tau), _dp(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def _estimate_chunk(args):
+    n, i0, i1, Vc, S, t, tau, gl_t, gg_t, L, T, gl0 = args
+    res = np.zeros(4)
+    n_in = ctypes.c_int64(0)
+    rc = lib().oracle_estimate(n, i0, i1, _u32p(Vc), _u32p(S), t, tau, _dp(gl_t), _dp(gg_t), L, T,
+                               float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in))
+    if rc != 0:
+        raise ValueError("oracle_estimate rejected its arguments")
+    return res, n_in.value
+
+
+def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T: float,
+             V: np.ndarray | None = None, threads: int | None = None, i0: int = 0,
+             chunk: int = 4096):
+    """Per-shift estimates S_k = (1/N) sum_{i=i0}^{i0+N-1} w_i c(u_i), Eq. (warped_int2).
+
+    shifts: uint32 [K, >= n] digital-shift words.  Returns (S [K] complex,
+    n_in [K] int).  Point ranges are split into chunks run on a thread pool
+    (the C call releases the GIL); each chunk is a Neumaier sum and the
+    chunk totals are combined with math.fsum (exact rounding).
+    """
+    if V is None:
+        V = sobol_direction_numbers(max(n, 1))
+    Vc = np.ascontiguousarray(V[:n], dtype=np.uint32)
+    gl, gg, gl0 = tables
+    gl_t, gg_t = _tab(gl), _tab(gg)
+    L = gl_t.size // 2
+    shifts = np.atleast_2d(np.asarray(shifts, dtype=np.uint32))
+    K = shifts.shape[0]
+    jobs = []
+    for k in range(K):
+        S = np.ascontiguousarray(shifts[k, :n])
+        for a in range(i0, i0 + N, chunk):
+            b = min(a + chunk, i0 + N)
+            jobs.append((k, (n, a, b, Vc, S, t, tau, gl_t, gg_t, L, T, gl0)))
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        results = list(ex.map(_estimate_chunk, [j[1] for j in jobs]))
+    re_parts = [[] for _ in range(K)]
+    im_parts = [[] for _ in range(K)]
+    n_in = np.zeros(K, dtype=np.int64)
+    for (k, _), (res, cnt) in zip(jobs, results):
+        re_parts[k].extend([res[0], res[2]])
+        im_parts[k].extend([res[1], res[3]])
+        n_in[k] += cnt
+    S = np.array([complex(math.fsum(re_parts[k]), math.fsum(im_parts[k])) / N for k in range(K)])
+    return S, n_in
+
+
+def q_from_sums(S: np.ndarray) -> np.ndarray:
+    """Q_n^{(k)} = -2i * S_k (readout of the charge from G^<(t,t) = i<n_up>)."""
+    return -2j * np.asarray(S)
+
+
+def shift_statistics(values: np.ndarray):
+    """Mean over shifts and the RQMC error bar std_{ddof=1}/sqrt(K) (App. H)."""
+    v = np.asarray(values, dtype=np.float64)
+    K = v.size
+    return float(np.mean(v)), float(np.std(v, ddof=1) / math.sqrt(K))
+
+
+def splitmix64(x: int) -> int:
+    """One output of the splitmix64 generator for state x (Steele, Lea & Flood 2014)."""
+    M = (1 << 64) - 1
+    z = (x + 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def shift_words(seed: int, K: int, n_dims: int) -> np.ndarray:
+    """Digital-shift words S[k, d] = high 32 bits of splitmix64(seed XOR (k*2^16 + d))."""
+    out = np.zeros((K, n_dims), dtype=np.uint32)
+    for k in range(K):
+        for d in range(n_dims):
+            out[k, d] = splitmix64((seed ^ (k * 65536 + d)) & ((1 << 64) - 1)) >> 32
+    return out
