@@ -192,10 +192,10 @@ def test_integrand_symmetric_in_vertex_labels(oracle):
 
 # ------------------------------------------------------------ warp & estimate ---
 
-@pytest.mark.parametrize("n", [1, 2, 3, 4])
-def test_warp_weight_gives_simplex_volume(oracle, n):
+@pytest.mark.parametrize("n,tau", [(1, 1.0), (2, 0.6), (3, 1.0), (4, 0.95), (3, 1.7)])
+def test_warp_weight_gives_simplex_volume(oracle, n, tau):
     """With f = 1 the warped estimator integrates the ordered simplex: t^n / n!."""
-    t, tau, N, K = 3.0, 1.0, 2 ** 14, 8
+    t, N, K = 3.0, 2 ** 14, 8
     V = oracle.sobol_direction_numbers(n)
     vals = []
     for S in oracle.shift_words(42, K, n):
@@ -222,7 +222,7 @@ def test_order1_against_adaptive_quadrature(oracle):
         if hi > lo:
             exact += quad(f, lo, hi, epsabs=1e-15, epsrel=1e-13, limit=200)[0]
             lo = hi
-    S, _ = oracle.estimate(1, 2 ** 16, oracle.shift_words(9, 8, 1), t, 1.0, tabs, t)
+    S, _ = oracle.estimate(1, 2 ** 16, oracle.shift_words(9, 8, 1), t, 0.95, tabs, t)
     m, e = oracle.shift_statistics(oracle.q_from_sums(S).real)
     assert abs(m - exact) < 5 * e + 1e-9
     assert e < 1e-6
@@ -249,7 +249,7 @@ def test_order2_against_nested_gauss_legendre(oracle):
     pts, wts = np.concatenate(pts), np.concatenate(wts)
     vals = (-2j * oracle.integrand(2, pts, t, tabs, t)).real
     gauss = float(np.sum(wts * vals))
-    S, _ = oracle.estimate(2, 2 ** 16, oracle.shift_words(10, 8, 2), t, 1.0, tabs, t)
+    S, _ = oracle.estimate(2, 2 ** 16, oracle.shift_words(10, 8, 2), t, 1.3, tabs, t)
     m, e = oracle.shift_statistics(oracle.q_from_sums(S).real)
     assert abs(m - gauss) < 5 * e + 2e-8
 
