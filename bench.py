@@ -1,0 +1,344 @@
+"""Benchmark of the QQMC hot path on GB300.
+
+Workload (default): the plain method at scale on the single-level dot --
+Gamma = 1, wide band, T = 0, t_max = 10, tau = 1, L = 4096 table nodes,
+eps_d in {-1, 0, +1}, orders n = 1..10, N = 2^20 Sobol' points x K = 32
+digitally shifted sequences per (eps_d, n), FP64 throughout.
+
+A step is one batch of that workload: all 30 (eps_d, n) integrations over
+one contiguous slice of 2^16 Sobol' indices of every shifted sequence, run
+as ONE persistent-kernel launch (plus its reduction kernel).  Sixteen steps
+cover the whole N = 2^20; step s takes slice s mod 16 (partial sums over
+slices add up exactly to the full integration).  L2 is flushed (a 256 MiB
+write) between timed steps; the Green-function tables (64 KiB) would
+otherwise stay L2-resident.
+
+Metric: integrand evaluations per second (every Sobol' point counts, as in
+the paper's N; the line also gives in-domain and Keldysh-determinant rates).
+`e2e` runs the same batches through the public C ABI from host parameters:
+problem creation (tables built on the device), shift-word upload, launch and
+result download inside the timed region.
+
+--impl reference times the CPU oracle (this project's reference arm) on a
+bounded sample of the same workload.  Multi-GPU runs are independent
+replicas (one full workload per rank, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EPS = (-1.0, 0.0, 1.0)
+ORDERS = tuple(range(1, 11))
+N_TOTAL = 2 ** 20
+SLICE = 2 ** 16
+K_SHIFTS = 32
+T_MAX, TAU, GAMMA, L_TABLE = 10.0, 1.0, 1.0, 4096
+SEED = 2002123720
+METRIC = "integrand_evals_per_s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def _barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def _max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [x for x in sm if mx and x > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_items(Q, problems, s: int, slice_n: int = SLICE):
+    """Items of step s: every (eps_d, n) over Sobol' slice s (shift words from the seed)."""
+    first = (s % (N_TOTAL // slice_n)) * slice_n
+    items = []
+    for pr in problems:
+        for n in ORDERS:
+            items.append((pr, n, K_SHIFTS, slice_n, None, first))
+    return items
+
+
+def run_ours(args, ws, rank, local, pg):
+    import torch
+
+    from paper_2002_12372_gb300 import build as b
+    from paper_2002_12372_gb300 import perf
+    from paper_2002_12372_gb300 import qqmc as Q
+
+    if rank == 0 or ws > 1:
+        b.build()
+    _barrier(pg)
+    torch.cuda.set_device(local)
+    Q.load()
+    prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
+    stream = torch.cuda.Stream()
+    problems = [Q.qqmc_create_problem(Q.make_params(GAMMA, e, T_MAX, TAU, L_TABLE, SEED)) for e in EPS]
+    slice_n = 2 ** args.slice_log2
+    n_plans = min(args.steps + args.warmup, N_TOTAL // slice_n)
+    plans = [Q.Plan(workload_items(Q, problems, s, slice_n), prec) for s in range(n_plans)]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    wpb, flat = Q.qqmc_get_tuning(prec, max(ORDERS))
+
+    def step(s):
+        p = plans[s % n_plans]
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        p.launch(stream.cuda_stream)
+        ev1.record(stream)
+        return p, ev0, ev1
+
+    for s in range(args.warmup):
+        p, _, _ = step(s)
+        p.results()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    _barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step_ms, kern_ms, flops, pts, pts_in, dets, naive = [], [], 0.0, 0, 0, 0.0, 0.0
+    for s in range(args.warmup, args.warmup + args.steps):
+        p, ev0, ev1 = step(s)
+        res = p.results()  # waits for this launch
+        km, _ = p.timing()
+        step_ms.append(ev0.elapsed_time(ev1))
+        kern_ms.append(km)
+        for r, _S in res:
+            pts += r.n_points * r.n_shifts
+            pts_in += r.n_in_domain
+            dets += r.n_in_domain * 2.0 ** r.order
+            flops += r.n_in_domain * perf.flops_per_point(r.order, flat)
+            naive += r.n_in_domain * perf.w_naive(r.order)
+    torch.cuda.synchronize()
+    _barrier(pg)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    dev_s = sum(step_ms) / 1e3
+    dev_s_max = _max_over_ranks(pg, dev_s)
+    k_s = sum(kern_ms) / 1e3
+    value = pts * ws / dev_s_max
+    launches = args.steps * plans[0].kernel_count()
+
+    # e2e through the public API from host parameters
+    e2e_steps = max(1, min(2, args.steps))
+    _barrier(pg)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    e2e_pts, h2d, d2h = 0, 0, 0
+    for s in range(e2e_steps):
+        prs = [Q.qqmc_create_problem(Q.make_params(GAMMA, e, T_MAX, TAU, L_TABLE, SEED)) for e in EPS]
+        pl = Q.Plan(workload_items(Q, prs, s, slice_n), prec)
+        pl.launch(stream.cuda_stream)
+        res = pl.results()
+        pl.close()
+        for pr in prs:
+            Q.qqmc_destroy_problem(pr)
+        for r, _S in res:
+            e2e_pts += r.n_points * r.n_shifts
+        # host -> device: item descriptors (128 B each) and shift words; device -> host:
+        # per-shift complex sums (16 B) and in-domain counts (8 B)
+        h2d += len(res) * 128 + sum(r.n_shifts * r.order * 4 for r, _ in res)
+        d2h += sum(r.n_shifts * (16 + 8) for r, _ in res)
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(pg, time.perf_counter() - te)
+    e2e_value = e2e_pts * ws / e2e_s
+
+    peak = perf.peak_tflops(args.precision)
+    achieved = flops / k_s / 1e12 if k_s > 0 else None
+    out = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_s_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "plain QQMC single-level dot: Gamma=1, eps_d in {-1,0,1}, t_max=10, tau=1, "
+                               "L=4096, orders 1..10, N=2^20 x 32 shifts (16 batches of 2^16 indices)",
+                   "batch": "30 (eps_d, n) integrations x 2^%d indices x 32 shifts per step" % args.slice_log2,
+                   "precision": args.precision, "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "tuning": {"warps_per_block": wpb, "flat_vertices": flat}},
+        "in_domain_evals_per_s": pts_in * ws / dev_s_max,
+        "keldysh_det_evals_per_s": dets * ws / dev_s_max,
+        "naive_equivalent_tflops": naive / dev_s_max / 1e12 * ws,
+        "wall_s": wall,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d // e2e_steps,
+                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "detsum_kernel<%s,%d>" % ("double" if args.precision == "fp64" else "float", flat),
+                     "peak_source": "derived: 152 SMs x %d %s FMA lanes x 2 flops x 2070 MHz" % (
+                         perf.FP64_LANES if args.precision == "fp64" else perf.FP32_LANES, args.precision),
+                     "kernel_ms_per_step": k_s * 1e3 / args.steps},
+        "clocks": clk,
+    }
+    for pl in plans:
+        pl.close()
+    for pr in problems:
+        Q.qqmc_destroy_problem(pr)
+    return out
+
+
+def cpu_oracle_sample(seconds_per_order: float = 1.5, orders=ORDERS, shift_seed: int = SEED):
+    """Time the CPU oracle on a bounded sample of the workload (eps_d = 0, one shift,
+    first M points per order with M chosen so each order runs ~seconds_per_order)."""
+    from oracle import oracle as O
+
+    tabs = O.gf_tables(GAMMA, 0.0, T_MAX, L_TABLE)
+    sw = O.shift_words(shift_seed, 1, max(orders))
+    threads = os.cpu_count() or 1
+    per_point = {}
+    sample = {}
+    for n in orders:
+        M = 64 * threads
+        while True:
+            t0 = time.perf_counter()
+            O.estimate(n, M, sw, T_MAX, TAU, tabs, T_MAX, threads=threads, chunk=max(1, M // (4 * threads)))
+            dt = time.perf_counter() - t0
+            if dt > 0.25 * seconds_per_order or M >= 2 ** 20:
+                break
+            M *= 4
+        per_point[n] = dt / M
+        sample[n] = M
+    # the workload has equal point counts per order: evals/s = n_orders / sum_n t_n
+    value = len(orders) / sum(per_point.values())
+    return value, threads, sample
+
+
+def run_reference(args, ws, rank, pg):
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        cpu_oracle_sample(0.05)
+    vals = []
+    t0 = time.perf_counter()
+    threads, sample = 1, {}
+    for _ in range(args.steps):
+        v, threads, sample = cpu_oracle_sample(0.6)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    desc = "CPU oracle (complex128, naive 2^n pivoted LU), eps_d=0, 1 shift, points per order %s" % (
+        ",".join("n%d:%d" % (n, m) for n, m in sample.items()))
+    return {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "plain QQMC single-level dot: Gamma=1, eps_d in {-1,0,1}, t_max=10, tau=1, "
+                                   "L=4096, orders 1..10, N=2^20 x 32 shifts (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slice-log2", type=int, default=16,
+                    help="Sobol' indices per shift in one step (16: the benchmark batch; smaller for profiling)")
+    args = ap.parse_args()
+    ws, rank, local, pg = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank, pg)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_ours(args, ws, rank, local, pg)
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            v, threads, sample = cpu_oracle_sample(1.5)
+            out["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": threads, "kind": "oracle",
+                                   "sample": "eps_d=0, 1 shift, first points per order " + ",".join(
+                                       "n%d:%d" % (n, m) for n, m in sample.items())}
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * qqmc.h -- C ABI of the GB300 quantum quasi-Monte Carlo (QQMC) library.
+ *
+ * The library evaluates the order-n perturbative coefficient Q_n of the charge
+ * on the Anderson single-level dot (wide-band leads, T = 0, zero bias) by the
+ * QQMC method: digitally shifted Sobol' points are warped through the product
+ * model function p_n(u) = prod_i exp(-(u_{i-1}-u_i)/tau) into ordered vertex
+ * times t = u_0 > u_1 > ... > u_n > 0, the Keldysh integrand (sum over the
+ * 2^n Keldysh index vectors of det M_up * det M_down) is evaluated there, and
+ * the weighted values are reduced per shifted sequence into Q_n and its
+ * shift-to-shift error bar.
+ *
+ * Conventions shared by every call:
+ *  - Green functions: g^<(tau), g^>(tau) of the dot with g^<(0) = i<n>;
+ *    tables hold L nodes tau_k = -t_max + k * 2 t_max / (L-1), k = 0..L-1,
+ *    as interleaved (re, im) doubles, linearly interpolated in re and im.
+ *  - Integrand c_n(u) = i^n sum_a (-1)^{|a|} det M_up(a) det M_down(a),
+ *    paper App. E Eq. (integral_gf) over the ordered simplex (the 1/n! of the
+ *    cube form is absorbed by ordering the vertices).
+ *  - Charge readout Q_n = -2i * (1/N) sum_i w_i c_n(u_i), paper Eq.
+ *    (warped_int2) with w = C/p_n, C = tau^n; points with u_n <= 0 add 0.
+ *  - Error bar: sample standard deviation over the K shifted sequences
+ *    (ddof = 1) divided by sqrt(K), paper App. G and App. H.
+ *  - Sobol' points in Gray-code order, X_i = XOR of the direction words
+ *    selected by the bits of gray(i); shifted by XOR with one 32-bit word per
+ *    dimension; x = X * 2^-32.  Dimension m-1 drives the gap v_m.
+ *  - Shift words, when not given, are the high 32 bits of
+ *    splitmix64(seed XOR (k * 65536 + d)) for shift k and dimension d.
+ *
+ * Memory and errors: every pointer argument is HOST memory unless its
+ * description says device.  The library allocates its own device memory
+ * (tables, shift words, partial sums) and frees it in the matching destroy
+ * call.  Calls return QQMC_OK (0) or a negative QQMC_E_* code; no call
+ * throws, aborts or exits.  qqmc_last_error() describes the last failure of
+ * the calling thread.  Objects may be used from several threads, but one
+ * problem or plan must not be used by two threads at once; a server is
+ * fully thread-safe.
+ */
+#ifndef QQMC_H
+#define QQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QQMC_OK 0
+#define QQMC_PENDING 1
+#define QQMC_E_INVAL (-1)     /* malformed argument */
+#define QQMC_E_RANGE (-2)     /* order outside 1..QQMC_MAX_ORDER */
+#define QQMC_E_NOMEM (-3)     /* device or host allocation failed */
+#define QQMC_E_CUDA (-4)      /* CUDA runtime error (no device, launch failure) */
+#define QQMC_E_BUSY (-5)      /* server queue full */
+#define QQMC_E_TIMEOUT (-6)   /* request or wait exceeded its limit */
+#define QQMC_E_CANCELLED (-7) /* request cancelled before completion */
+#define QQMC_E_NOTFOUND (-8)  /* unknown handle */
+
+#define QQMC_MAX_ORDER 12
+#define QQMC_MAX_POINTS_LOG2 30 /* N <= 2^30 points per shifted sequence */
+
+/* Arithmetic of the determinant stage. */
+#define QQMC_PREC_FP64 0  /* tables, Schur updates and sums in FP64 */
+#define QQMC_PREC_MIXED 1 /* tables and Schur updates in FP32, leaf sums two-sum
+                             compensated, point and shift sums in FP64 */
+
+/* Physical problem and warp (paper: App. E model, App. F exponential h). */
+typedef struct qqmc_params {
+    double gamma;    /* tunnelling rate Gamma (Lorentzian half-width), > 0 */
+    double eps_d;    /* dot level eps_d */
+    double t_max;    /* measurement time t = u_0; tables cover [-t_max, t_max]; > 0 */
+    double tau;      /* model-function decay: h(v) = exp(-v / tau), > 0 */
+    int32_t n_table; /* L, number of table nodes; even, 4 <= L <= 2^20 */
+    int32_t reserved;
+    uint64_t seed;   /* digital-shift seed (used when no shift words are given) */
+} qqmc_params;
+
+typedef struct qqmc_problem qqmc_problem;
+
+/*
+ * Build a problem: the g^<, g^> tables of the wide-band dot at T = 0, V = 0
+ * are computed on the device by the App. E contour-deformed Fourier integral
+ * (vertical ray into the half plane where e^{-i w tau} decays, plus the real
+ * segment up to the Fermi level; composite Gauss-Legendre), g^> from the
+ * exact sum rule g^> - g^< = -i exp(-i eps_d tau - Gamma |tau|), and kept
+ * resident in device memory.  *out is owned by the caller until
+ * qqmc_destroy_problem.  Errors: E_INVAL (bad params), E_NOMEM, E_CUDA.
+ */
+int qqmc_create_problem(const qqmc_params *p, qqmc_problem **out);
+
+/*
+ * Build a problem from caller tables (any Green function known on the mesh,
+ * paper App. E: the integrand is defined once g is known in time).
+ * g_lesser, g_greater: 2*L doubles each (interleaved complex) on the nodes
+ * above; only the nodes with tau > 0 and the node next to 0 are read (the
+ * tables are assumed to obey g(-tau) = -conj g(tau)).  g0 = g^<(0), used on
+ * the diagonal of every Wick determinant.  Copied; the caller keeps its
+ * buffers.  Errors: E_INVAL, E_NOMEM, E_CUDA.
+ */
+int qqmc_create_problem_tables(const qqmc_params *p, const double *g_lesser, const double *g_greater,
+                               double g0_re, double g0_im, qqmc_problem **out);
+
+/* Free a problem and its device memory.  NULL is accepted. */
+int qqmc_destroy_problem(qqmc_problem *pr);
+
+/* Copy the problem's tables to host: 2*L doubles each, full [-t_max, t_max]
+ * mesh (negative nodes filled by g(-tau) = -conj g(tau)). */
+int qqmc_problem_tables(const qqmc_problem *pr, double *g_lesser, double *g_greater, double *g0);
+
+/* Result of one order-n integration. */
+typedef struct qqmc_result {
+    int32_t order;
+    int32_t n_shifts;          /* K */
+    uint64_t n_points;         /* N per shifted sequence */
+    double q_mean;             /* mean over shifts of Q_n^(k) */
+    double q_err;              /* std_{ddof=1} over shifts / sqrt(K) (0 if K == 1) */
+    double q_imag_absmax;      /* max_k |Im Q_n^(k)| (zero in exact arithmetic) */
+    uint64_t n_in_domain;      /* points with u_n > 0, summed over shifts */
+    double device_ms;          /* device time of the launch that produced it */
+} qqmc_result;
+
+/*
+ * One order-n integration (paper App. B main loop, Eq. (warped_int2)),
+ * blocking.  order in 1..QQMC_MAX_ORDER (else E_RANGE); 1 <= n_points <=
+ * 2^QQMC_MAX_POINTS_LOG2, 1 <= n_shifts <= 1024 (else E_INVAL).
+ * shift_words: host [n_shifts][order] uint32 or NULL (then from the seed).
+ * per_shift: host [n_shifts][2] doubles or NULL; receives
+ *   S_k = (1/N) sum_i w_i c_n(u_i) (complex), so Q_n^(k) = -2i S_k.
+ * precision: QQMC_PREC_FP64 or QQMC_PREC_MIXED.
+ */
+int qqmc_integrate(qqmc_problem *pr, int order, uint64_t n_points, int n_shifts, int precision,
+                   const uint32_t *shift_words, double *per_shift, qqmc_result *out);
+
+/* One work item of a batched launch: an order-n integration of a problem. */
+typedef struct qqmc_item {
+    qqmc_problem *problem;
+    int32_t order;
+    int32_t n_shifts;
+    uint64_t n_points;
+    uint64_t first_index;         /* first Sobol' index (0 normally; resume point otherwise) */
+    const uint32_t *shift_words;  /* host [n_shifts][order] or NULL (from the problem seed) */
+} qqmc_item;
+
+typedef struct qqmc_plan qqmc_plan;
+
+/*
+ * Batched, device-resident execution.  qqmc_plan_create uploads the items'
+ * shift words and allocates the partial-sum buffers (the problems must
+ * outlive the plan).  qqmc_plan_launch enqueues the whole batch -- one
+ * persistent kernel over all items (uneven orders and point counts share
+ * one launch) and one reduction kernel -- on `stream` (a cudaStream_t, or
+ * NULL for the legacy default stream) and returns without waiting; with
+ * use_graph != 0 the pair is captured once into a CUDA graph and replayed.
+ * qqmc_plan_results waits for the last launch and copies per-item results
+ * (results: [n_items]; per_shift: concatenated [sum_k n_shifts][2] S_k, or
+ * NULL).  qqmc_plan_device_ms returns the device time of the last launch.
+ */
+int qqmc_plan_create(const qqmc_item *items, int n_items, int precision, qqmc_plan **out);
+int qqmc_plan_launch(qqmc_plan *plan, void *stream, int use_graph);
+int qqmc_plan_results(qqmc_plan *plan, qqmc_result *results, double *per_shift);
+int qqmc_plan_destroy(qqmc_plan *plan);
+/* Kernel launches a plan issues per qqmc_plan_launch (for launch accounting). */
+int qqmc_plan_kernel_count(const qqmc_plan *plan);
+/* Device time of the last launch, after qqmc_plan_results: the determinant
+ * kernel alone (events on the launch stream around it; 0 when the launch was a
+ * graph replay) and the whole launch. */
+int qqmc_plan_timing(const qqmc_plan *plan, double *kernel_ms, double *total_ms);
+
+/*
+ * Tuning of the determinant kernel (the autotuner writes these): for
+ * each order, the number of warps per block and the number of vertices
+ * resolved per lane in the flat (per-lane) phase.  Values <= 0 restore
+ * the built-in defaults.  Applies to plans created afterwards.
+ */
+int qqmc_set_tuning(int precision, int order, int warps_per_block, int flat_vertices);
+int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_vertices);
+
+/* ---------------------------- inspection calls ---------------------------- */
+
+/* Sobol' direction words of the product generator (Joe-Kuo primitive
+ * polynomials and initial values, standard recurrence): out [n_dims][32]. */
+int qqmc_direction_numbers(int n_dims, uint32_t *out);
+
+/* Shift words derived from a seed: out [n_shifts][n_dims] (splitmix64 rule above). */
+int qqmc_shift_words(uint64_t seed, int n_shifts, int n_dims, uint32_t *out);
+
+/* Shifted Sobol' integers Y_i = X_i XOR shift computed on the device for
+ * indices first_index .. first_index+count-1: out [count][order] (host).
+ * shift: host [order] or NULL (zero shift). */
+int qqmc_sobol_points(int order, uint64_t first_index, uint64_t count, const uint32_t *shift, uint32_t *out);
+
+/* Warped points on the device: u [count][order], weight C/p_n [count],
+ * inside [count] (1 iff u_n > 0), for the problem's t_max and tau. */
+int qqmc_warp_points(const qqmc_problem *pr, int order, uint64_t first_index, uint64_t count,
+                     const uint32_t *shift, double *u, double *w, int32_t *inside);
+
+/* Integrand c_n(u) at caller points u [count][order] (host, strictly
+ * decreasing within t_max > u_1 > ... > u_n > 0), evaluated by the same
+ * device code as the integration: out [count][2] (complex). */
+int qqmc_integrand(const qqmc_problem *pr, int order, uint64_t count, const double *u, int precision,
+                   double *out);
+
+/* ------------------------------- serving ---------------------------------- */
+
+typedef struct qqmc_server qqmc_server;
+
+typedef struct qqmc_server_opts {
+    uint64_t device_memory_limit; /* bytes the server may hold on the device (0: 4 GiB) */
+    int32_t max_queue;            /* pending requests before E_BUSY (0: 4096) */
+    int32_t max_batch_items;      /* items per persistent launch (0: 256) */
+    int32_t precision;            /* QQMC_PREC_* used for every request */
+    int32_t use_graph;            /* capture each batch launch in a CUDA graph */
+    double request_timeout_s;     /* 0: none */
+} qqmc_server_opts;
+
+/* A request: Q_1..Q_{n_max} of one dot (paper App. H parameter sweep). */
+typedef struct qqmc_request {
+    qqmc_params params;
+    int32_t n_max;      /* 1..QQMC_MAX_ORDER */
+    int32_t n_shifts;   /* K >= 2 */
+    uint64_t n_points;  /* N per shift */
+    double U;           /* interaction for the truncated series sum_n Q_n U^n */
+} qqmc_request;
+
+typedef struct qqmc_series {
+    int32_t n_max;
+    int32_t status;                    /* QQMC_OK or an error code */
+    double q[QQMC_MAX_ORDER + 1];      /* q[0] = Q_0 = -2i g^<(0); q[n] = Q_n */
+    double q_err[QQMC_MAX_ORDER + 1];
+    double series_sum;                 /* sum_{n <= n_max} Q_n U^n (truncated, not resummed) */
+    double latency_ms;                 /* submit -> completion */
+    double queue_ms;                   /* submit -> admission */
+    uint64_t n_in_domain;
+} qqmc_series;
+
+int qqmc_server_create(const qqmc_server_opts *opts, qqmc_server **out);
+/* Non-blocking.  E_BUSY when the pending queue is full. */
+int qqmc_submit(qqmc_server *s, const qqmc_request *r, uint64_t *handle);
+/* QQMC_PENDING, QQMC_OK (out filled; the handle is released) or an error code
+ * (out->status set; the handle is released). */
+int qqmc_poll(qqmc_server *s, uint64_t handle, qqmc_series *out);
+int qqmc_cancel(qqmc_server *s, uint64_t handle);
+/* Waits for in-flight work, fails pending requests with E_CANCELLED, frees all. */
+int qqmc_server_destroy(qqmc_server *s);
+
+/* Copy the calling thread's last error message (NUL-terminated, truncated). */
+int qqmc_last_error(char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QQMC_H */

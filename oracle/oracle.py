@@ -42,6 +42,7 @@ import ctypes
 import math
 import os
 import subprocess
+import threading
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
@@ -52,6 +53,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 _lib = None
+_lib_lock = threading.Lock()
 
 
 def build(force: bool = False) -> str:
@@ -67,7 +69,11 @@ def build(force: bool = False) -> str:
 
 def lib():
     global _lib
-    if _lib is None:
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
         build()
         L = ctypes.CDLL(_SO)
         dp = ctypes.POINTER(ctypes.c_double)

@@ -1,0 +1,572 @@
+// C ABI: problems, single and batched integrations, inspection calls.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qqmc_internal.h"
+
+using namespace qqmc;
+
+struct qqmc_problem : public qqmc::Problem {};
+
+namespace qqmc {
+
+// ---------------------------------------------------------------- device init
+static std::mutex g_init_mu;
+static bool g_init_done[64];
+
+static int ensure_device() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(QQMC_E_CUDA, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (g_init_done[dev]) return QQMC_OK;
+    int rc = upload_direction_numbers();
+    if (rc != QQMC_OK) return rc;
+    g_init_done[dev] = true;
+    return QQMC_OK;
+}
+
+// ---------------------------------------------------------------- tuning
+static std::mutex g_tune_mu;
+static Tuning g_tune[2][kMaxOrder + 1];
+static bool g_tune_set[2][kMaxOrder + 1];
+
+static Tuning default_tuning(int precision, int order) {
+    (void)order;
+    Tuning t;
+    t.flat = 5;
+    t.warps_per_block = precision == QQMC_PREC_FP64 ? 2 : 4;
+    return t;
+}
+
+Tuning get_tuning(int precision, int order) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int p = precision == QQMC_PREC_FP64 ? 0 : 1;
+    if (order >= 1 && order <= kMaxOrder && g_tune_set[p][order]) return g_tune[p][order];
+    return default_tuning(precision, order);
+}
+
+}  // namespace qqmc
+
+static bool valid_params(const qqmc_params *p, std::string &why) {
+    if (!p) { why = "params is NULL"; return false; }
+    if (!(p->gamma > 0) || !isfinite(p->gamma)) { why = "gamma must be > 0"; return false; }
+    if (!isfinite(p->eps_d)) { why = "eps_d must be finite"; return false; }
+    if (!(p->t_max > 0) || !isfinite(p->t_max)) { why = "t_max must be > 0"; return false; }
+    if (!(p->tau > 0) || !isfinite(p->tau)) { why = "tau must be > 0"; return false; }
+    if (p->n_table < 4 || p->n_table > (1 << 20) || (p->n_table & 1)) {
+        why = "n_table must be even and in 4..2^20";
+        return false;
+    }
+    return true;
+}
+
+static int alloc_problem(const qqmc_params *p, qqmc_problem **out) {
+    std::string why;
+    if (!out) return set_error(QQMC_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!valid_params(p, why)) return set_error(QQMC_E_INVAL, "qqmc params: " + why);
+    int rc = ensure_device();
+    if (rc != QQMC_OK) return rc;
+    qqmc_problem *pr = new (std::nothrow) qqmc_problem();
+    if (!pr) return set_error(QQMC_E_NOMEM, "host allocation failed");
+    pr->params = *p;
+    pr->L = p->n_table;
+    pr->h = 2.0 * p->t_max / (double)(p->n_table - 1);
+    cudaGetDevice(&pr->device);
+    size_t nh = (size_t)pr->L / 2 + 1;
+    cudaError_t e = cudaMalloc(&pr->d_table, nh * sizeof(dbl4));
+    if (e == cudaSuccess) e = cudaMalloc(&pr->d_table32, nh * sizeof(float4));
+    if (e != cudaSuccess) {
+        cudaFree(pr->d_table);
+        delete pr;
+        return set_error(QQMC_E_NOMEM, std::string("device allocation of the tables failed: ") + cudaGetErrorString(e));
+    }
+    *out = pr;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_create_problem(const qqmc_params *p, qqmc_problem **out) {
+    qqmc_problem *pr = nullptr;
+    int rc = alloc_problem(p, &pr);
+    if (rc != QQMC_OK) return rc;
+    pr->g0_re = 0.0;
+    pr->g0_im = 0.5 - atan(p->eps_d / p->gamma) / M_PI;
+    rc = launch_gf_table(*pr, 0);
+    if (rc == QQMC_OK) {
+        cudaError_t e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) rc = cuda_error(e, "table build");
+    }
+    if (rc != QQMC_OK) {
+        qqmc_destroy_problem(pr);
+        return rc;
+    }
+    *out = pr;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_create_problem_tables(const qqmc_params *p, const double *gl, const double *gg, double g0_re,
+                                          double g0_im, qqmc_problem **out) {
+    if (!gl || !gg) return set_error(QQMC_E_INVAL, "tables are NULL");
+    if (!isfinite(g0_re) || !isfinite(g0_im)) return set_error(QQMC_E_INVAL, "g0 must be finite");
+    qqmc_problem *pr = nullptr;
+    int rc = alloc_problem(p, &pr);
+    if (rc != QQMC_OK) return rc;
+    pr->g0_re = g0_re;
+    pr->g0_im = g0_im;
+    const int L = pr->L;
+    const int k0 = L / 2 - 1;
+    std::vector<dbl4> h(L / 2 + 1);
+    std::vector<float4> h32(L / 2 + 1);
+    for (int q = 0; q <= L / 2; ++q) {
+        int k = k0 + q;
+        h[q] = make_double4_32a(gl[2 * k], gl[2 * k + 1], gg[2 * k], gg[2 * k + 1]);
+        h32[q] = make_float4((float)gl[2 * k], (float)gl[2 * k + 1], (float)gg[2 * k], (float)gg[2 * k + 1]);
+    }
+    cudaError_t e = cudaMemcpy(pr->d_table, h.data(), h.size() * sizeof(dbl4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pr->d_table32, h32.data(), h32.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        qqmc_destroy_problem(pr);
+        return cuda_error(e, "table upload");
+    }
+    *out = pr;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_destroy_problem(qqmc_problem *pr) {
+    if (!pr) return QQMC_OK;
+    cudaFree(pr->d_table);
+    cudaFree(pr->d_table32);
+    delete pr;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_problem_tables(const qqmc_problem *pr, double *gl, double *gg, double *g0) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    const int L = pr->L;
+    std::vector<dbl4> h(L / 2 + 1);
+    cudaError_t e = cudaMemcpy(h.data(), pr->d_table, h.size() * sizeof(dbl4), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "table download");
+    const int k0 = L / 2 - 1;
+    for (int k = 0; k < L; ++k) {
+        dbl4 v;
+        if (k >= k0) {
+            v = h[k - k0];
+        } else {  // mirror: node k is -tau of node L-1-k
+            dbl4 m = h[(L - 1 - k) - k0];
+            v = make_double4_32a(-m.x, m.y, -m.z, m.w);
+        }
+        if (gl) { gl[2 * k] = v.x; gl[2 * k + 1] = v.y; }
+        if (gg) { gg[2 * k] = v.z; gg[2 * k + 1] = v.w; }
+    }
+    if (g0) { g0[0] = pr->g0_re; g0[1] = pr->g0_im; }
+    return QQMC_OK;
+}
+
+// ---------------------------------------------------------------- plans
+struct qqmc_plan {
+    std::vector<qqmc_item> items;
+    std::vector<ItemDev> hitems;
+    int precision = 0;
+    int n_max = 0;
+    long long total_chunks = 0;
+    int total_shifts = 0;
+    ItemDev *d_items = nullptr;
+    uint32_t *d_shifts = nullptr;
+    double *d_partials = nullptr;
+    unsigned int *d_inside = nullptr;
+    unsigned long long *d_counter = nullptr;
+    double *d_out = nullptr;
+    unsigned long long *d_counts = nullptr;
+    Tuning tune{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ek0 = nullptr, ek1 = nullptr;
+    bool kernel_timed = false;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    bool launched = false;
+    int device = 0;
+};
+
+static void free_plan(qqmc_plan *pl) {
+    if (!pl) return;
+    if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+    cudaFree(pl->d_items);
+    cudaFree(pl->d_shifts);
+    cudaFree(pl->d_partials);
+    cudaFree(pl->d_inside);
+    cudaFree(pl->d_counter);
+    cudaFree(pl->d_out);
+    cudaFree(pl->d_counts);
+    if (pl->ev0) cudaEventDestroy(pl->ev0);
+    if (pl->ev1) cudaEventDestroy(pl->ev1);
+    if (pl->ek0) cudaEventDestroy(pl->ek0);
+    if (pl->ek1) cudaEventDestroy(pl->ek1);
+    delete pl;
+}
+
+extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precision, qqmc_plan **out) {
+    if (!out) return set_error(QQMC_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!items || n_items < 1 || n_items > 65536) return set_error(QQMC_E_INVAL, "n_items must be in 1..65536");
+    if (precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED)
+        return set_error(QQMC_E_INVAL, "precision must be QQMC_PREC_FP64 or QQMC_PREC_MIXED");
+    for (int i = 0; i < n_items; ++i) {
+        const qqmc_item &it = items[i];
+        if (!it.problem) return set_error(QQMC_E_INVAL, "item has no problem");
+        if (it.order < 1 || it.order > kMaxOrder) return set_error(QQMC_E_RANGE, "order outside 1..QQMC_MAX_ORDER");
+        if (it.n_points < 1 || it.n_points > (1ull << QQMC_MAX_POINTS_LOG2))
+            return set_error(QQMC_E_INVAL, "n_points must be in 1..2^30");
+        if (it.n_shifts < 1 || it.n_shifts > 1024) return set_error(QQMC_E_INVAL, "n_shifts must be in 1..1024");
+        if (it.first_index > (1ull << 40)) return set_error(QQMC_E_INVAL, "first_index too large");
+    }
+    int rc = ensure_device();
+    if (rc != QQMC_OK) return rc;
+    qqmc_plan *pl = new (std::nothrow) qqmc_plan();
+    if (!pl) return set_error(QQMC_E_NOMEM, "host allocation failed");
+    cudaGetDevice(&pl->device);
+    pl->items.assign(items, items + n_items);
+    pl->precision = precision;
+    size_t shift_words_total = 0, chunk_total = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const qqmc_item &it = items[i];
+        pl->n_max = it.order > pl->n_max ? it.order : pl->n_max;
+        shift_words_total += (size_t)it.n_shifts * it.order;
+        size_t cps = (it.n_points + kChunk - 1) / kChunk;
+        chunk_total += cps * it.n_shifts;
+        pl->total_shifts += it.n_shifts;
+    }
+    pl->total_chunks = (long long)chunk_total;
+    pl->tune = get_tuning(precision, pl->n_max);
+    cudaError_t e = cudaMalloc(&pl->d_items, sizeof(ItemDev) * n_items);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_shifts, sizeof(uint32_t) * shift_words_total);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_partials, sizeof(double) * 4 * chunk_total);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_inside, sizeof(unsigned int) * chunk_total);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_out, sizeof(double) * 2 * pl->total_shifts);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counts, sizeof(unsigned long long) * pl->total_shifts);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return set_error(QQMC_E_NOMEM, std::string("device allocation of the plan failed: ") + cudaGetErrorString(e));
+    }
+    std::vector<uint32_t> hs(shift_words_total);
+    size_t so = 0, co = 0;
+    pl->hitems.resize(n_items);
+    for (int i = 0; i < n_items; ++i) {
+        const qqmc_item &it = items[i];
+        const qqmc_problem *pr = it.problem;
+        if (it.shift_words)
+            memcpy(hs.data() + so, it.shift_words, sizeof(uint32_t) * it.n_shifts * it.order);
+        else
+            shift_words(pr->params.seed, it.n_shifts, it.order, hs.data() + so);
+        ItemDev &d = pl->hitems[i];
+        d.table = pr->d_table;
+        d.table32 = pr->d_table32;
+        d.shifts = pl->d_shifts + so;
+        size_t cps = (it.n_points + kChunk - 1) / kChunk;
+        d.partials = pl->d_partials + 4 * co;
+        d.inside = pl->d_inside + co;
+        d.g0_re = pr->g0_re;
+        d.g0_im = pr->g0_im;
+        d.t = pr->params.t_max;
+        d.tau = pr->params.tau;
+        d.T = pr->params.t_max;
+        d.h = pr->h;
+        d.first_index = (long long)it.first_index;
+        d.n_points = (long long)it.n_points;
+        d.chunk_begin = (long long)co;
+        d.order = it.order;
+        d.n_shifts = it.n_shifts;
+        d.L = pr->L;
+        d.chunks_per_shift = (int)cps;
+        so += (size_t)it.n_shifts * it.order;
+        co += cps * it.n_shifts;
+    }
+    e = cudaMemcpy(pl->d_shifts, hs.data(), sizeof(uint32_t) * shift_words_total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_items, pl->hitems.data(), sizeof(ItemDev) * n_items, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreate(&pl->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&pl->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&pl->ek0);
+    if (e == cudaSuccess) e = cudaEventCreate(&pl->ek1);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return cuda_error(e, "plan upload");
+    }
+    *out = pl;
+    return QQMC_OK;
+}
+
+static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
+    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecord(pl->ek0, s)) != cudaSuccess) return e;
+    e = launch_detsum(pl->d_items, (int)pl->items.size(), pl->total_chunks, pl->d_counter, pl->n_max, pl->precision,
+                      pl->tune, s);
+    if (e != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecord(pl->ek1, s)) != cudaSuccess) return e;
+    return launch_reduce(pl->d_items, (int)pl->items.size(), pl->total_shifts, pl->d_out, pl->d_counts, s);
+}
+
+extern "C" int qqmc_plan_launch(qqmc_plan *pl, void *stream, int use_graph) {
+    if (!pl) return set_error(QQMC_E_INVAL, "plan is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaEventRecord(pl->ev0, s);
+    if (e != cudaSuccess) return cuda_error(e, "event record");
+    if (use_graph) {
+        if (!pl->gexec || pl->gstream != s) {
+            if (pl->gexec) {
+                cudaGraphExecDestroy(pl->gexec);
+                pl->gexec = nullptr;
+            }
+            cudaStream_t cs = s;
+            bool own = false;
+            if (cs == 0) {  // the legacy stream cannot be captured: capture on a private stream
+                e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+                if (e != cudaSuccess) return cuda_error(e, "stream create");
+                own = true;
+            }
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e2 = enqueue_plan(pl, cs, false);
+                e = cudaStreamEndCapture(cs, &g);
+                if (e2 != cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->gexec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (own) cudaStreamDestroy(cs);
+            if (e != cudaSuccess) return cuda_error(e, "graph capture");
+            pl->gstream = s;
+        }
+        e = cudaGraphLaunch(pl->gexec, s);
+        pl->kernel_timed = false;
+    } else {
+        e = enqueue_plan(pl, s, true);
+        pl->kernel_timed = true;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "plan launch");
+    e = cudaEventRecord(pl->ev1, s);
+    if (e != cudaSuccess) return cuda_error(e, "event record");
+    pl->launched = true;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_plan_kernel_count(const qqmc_plan *pl) { return pl ? 2 : 0; }
+
+extern "C" int qqmc_plan_timing(const qqmc_plan *pl, double *kernel_ms, double *total_ms) {
+    if (!pl || !pl->launched) return set_error(QQMC_E_INVAL, "plan is NULL or was not launched");
+    cudaError_t e = cudaEventSynchronize(pl->ev1);
+    if (e != cudaSuccess) return cuda_error(e, "plan execution");
+    float a = 0.f, k = 0.f;
+    cudaEventElapsedTime(&a, pl->ev0, pl->ev1);
+    if (pl->kernel_timed) cudaEventElapsedTime(&k, pl->ek0, pl->ek1);
+    if (kernel_ms) *kernel_ms = k;
+    if (total_ms) *total_ms = a;
+    return QQMC_OK;
+}
+
+static void finish_result(const qqmc_item &it, const double *S, const unsigned long long *cnt, float ms,
+                          qqmc_result *r) {
+    const int K = it.n_shifts;
+    const double N = (double)it.n_points;
+    double mean = 0.0, imax = 0.0;
+    uint64_t nin = 0;
+    std::vector<double> q(K);
+    for (int k = 0; k < K; ++k) {
+        // Q = -2i S / N
+        q[k] = 2.0 * S[2 * k + 1] / N;
+        double qi = -2.0 * S[2 * k] / N;
+        mean += q[k];
+        imax = fabs(qi) > imax ? fabs(qi) : imax;
+        nin += cnt[k];
+    }
+    mean /= K;
+    double var = 0.0;
+    for (int k = 0; k < K; ++k) var += (q[k] - mean) * (q[k] - mean);
+    r->order = it.order;
+    r->n_shifts = K;
+    r->n_points = it.n_points;
+    r->q_mean = mean;
+    r->q_err = K > 1 ? sqrt(var / (K - 1)) / sqrt((double)K) : 0.0;
+    r->q_imag_absmax = imax;
+    r->n_in_domain = nin;
+    r->device_ms = ms;
+}
+
+extern "C" int qqmc_plan_results(qqmc_plan *pl, qqmc_result *results, double *per_shift) {
+    if (!pl) return set_error(QQMC_E_INVAL, "plan is NULL");
+    if (!pl->launched) return set_error(QQMC_E_INVAL, "plan was not launched");
+    cudaError_t e = cudaEventSynchronize(pl->ev1);
+    if (e != cudaSuccess) return cuda_error(e, "plan execution");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pl->ev0, pl->ev1);
+    std::vector<double> S(2 * (size_t)pl->total_shifts);
+    std::vector<unsigned long long> cnt(pl->total_shifts);
+    e = cudaMemcpy(S.data(), pl->d_out, sizeof(double) * S.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(cnt.data(), pl->d_counts, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "result download");
+    size_t g = 0;
+    for (size_t i = 0; i < pl->items.size(); ++i) {
+        const qqmc_item &it = pl->items[i];
+        if (results) finish_result(it, S.data() + 2 * g, cnt.data() + g, ms, &results[i]);
+        if (per_shift)
+            for (int k = 0; k < it.n_shifts; ++k) {
+                per_shift[2 * (g + k)] = S[2 * (g + k)] / (double)it.n_points;
+                per_shift[2 * (g + k) + 1] = S[2 * (g + k) + 1] / (double)it.n_points;
+            }
+        g += it.n_shifts;
+    }
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_plan_destroy(qqmc_plan *pl) {
+    free_plan(pl);
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_integrate(qqmc_problem *pr, int order, uint64_t n_points, int n_shifts, int precision,
+                              const uint32_t *shift_words, double *per_shift, qqmc_result *out) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    qqmc_item it;
+    it.problem = pr;
+    it.order = order;
+    it.n_shifts = n_shifts;
+    it.n_points = n_points;
+    it.first_index = 0;
+    it.shift_words = shift_words;
+    qqmc_plan *pl = nullptr;
+    int rc = qqmc_plan_create(&it, 1, precision, &pl);
+    if (rc != QQMC_OK) return rc;
+    rc = qqmc_plan_launch(pl, nullptr, 0);
+    if (rc == QQMC_OK) rc = qqmc_plan_results(pl, out, per_shift);
+    qqmc_plan_destroy(pl);
+    return rc;
+}
+
+extern "C" int qqmc_set_tuning(int precision, int order, int warps_per_block, int flat_vertices) {
+    if ((precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED) || order < 1 || order > kMaxOrder)
+        return set_error(QQMC_E_INVAL, "qqmc_set_tuning: bad precision or order");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int p = precision == QQMC_PREC_FP64 ? 0 : 1;
+    if (warps_per_block <= 0 || flat_vertices <= 0) {
+        g_tune_set[p][order] = false;
+        return QQMC_OK;
+    }
+    if (warps_per_block > 16 || flat_vertices < 3 || flat_vertices > 5)
+        return set_error(QQMC_E_INVAL, "qqmc_set_tuning: warps_per_block in 1..16, flat_vertices in 3..5");
+    g_tune[p][order].warps_per_block = warps_per_block;
+    g_tune[p][order].flat = flat_vertices;
+    g_tune_set[p][order] = true;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_get_tuning(int precision, int order, int *wpb, int *flat) {
+    if ((precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED) || order < 1 || order > kMaxOrder || !wpb ||
+        !flat)
+        return set_error(QQMC_E_INVAL, "qqmc_get_tuning: bad arguments");
+    Tuning t = get_tuning(precision, order);
+    *wpb = t.warps_per_block;
+    *flat = t.flat;
+    return QQMC_OK;
+}
+
+// ---------------------------------------------------------------- inspection
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    cudaError_t alloc(size_t n) { return cudaMalloc(&p, sizeof(T) * (n ? n : 1)); }
+    ~DevBuf() { cudaFree(p); }
+};
+
+extern "C" int qqmc_sobol_points(int order, uint64_t first, uint64_t count, const uint32_t *shift, uint32_t *out) {
+    if (order < 1 || order > kMaxOrder) return set_error(QQMC_E_RANGE, "order outside 1..QQMC_MAX_ORDER");
+    if (!out || count > (1ull << 28)) return set_error(QQMC_E_INVAL, "bad output or count");
+    if (count == 0) return QQMC_OK;
+    int rc = ensure_device();
+    if (rc != QQMC_OK) return rc;
+    DevBuf<uint32_t> d_out, d_shift;
+    cudaError_t e = d_out.alloc(count * order);
+    if (e == cudaSuccess && shift) {
+        e = d_shift.alloc(order);
+        if (e == cudaSuccess) e = cudaMemcpy(d_shift.p, shift, sizeof(uint32_t) * order, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = launch_sobol(order, first, count, shift ? d_shift.p : nullptr, d_out.p, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out.p, sizeof(uint32_t) * count * order, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "qqmc_sobol_points");
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_warp_points(const qqmc_problem *pr, int order, uint64_t first, uint64_t count,
+                                const uint32_t *shift, double *u, double *w, int32_t *inside) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    if (order < 1 || order > kMaxOrder) return set_error(QQMC_E_RANGE, "order outside 1..QQMC_MAX_ORDER");
+    if (!u || !w || !inside || count > (1ull << 26)) return set_error(QQMC_E_INVAL, "bad output or count");
+    if (count == 0) return QQMC_OK;
+    int rc = ensure_device();
+    if (rc != QQMC_OK) return rc;
+    DevBuf<uint32_t> d_shift;
+    DevBuf<double> d_u, d_w;
+    DevBuf<int32_t> d_in;
+    cudaError_t e = d_u.alloc(count * order);
+    if (e == cudaSuccess) e = d_w.alloc(count);
+    if (e == cudaSuccess) e = d_in.alloc(count);
+    if (e == cudaSuccess && shift) {
+        e = d_shift.alloc(order);
+        if (e == cudaSuccess) e = cudaMemcpy(d_shift.p, shift, sizeof(uint32_t) * order, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess)
+        e = launch_warp(order, first, count, shift ? d_shift.p : nullptr, pr->params.t_max, pr->params.tau, d_u.p,
+                        d_w.p, d_in.p, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(u, d_u.p, sizeof(double) * count * order, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(w, d_w.p, sizeof(double) * count, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(inside, d_in.p, sizeof(int32_t) * count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "qqmc_warp_points");
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_integrand(const qqmc_problem *pr, int order, uint64_t count, const double *u, int precision,
+                              double *out) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    if (order < 1 || order > kMaxOrder) return set_error(QQMC_E_RANGE, "order outside 1..QQMC_MAX_ORDER");
+    if (precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED)
+        return set_error(QQMC_E_INVAL, "precision must be QQMC_PREC_FP64 or QQMC_PREC_MIXED");
+    if (!u || !out || count > (1ull << 24)) return set_error(QQMC_E_INVAL, "bad input, output or count");
+    const double t = pr->params.t_max;
+    for (uint64_t q = 0; q < count; ++q) {
+        double prev = t;
+        for (int m = 0; m < order; ++m) {
+            double v = u[q * order + m];
+            if (!(v < prev) || !(v > 0.0)) return set_error(QQMC_E_INVAL, "points must satisfy t_max > u_1 > ... > u_n > 0");
+            prev = v;
+        }
+    }
+    if (count == 0) return QQMC_OK;
+    int rc = ensure_device();
+    if (rc != QQMC_OK) return rc;
+    DevBuf<double> d_u, d_out;
+    cudaError_t e = d_u.alloc(count * order);
+    if (e == cudaSuccess) e = d_out.alloc(2 * count);
+    if (e == cudaSuccess) e = cudaMemcpy(d_u.p, u, sizeof(double) * count * order, cudaMemcpyHostToDevice);
+    ItemDev it{};
+    it.table = pr->d_table;
+    it.table32 = pr->d_table32;
+    it.g0_re = pr->g0_re;
+    it.g0_im = pr->g0_im;
+    it.t = t;
+    it.tau = pr->params.tau;
+    it.T = t;
+    it.h = pr->h;
+    it.L = pr->L;
+    it.order = order;
+    if (e == cudaSuccess) e = launch_integrand(it, count, d_u.p, d_out.p, precision, get_tuning(precision, order), 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out.p, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "qqmc_integrand");
+    return QQMC_OK;
+}

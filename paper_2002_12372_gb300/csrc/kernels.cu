@@ -1,0 +1,830 @@
+// QQMC device kernels for sm_103a.
+//
+//  * gf_table_kernel   -- g^<(tau), g^>(tau) of the wide-band dot by the
+//                         contour-deformed Fourier integral of App. E.
+//  * detsum_kernel     -- the hot path: Sobol' point generation with a digital
+//                         shift, exponential product-model warp, pair
+//                         interpolation of the Green-function tables and the
+//                         Keldysh sum of det M_up * det M_down (App. E
+//                         Eq. (integral_gf)), weighted and reduced per chunk.
+//  * reduce_kernel     -- per shifted sequence, compensated sum of the chunk
+//                         partials (Eq. (warped_int2)).
+//  * sobol/warp/integrand kernels -- the same device code exposed for checks.
+//
+// Keldysh sum: the vertices are ordered t = u_0 > u_1 > ... > u_n > 0.  For a
+// pair j < k the Keldysh matrix entry above the diagonal depends only on a_k
+// (a_k = 0: g^>(u_j-u_k), a_k = 1: g^<(u_j-u_k)) and the one below only on a_k
+// too (a_k = 0: g^<(u_k-u_j), a_k = 1: g^>(u_k-u_j)); the diagonal is g^<(0).
+// Row 0 / column 0 of M_up are the measurement points (t, a=0) / (t, a=1).
+// Hence, once the leading vertices are eliminated, every entry of the Schur
+// complement depends only on the Keldysh indices of its own row and column
+// vertices.  The kernel walks the binary tree of Keldysh indices depth first
+// and keeps, per tree level, the Schur complement for BOTH choices of every
+// remaining vertex: a (2R+2) x (2R+2) matrix (rows/columns = (vertex, choice)
+// plus two copies of the measurement row/column, one per choice of a_1).
+// Fixing a_k is one rank-1 update of that matrix with the pivot (k, a_k).
+// det M_down is the product of the pivots, det M_up / det M_down is the final
+// measurement entry, and sum_{a_1} (-1)^{a_1} det M_up det M_down =
+// det M_down^2 (S_00(a_1=0) - S_00(a_1=1)).  The last F vertices are resolved
+// per lane (one lane per choice path, 2^F paths).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "qqmc_internal.h"
+
+namespace qqmc {
+
+__constant__ uint32_t c_dirs[kMaxOrder][32];
+__constant__ double c_gl_x[16];
+__constant__ double c_gl_w[16];
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ----------------------------------------------------------------------------
+// complex helpers
+// ----------------------------------------------------------------------------
+template <class R>
+struct __align__(2 * sizeof(R)) cx {
+    R re, im;
+};
+
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class R>
+__device__ __forceinline__ cx<R> mk(R a, R b) {
+    cx<R> z;
+    z.re = a;
+    z.im = b;
+    return z;
+}
+template <class R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+    return mk<R>(fmaR(a.re, b.re, -a.im * b.im), fmaR(a.re, b.im, a.im * b.re));
+}
+// c - a * b
+template <class R>
+__device__ __forceinline__ cx<R> cfms(cx<R> c, cx<R> a, cx<R> b) {
+    return mk<R>(fmaR(-a.re, b.re, fmaR(a.im, b.im, c.re)), fmaR(-a.re, b.im, fmaR(-a.im, b.re, c.im)));
+}
+template <class R>
+__device__ __forceinline__ cx<R> crcp(cx<R> a) {
+    R s = R(1) / fmaR(a.re, a.re, a.im * a.im);
+    return mk<R>(a.re * s, -a.im * s);
+}
+template <class R>
+__device__ __forceinline__ cx<R> nconj(cx<R> a) {  // -conj(a)
+    return mk<R>(-a.re, a.im);
+}
+
+// Knuth two-sum accumulator: value = s + c.
+template <class R>
+struct Acc {
+    R s, c;
+    __device__ __forceinline__ void init() { s = R(0); c = R(0); }
+    __device__ __forceinline__ void add(R x) {
+        R t = s + x;
+        R z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+};
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = a + b;
+    double z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+// Deterministic butterfly reduction of (s, c) pairs over the warp.
+__device__ __forceinline__ void warp_reduce_pair(double &s, double &c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double s2 = __shfl_xor_sync(FULL, s, o);
+        double c2 = __shfl_xor_sync(FULL, c, o);
+        double t, e;
+        // combine in a lane-independent order (lower lane's value first)
+        int lo = ((threadIdx.x & 31) & o) == 0;
+        if (lo) two_sum(s, s2, t, e); else two_sum(s2, s, t, e);
+        s = t;
+        c = lo ? (c + c2) + e : (c2 + c) + e;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Sobol' point, shift and warp (shared by the integration and check kernels)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sobol_word(int d, uint64_t i) {
+    uint64_t g = i ^ (i >> 1);
+    uint32_t x = 0;
+    while (g) {
+        int j = __ffsll((long long)g) - 1;
+        x ^= c_dirs[d][j];
+        g &= g - 1;
+    }
+    return x;
+}
+
+// ----------------------------------------------------------------------------
+// Table interpolation: half table starting at node L/2 - 1 (tau = -h/2).
+// ----------------------------------------------------------------------------
+template <class R>
+struct TabT;
+template <>
+struct TabT<double> {
+    using V = dbl4;
+};
+template <>
+struct TabT<float> {
+    using V = float4;
+};
+
+// pair values for tau > 0: gl = g^<(tau), gg = g^>(tau)
+template <class R>
+__device__ __forceinline__ void interp_pair(const typename TabT<R>::V *tab, double T, double h, int L, double tau,
+                                            cx<R> &gl, cx<R> &gg) {
+    double s = (tau + T) / h;
+    double kf = floor(s);
+    int k = (int)kf;
+    int kmin = L / 2 - 1, kmax = L - 2;
+    k = k < kmin ? kmin : (k > kmax ? kmax : k);
+    double f = s - (double)k;
+    typename TabT<R>::V a = tab[k - kmin];
+    typename TabT<R>::V b = tab[k - kmin + 1];
+    R fr = (R)f, g = (R)(1.0 - f);
+    gl = mk<R>(fmaR(fr, b.x, g * a.x), fmaR(fr, b.y, g * a.y));
+    gg = mk<R>(fmaR(fr, b.z, g * a.z), fmaR(fr, b.w, g * a.w));
+}
+
+// ----------------------------------------------------------------------------
+// Per-warp shared-memory layout for the Keldysh sum.
+// ----------------------------------------------------------------------------
+template <class R>
+struct WarpSmem {
+    cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l
+    cx<R> *wrow;    // scaled pivot row, <= 2 n_max entries
+    cx<R> *P;       // P[j*(n_max+1)+k] = g^>(u_j - u_k), j < k
+    cx<R> *Rr;      // Rr[...]          = g^<(u_j - u_k)
+    cx<R> *detD;    // per level
+    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t)
+    double *wpt;    // [32] weights
+};
+
+__host__ __device__ inline size_t stack_entries(int n_max, int F) {
+    size_t tot = 0;
+    int R0 = n_max - 1;
+    int levels = R0 > F ? R0 - F : 0;
+    for (int l = 0; l <= levels; ++l) {
+        size_t S = 2 * (size_t)(R0 - l) + 2;
+        tot += S * S;
+    }
+    return tot;
+}
+
+template <class R>
+__host__ __device__ inline size_t warp_smem_bytes(int n_max, int F) {
+    size_t c = stack_entries(n_max, F) + 2 * (size_t)n_max + 2 * (size_t)(n_max + 1) * (n_max + 1) + n_max + 1;
+    size_t bytes = c * sizeof(cx<R>);
+    bytes = (bytes + 15) & ~(size_t)15;
+    bytes += (32 * (size_t)(n_max + 1) + 32) * sizeof(double);
+    return (bytes + 127) & ~(size_t)127;
+}
+
+template <class R>
+__device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int F) {
+    WarpSmem<R> w;
+    cx<R> *p = reinterpret_cast<cx<R> *>(base);
+    w.stack = p;
+    p += stack_entries(n_max, F);
+    w.wrow = p;
+    p += 2 * n_max;
+    w.P = p;
+    p += (n_max + 1) * (n_max + 1);
+    w.Rr = p;
+    p += (n_max + 1) * (n_max + 1);
+    w.detD = p;
+    p += n_max + 1;
+    size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
+    w.upt = reinterpret_cast<double *>(base + off);
+    w.wpt = w.upt + 32 * (n_max + 1);
+    return w;
+}
+
+// Generalised Keldysh entry between global vertices v (row) and w (column),
+// 0 = measurement point (row: (t, a=0); column: (t, a=1)).
+template <class R>
+__device__ __forceinline__ cx<R> G(const WarpSmem<R> &ws, int NP, cx<R> d, int v, int av, int w, int aw) {
+    if (v == w) return d;
+    if (v < w) return aw ? ws.Rr[v * NP + w] : ws.P[v * NP + w];
+    return av ? nconj(ws.P[w * NP + v]) : nconj(ws.Rr[w * NP + v]);
+}
+
+// Flat phase: one lane per choice path of the F remaining vertices of the tree
+// leaf matrix E (size S = 2F + 2).  The first elimination is fused with the
+// gather; the rest runs on an (F+1) x (F+1) register matrix whose rows and
+// columns are {copy a_1 = 0, copy a_1 = 1, remaining vertices}.
+template <class R, int F>
+__device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parity, int lane, Acc<R> &acc_re,
+                                           Acc<R> &acc_im) {
+    constexpr int S = 2 * F + 2;
+    if (lane >= (1 << F)) return;
+    if (F == 0) {
+        cx<R> dd = cmul(detD, detD);
+        cx<R> diff = mk<R>(E[0].re - E[S + 1].re, E[0].im - E[S + 1].im);
+        cx<R> term = cmul(dd, diff);
+        if (parity) term = mk<R>(-term.re, -term.im);
+        acc_re.add(term.re);
+        acc_im.add(term.im);
+        return;
+    }
+    constexpr int M = F + 1;  // after the first elimination: 2 copies + F-1 vertices
+    int idx[M];
+    idx[0] = 0;
+    idx[1] = 1;
+#pragma unroll
+    for (int q = 1; q < F; ++q) idx[q + 1] = 2 + 2 * q + ((lane >> q) & 1);
+    const int p0 = 2 + (lane & 1);
+    cx<R> piv = E[p0 * S + p0];
+    detD = cmul(detD, piv);
+    cx<R> ip = crcp(piv);
+    cx<R> m[M][M];
+    cx<R> prow[M];
+#pragma unroll
+    for (int y = 0; y < M; ++y) prow[y] = cmul(E[p0 * S + idx[y]], ip);
+#pragma unroll
+    for (int x = 0; x < M; ++x) {
+        cx<R> cf = E[idx[x] * S + p0];
+#pragma unroll
+        for (int y = 0; y < M; ++y) {
+            if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
+            m[x][y] = cfms(E[idx[x] * S + idx[y]], cf, prow[y]);
+        }
+    }
+#pragma unroll
+    for (int q = 1; q < F; ++q) {
+        const int p = q + 1;
+        cx<R> pv = m[p][p];
+        detD = cmul(detD, pv);
+        cx<R> iq = crcp(pv);
+#pragma unroll
+        for (int y = 0; y < M; ++y)
+            if (y < 2 || y > p) m[p][y] = cmul(m[p][y], iq);
+#pragma unroll
+        for (int x = 0; x < M; ++x) {
+            if (!(x < 2 || x > p)) continue;
+#pragma unroll
+            for (int y = 0; y < M; ++y) {
+                if (!(y < 2 || y > p)) continue;
+                if (x < 2 && y < 2 && x != y) continue;
+                m[x][y] = cfms(m[x][y], m[x][p], m[p][y]);
+            }
+        }
+    }
+    cx<R> dd = cmul(detD, detD);
+    cx<R> diff = mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im);
+    cx<R> term = cmul(dd, diff);
+    parity ^= __popc(lane) & 1;
+    if (parity) term = mk<R>(-term.re, -term.im);
+    acc_re.add(term.re);
+    acc_im.add(term.im);
+}
+
+template <class R, int F>
+__device__ __forceinline__ void flat_dispatch(int Rleaf, const cx<R> *E, cx<R> detD, int parity, int lane,
+                                              Acc<R> &ar, Acc<R> &ai) {
+    // Rleaf <= F
+    switch (Rleaf) {
+        case 0: flat_phase<R, 0>(E, detD, parity, lane, ar, ai); break;
+        case 1: flat_phase<R, 1>(E, detD, parity, lane, ar, ai); break;
+        case 2: flat_phase<R, 2>(E, detD, parity, lane, ar, ai); break;
+        case 3: flat_phase<R, 3>(E, detD, parity, lane, ar, ai); break;
+        case 4: if (F >= 4) flat_phase<R, (F >= 4 ? 4 : 0)>(E, detD, parity, lane, ar, ai); break;
+        default: if (F >= 5) flat_phase<R, (F >= 5 ? 5 : 0)>(E, detD, parity, lane, ar, ai); break;
+    }
+}
+
+// Keldysh sum for one point whose times are in ws.upt[src] (u_0 = t first).
+// Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
+// i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
+template <class R, int F>
+__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d,
+                                  const typename TabT<R>::V *tab, double T, double h, int L, int lane) {
+    const int NP = n_max + 1;
+    // 1. pair interpolation, 0 <= j < k <= n
+    const int npairs = n * (n + 1) / 2;
+    for (int p = lane; p < npairs; p += 32) {
+        int k = (int)((1.0 + sqrt(8.0 * p + 1.0)) * 0.5);
+        while (k * (k - 1) / 2 > p) --k;
+        while ((k + 1) * k / 2 <= p) ++k;
+        int j = p - k * (k - 1) / 2;
+        cx<R> gl, gg;
+        interp_pair<R>(tab, T, h, L, u[j] - u[k], gl, gg);
+        ws.P[j * NP + k] = gg;
+        ws.Rr[j * NP + k] = gl;
+    }
+    __syncwarp();
+    // 2. level 0: vertex 1 eliminated (both a_1 kept in the two measurement copies)
+    const int R0 = n - 1;
+    const int S0 = 2 * R0 + 2;
+    const cx<R> id = crcp(d);
+    for (int e = lane; e < S0 * S0; e += 32) {
+        int r = e / S0, c = e - r * S0;
+        int vr, ar, vc, ac, er, ec;
+        if (r < 2) { vr = 0; ar = 0; er = r; } else { vr = 2 + ((r - 2) >> 1); ar = (r - 2) & 1; er = 0; }
+        if (c < 2) { vc = 0; ac = 1; ec = c; } else { vc = 2 + ((c - 2) >> 1); ac = (c - 2) & 1; ec = 0; }
+        cx<R> base = G<R>(ws, NP, d, vr, ar, vc, ac);
+        cx<R> left = G<R>(ws, NP, d, vr, ar, 1, er);
+        cx<R> right = cmul(G<R>(ws, NP, d, 1, ec, vc, ac), id);
+        ws.stack[e] = cfms(base, left, right);
+    }
+    if (lane == 0) ws.detD[0] = d;
+    __syncwarp();
+    // 3. tree over a_2 .. a_{levels+1}, flat phase on the remaining vertices
+    const int levels = R0 > F ? R0 - F : 0;
+    const int Rleaf = R0 - levels;
+    // offsets of each level
+    int off[kMaxOrder];
+    {
+        int o = 0;
+        for (int l = 0; l <= levels; ++l) {
+            off[l] = o;
+            int S = 2 * (R0 - l) + 2;
+            o += S * S;
+        }
+    }
+    Acc<R> ar, ai;
+    ar.init();
+    ai.init();
+    const int nleaf = 1 << levels;
+    for (int b = 0; b < nleaf; ++b) {
+        int from = (b == 0) ? 0 : levels - (__ffs(b) - 1) - 1;
+        for (int l = from; l < levels; ++l) {
+            const int a = (b >> (levels - 1 - l)) & 1;
+            const int S = 2 * (R0 - l) + 2;
+            const int S2 = S - 2;
+            const cx<R> *E = ws.stack + off[l];
+            cx<R> *E2 = ws.stack + off[l + 1];
+            const int pr = 2 + a;
+            cx<R> piv = E[pr * S + pr];
+            cx<R> ip = crcp(piv);
+            for (int c2 = lane; c2 < S2; c2 += 32) {
+                int c = c2 < 2 ? c2 : c2 + 2;
+                ws.wrow[c2] = cmul(E[pr * S + c], ip);
+            }
+            if (lane == 0) ws.detD[l + 1] = cmul(ws.detD[l], piv);
+            __syncwarp();
+            for (int e = lane; e < S2 * S2; e += 32) {
+                int r2 = e / S2, c2 = e - r2 * S2;
+                int r = r2 < 2 ? r2 : r2 + 2;
+                int c = c2 < 2 ? c2 : c2 + 2;
+                E2[e] = cfms(E[r * S + c], E[r * S + pr], ws.wrow[c2]);
+            }
+            __syncwarp();
+        }
+        const int parity = __popc(b) & 1;
+        flat_dispatch<R, F>(Rleaf, ws.stack + off[levels], ws.detD[levels], parity, lane, ar, ai);
+        __syncwarp();
+    }
+    double sr = (double)ar.s, cr = (double)ar.c, si = (double)ai.s, ci = (double)ai.c;
+    warp_reduce_pair(sr, cr);
+    warp_reduce_pair(si, ci);
+    return mk<double>(sr + cr, si + ci);
+}
+
+// i^n * z
+__device__ __forceinline__ cx<double> times_i_pow(cx<double> z, int n) {
+    switch (n & 3) {
+        case 0: return z;
+        case 1: return mk<double>(-z.im, z.re);
+        case 2: return mk<double>(-z.re, -z.im);
+        default: return mk<double>(z.im, -z.re);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ const typename TabT<R>::V *item_table(const ItemDev &it);
+template <>
+__device__ __forceinline__ const dbl4 *item_table<double>(const ItemDev &it) { return it.table; }
+template <>
+__device__ __forceinline__ const float4 *item_table<float>(const ItemDev &it) { return it.table32; }
+
+// ----------------------------------------------------------------------------
+// Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
+// ----------------------------------------------------------------------------
+template <class R, int F>
+__global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
+                              unsigned long long *counter, int n_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, F), n_max, F);
+    const int NU = n_max + 1;
+    while (true) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(counter, 1ull);
+        c = __shfl_sync(FULL, c, 0);
+        if ((long long)c >= total_chunks) break;
+        int it = 0;
+        while (it + 1 < n_items && items[it + 1].chunk_begin <= (long long)c) ++it;
+        const ItemDev &I = items[it];
+        const int n = I.order;
+        const long long local = (long long)c - I.chunk_begin;
+        const int k = (int)(local / I.chunks_per_shift);
+        const long long blk = local - (long long)k * I.chunks_per_shift;
+        const long long idx = blk * kChunk + lane;
+        const bool valid = idx < I.n_points;
+        // point generation and warp (FP64; Sobol' integers are exact)
+        bool inside = false;
+        double w = 0.0;
+        if (valid) {
+            const uint64_t i = (uint64_t)(I.first_index + idx);
+            double uprev = I.t, prod = 1.0;
+            ws.upt[lane * NU] = I.t;
+            for (int m = 0; m < n; ++m) {
+                uint32_t y = sobol_word(m, i) ^ I.shifts[k * n + m];
+                double x = (double)y * 0x1p-32;
+                double v = -I.tau * log1p(-x);
+                uprev = uprev - v;
+                ws.upt[lane * NU + 1 + m] = uprev;
+                prod *= (1.0 - x);
+            }
+            inside = uprev > 0.0;
+            w = pow(I.tau, (double)n) / prod;
+        }
+        ws.wpt[lane] = w;
+        unsigned mask = __ballot_sync(FULL, inside);
+        __syncwarp();
+        cx<double> myval = mk<double>(0.0, 0.0);
+        const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
+        const typename TabT<R>::V *tab = item_table<R>(I);
+        unsigned mm = mask;
+        while (mm) {
+            const int src = __ffs(mm) - 1;
+            mm &= mm - 1;
+            cx<double> s = keldysh_sum<R, F>(ws, ws.upt + src * NU, n, n_max, d, tab, I.T, I.h, I.L, lane);
+            if (lane == src) {
+                cx<double> cval = times_i_pow(s, n);
+                myval = mk<double>(w * cval.re, w * cval.im);
+            }
+            __syncwarp();
+        }
+        double sr = myval.re, cr = 0.0, si = myval.im, ci = 0.0;
+        warp_reduce_pair(sr, cr);
+        warp_reduce_pair(si, ci);
+        if (lane == 0) {
+            double *pp = I.partials + 4 * (size_t)local;
+            pp[0] = sr;
+            pp[1] = si;
+            pp[2] = cr;
+            pp[3] = ci;
+            I.inside[local] = __popc(mask);
+        }
+    }
+}
+
+// Per shifted sequence: compensated sum of its chunk partials in a fixed order.
+// out[2*g], out[2*g+1] = sum_i w_i c_n(u_i) (complex, not divided by N);
+// counts[g] = in-domain points.  One block of 256 threads per sequence.
+__global__ void reduce_kernel(const ItemDev *__restrict__ items, int n_items, double *out,
+                              unsigned long long *counts) {
+    __shared__ double s_re[256], c_re[256], s_im[256], c_im[256];
+    __shared__ unsigned long long cnt[256];
+    int g = blockIdx.x;
+    int it = 0, base = 0;
+    while (it < n_items && g >= base + items[it].n_shifts) {
+        base += items[it].n_shifts;
+        ++it;
+    }
+    if (it >= n_items) return;
+    const ItemDev &I = items[it];
+    const int k = g - base;
+    const double *pp = I.partials + 4 * (size_t)k * I.chunks_per_shift;
+    const unsigned int *ins = I.inside + (size_t)k * I.chunks_per_shift;
+    Acc<double> ar, ai;
+    ar.init();
+    ai.init();
+    unsigned long long cn = 0;
+    for (int q = threadIdx.x; q < I.chunks_per_shift; q += blockDim.x) {
+        ar.add(pp[4 * q]);
+        ar.add(pp[4 * q + 2]);
+        ai.add(pp[4 * q + 1]);
+        ai.add(pp[4 * q + 3]);
+        cn += ins[q];
+    }
+    s_re[threadIdx.x] = ar.s;
+    c_re[threadIdx.x] = ar.c;
+    s_im[threadIdx.x] = ai.s;
+    c_im[threadIdx.x] = ai.c;
+    cnt[threadIdx.x] = cn;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            double t, e;
+            two_sum(s_re[threadIdx.x], s_re[threadIdx.x + o], t, e);
+            s_re[threadIdx.x] = t;
+            c_re[threadIdx.x] = c_re[threadIdx.x] + c_re[threadIdx.x + o] + e;
+            two_sum(s_im[threadIdx.x], s_im[threadIdx.x + o], t, e);
+            s_im[threadIdx.x] = t;
+            c_im[threadIdx.x] = c_im[threadIdx.x] + c_im[threadIdx.x + o] + e;
+            cnt[threadIdx.x] += cnt[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * g] = s_re[0] + c_re[0];
+        out[2 * g + 1] = s_im[0] + c_im[0];
+        counts[g] = cnt[0];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Check kernels
+// ----------------------------------------------------------------------------
+__global__ void sobol_kernel(int order, uint64_t first, uint64_t count, const uint32_t *shift, uint32_t *out) {
+    uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    for (int m = 0; m < order; ++m) out[q * order + m] = sobol_word(m, first + q) ^ (shift ? shift[m] : 0u);
+}
+
+__global__ void warp_kernel(int order, uint64_t first, uint64_t count, const uint32_t *shift, double t, double tau,
+                            double *u, double *w, int32_t *inside) {
+    uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    double uprev = t, prod = 1.0;
+    for (int m = 0; m < order; ++m) {
+        uint32_t y = sobol_word(m, first + q) ^ (shift ? shift[m] : 0u);
+        double x = (double)y * 0x1p-32;
+        uprev = uprev - (-tau * log1p(-x));
+        u[q * order + m] = uprev;
+        prod *= (1.0 - x);
+    }
+    w[q] = pow(tau, (double)order) / prod;
+    inside[q] = uprev > 0.0;
+}
+
+// One warp per caller point.
+template <class R, int F>
+__global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, double *out, int n_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, F), n_max, F);
+    const int n = I.order;
+    const int NU = n_max + 1;
+    uint64_t q = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
+    if (q >= count) return;
+    if (lane == 0) {
+        ws.upt[0] = I.t;
+        for (int m = 0; m < n; ++m) ws.upt[1 + m] = u[q * n + m];
+    }
+    __syncwarp();
+    const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
+    cx<double> s = keldysh_sum<R, F>(ws, ws.upt, n, n_max, d, item_table<R>(I), I.T, I.h, I.L, lane);
+    if (lane == 0) {
+        cx<double> cval = times_i_pow(s, n);
+        out[2 * q] = cval.re;
+        out[2 * q + 1] = cval.im;
+    }
+    (void)NU;
+}
+
+// ----------------------------------------------------------------------------
+// Green-function table: contour-deformed Fourier integral (App. E).
+//   g^<(tau) = (i/2pi) Int_{-inf}^{0} e^{-i w tau} A(w) dw,   A(w) = 2 Gamma / ((w-eps)^2 + Gamma^2)
+// For tau > 0 the half line (-inf, w_m] is replaced by the vertical ray
+// w = w_m - i y, y in [0, inf) (no pole crossed for w_m < eps), on which the
+// exponential decays without oscillating; the rest [w_m, 0] stays on the real
+// axis.  Ray: exp-sinh rule y = exp(pi/2 sinh s); segment: composite 16-point
+// Gauss-Legendre.  g^> = g^< - i exp(-i eps tau - Gamma tau) (sum rule).
+// One warp per node with tau > 0; the node at -h/2 is the mirror image.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ cx<double> lorentz(cx<double> z, double eps, double gam) {
+    // 2 gam / ((z - eps)^2 + gam^2)
+    cx<double> q = mk<double>(z.re - eps, z.im);
+    cx<double> den = mk<double>(q.re * q.re - q.im * q.im + gam * gam, 2.0 * q.re * q.im);
+    cx<double> r = crcp(den);
+    return mk<double>(2.0 * gam * r.re, 2.0 * gam * r.im);
+}
+
+__global__ void gf_table_kernel(dbl4 *tab, float4 *tab32, int L, double T, double h, double eps, double gam,
+                                int panels) {
+    const int lane = threadIdx.x & 31;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // 0 .. L/2-1 -> node L/2 + q
+    if (q >= L / 2) return;
+    const int node = L / 2 + q;
+    const double tau = -T + (double)node * h;
+    const double wm = fmin(eps, 0.0) - 3.0 * gam;
+    double ar = 0.0, ai = 0.0;  // integral of e^{-i w tau} A(w) dw along the contour
+    // ray: Int = i Int_0^inf e^{-i wm tau} e^{-y tau} A(wm - i y) dy
+    {
+        const double hs = 1.0 / 32.0;
+        const int ns = 289;  // s in [-4.5, 4.5]
+        double rr = 0.0, ri = 0.0;
+        for (int j = lane; j < ns; j += 32) {
+            double s = -4.5 + hs * j;
+            double y = exp(1.5707963267948966 * sinh(s));
+            double dy = y * 1.5707963267948966 * cosh(s);
+            double e = exp(-y * tau) * dy;
+            cx<double> a = lorentz(mk<double>(wm, -y), eps, gam);
+            rr += e * a.re;
+            ri += e * a.im;
+        }
+        rr *= hs;
+        ri *= hs;
+        // multiply by i e^{-i wm tau}
+        double sn, cs;
+        sincos(wm * tau, &sn, &cs);
+        cx<double> ph = mk<double>(sn, cs);  // i * (cos - i sin) = sin + i cos
+        cx<double> v = cmul(ph, mk<double>(rr, ri));
+        ar += v.re;
+        ai += v.im;
+    }
+    // segment [wm, 0]
+    {
+        const double len = -wm;
+        const double pw = len / panels;
+        for (int j = lane; j < panels * 16; j += 32) {
+            int pnl = j >> 4, g = j & 15;
+            double w = wm + pw * (pnl + 0.5 * (c_gl_x[g] + 1.0));
+            double wt = 0.5 * pw * c_gl_w[g];
+            double sn, cs;
+            sincos(w * tau, &sn, &cs);
+            cx<double> a = lorentz(mk<double>(w, 0.0), eps, gam);
+            // e^{-i w tau} A = (cs - i sn) * a.re (A real on the axis)
+            ar += wt * cs * a.re;
+            ai -= wt * sn * a.re;
+        }
+    }
+    // warp sum
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(FULL, ar, o);
+        ai += __shfl_xor_sync(FULL, ai, o);
+    }
+    if (lane == 0) {
+        const double inv2pi = 0.15915494309189535;
+        // g^< = (i / 2pi) (ar + i ai) = (-ai + i ar) / 2pi
+        double glr = -ai * inv2pi, gli = ar * inv2pi;
+        double sn, cs;
+        sincos(eps * tau, &sn, &cs);
+        double dec = exp(-gam * tau);
+        // -i e^{-i eps tau} e^{-gam tau} = -i (cs - i sn) dec = (-sn - i cs) dec
+        double ggr = glr - sn * dec, ggi = gli - cs * dec;
+        tab[q + 1] = make_double4_32a(glr, gli, ggr, ggi);
+        tab32[q + 1] = make_float4((float)glr, (float)gli, (float)ggr, (float)ggi);
+        if (q == 0) {  // node at -h/2: g(-tau) = -conj g(tau)
+            tab[0] = make_double4_32a(-glr, gli, -ggr, ggi);
+            tab32[0] = make_float4((float)-glr, (float)gli, (float)-ggr, (float)ggi);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host launchers
+// ----------------------------------------------------------------------------
+static void gauss_legendre16(double *x, double *w) {
+    const int n = 16;
+    for (int i = 0; i < n; ++i) {
+        long double z = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (n + 0.5L));
+        long double pp = 0;
+        for (int it = 0; it < 100; ++it) {
+            long double p1 = 1, p2 = 0;
+            for (int j = 1; j <= n; ++j) {
+                long double p3 = p2;
+                p2 = p1;
+                p1 = ((2 * j - 1) * z * p2 - (j - 1) * p3) / j;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1);
+            long double z1 = z;
+            z = z1 - p1 / pp;
+            if (fabsl(z - z1) < 1e-19L) break;
+        }
+        x[i] = (double)z;
+        w[i] = (double)(2.0L / ((1 - z * z) * pp * pp));
+    }
+}
+
+int upload_direction_numbers() {
+    uint32_t dirs[kMaxOrder * 32];
+    direction_numbers(kMaxOrder, dirs);
+    cudaError_t e = cudaMemcpyToSymbol(c_dirs, dirs, sizeof(dirs));
+    if (e != cudaSuccess) return cuda_error(e, "upload direction numbers");
+    double gx[16], gw[16];
+    gauss_legendre16(gx, gw);
+    e = cudaMemcpyToSymbol(c_gl_x, gx, sizeof(gx));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gl_w, gw, sizeof(gw));
+    if (e != cudaSuccess) return cuda_error(e, "upload quadrature rule");
+    return QQMC_OK;
+}
+
+int launch_gf_table(const Problem &pr, cudaStream_t s) {
+    const qqmc_params &p = pr.params;
+    double wm = fmin(p.eps_d, 0.0) - 3.0 * p.gamma;
+    int panels = 64 + (int)ceil(-wm * (p.t_max + 4.0 / p.gamma));
+    if (panels > 8192) panels = 8192;
+    int warps = pr.L / 2;
+    int threads = 128;
+    int blocks = (warps * 32 + threads - 1) / threads;
+    gf_table_kernel<<<blocks, threads, 0, s>>>(pr.d_table, pr.d_table32, pr.L, p.t_max, pr.h, p.eps_d, p.gamma,
+                                               panels);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "gf_table_kernel launch");
+    return QQMC_OK;
+}
+
+size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
+    size_t per = precision == QQMC_PREC_FP64 ? warp_smem_bytes<double>(n_max, tune.flat)
+                                             : warp_smem_bytes<float>(n_max, tune.flat);
+    return per * tune.warps_per_block;
+}
+
+template <class R, int F>
+static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
+                                   unsigned long long *d_counter, int n_max, int wpb, cudaStream_t s) {
+    size_t smem = warp_smem_bytes<R>(n_max, F) * wpb;
+    cudaError_t e = cudaFuncSetAttribute(detsum_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, detsum_kernel<R, F>, wpb * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long want = (total_chunks + wpb - 1) / wpb;
+    long long grid = (long long)sms * per_sm;
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    detsum_kernel<R, F><<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
+                          int n_max, int precision, const Tuning &tune, cudaStream_t s) {
+    const int wpb = tune.warps_per_block;
+    if (precision == QQMC_PREC_FP64) {
+        switch (tune.flat) {
+            case 3: return launch_detsum_t<double, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+            case 4: return launch_detsum_t<double, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+            default: return launch_detsum_t<double, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+        }
+    }
+    switch (tune.flat) {
+        case 3: return launch_detsum_t<float, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+        case 4: return launch_detsum_t<float, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+        default: return launch_detsum_t<float, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+    }
+}
+
+cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out,
+                          unsigned long long *d_counts, cudaStream_t s) {
+    reduce_kernel<<<total_shifts, 256, 0, s>>>(d_items, n_items, d_out, d_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sobol(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, uint32_t *d_out,
+                         cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((count + 255) / 256);
+    sobol_kernel<<<blocks, 256, 0, s>>>(order, first, count, d_shift, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, double t, double tau,
+                        double *d_u, double *d_w, int32_t *d_inside, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((count + 255) / 256);
+    warp_kernel<<<blocks, 256, 0, s>>>(order, first, count, d_shift, t, tau, d_u, d_w, d_inside);
+    return cudaGetLastError();
+}
+
+template <class R, int F>
+static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
+                                      cudaStream_t s) {
+    const int wpb = 2;
+    size_t smem = warp_smem_bytes<R>(item.order, F) * wpb;
+    cudaError_t e =
+        cudaFuncSetAttribute(integrand_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    unsigned blocks = (unsigned)((count + wpb - 1) / wpb);
+    integrand_kernel<R, F><<<blocks, wpb * 32, smem, s>>>(item, count, d_u, d_out, item.order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
+                             const Tuning &tune, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    if (precision == QQMC_PREC_FP64) {
+        switch (tune.flat) {
+            case 3: return launch_integrand_t<double, 3>(item, count, d_u, d_out, s);
+            case 4: return launch_integrand_t<double, 4>(item, count, d_u, d_out, s);
+            default: return launch_integrand_t<double, 5>(item, count, d_u, d_out, s);
+        }
+    }
+    switch (tune.flat) {
+        case 3: return launch_integrand_t<float, 3>(item, count, d_u, d_out, s);
+        case 4: return launch_integrand_t<float, 4>(item, count, d_u, d_out, s);
+        default: return launch_integrand_t<float, 5>(item, count, d_u, d_out, s);
+    }
+}
+
+}  // namespace qqmc

@@ -1,0 +1,73 @@
+// Internal declarations shared by the QQMC library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/qqmc.h"
+
+namespace qqmc {
+
+using dbl4 = double4_32a;  // 32-byte aligned: one 256-bit load per table node
+
+constexpr int kMaxOrder = QQMC_MAX_ORDER;
+constexpr int kChunk = 32;  // Sobol' indices per work chunk (one per lane)
+
+// Device-resident problem: half table of (g^<, g^>) on the nodes with tau >= -h/2.
+struct Problem {
+    qqmc_params params;
+    int L = 0;
+    double h = 0;        // node spacing 2 t_max / (L - 1)
+    double g0_re = 0, g0_im = 0;
+    dbl4 *d_table = nullptr;  // [L/2 + 1]: (gl.re, gl.im, gg.re, gg.im) at nodes k = L/2-1 .. L-1
+    float4 *d_table32 = nullptr; // same, FP32 (mixed precision)
+    int device = 0;
+};
+
+// One item as the device sees it.
+struct ItemDev {
+    const dbl4 *table;
+    const float4 *table32;
+    const uint32_t *shifts;  // [n_shifts][order]
+    double *partials;        // [n_shifts * chunks_per_shift][4]: sum.re, sum.im, comp.re, comp.im
+    unsigned int *inside;    // [n_shifts * chunks_per_shift]: in-domain count per chunk
+    double g0_re, g0_im, t, tau, T, h;
+    long long first_index;
+    long long n_points;
+    long long chunk_begin;   // first global chunk of this item
+    int order, n_shifts, L, chunks_per_shift;
+};
+
+struct Tuning {
+    int warps_per_block;
+    int flat;
+};
+
+// Error reporting (thread-local message).
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+
+// Host-side generators (product side).
+void direction_numbers(int n_dims, uint32_t *out);  // [n_dims][32]
+uint64_t splitmix64(uint64_t x);
+void shift_words(uint64_t seed, int n_shifts, int n_dims, uint32_t *out);
+
+// Kernel launchers (kernels.cu).
+int upload_direction_numbers();
+int launch_gf_table(const Problem &pr, cudaStream_t s);
+cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
+                          int n_max, int precision, const Tuning &tune, cudaStream_t s);
+cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out, unsigned long long *d_counts,
+                          cudaStream_t s);
+size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune);
+cudaError_t launch_sobol(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, uint32_t *d_out,
+                         cudaStream_t s);
+cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, double t, double tau,
+                        double *d_u, double *d_w, int32_t *d_inside, cudaStream_t s);
+cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
+                             const Tuning &tune, cudaStream_t s);
+Tuning get_tuning(int precision, int order);
+
+}  // namespace qqmc

@@ -1,0 +1,65 @@
+"""Work accounting for the roofline of the determinant kernel.
+
+``flops_per_point(n, F)`` counts the real floating-point operations the
+kernel executes for one in-domain point of order n (complex FMA c - a*b = 8,
+complex product = 6, complex reciprocal = 6, the two-sum accumulation of a
+leaf term = 8), following the kernel's loops exactly: level 0 (vertex 1
+eliminated), the depth-first Schur tree over a_2.., and the per-lane flat
+phase over the last F vertices.  ``w_naive`` is the cost of the plain form
+(one LU per Keldysh configuration of M_up and of M_down), for an
+algorithm-independent "effective" rate.
+
+Peaks of the GB300 CUDA cores (the path is not a dense contraction and does
+not use tensor cores): 152 SMs at up to 2070 MHz; per SM and clock 128 FP32
+FMA lanes and 2 FP64 FMA lanes (the FP64 rate measured by an FMA-chain
+microbenchmark on this part, 1.20 TFLOP/s at ~1.97 GHz, fixes the latter).
+"""
+from __future__ import annotations
+
+SMS = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES = 128
+FP64_LANES = 2
+
+
+def peak_tflops(precision: str, mhz: float = SM_MAX_MHZ) -> float:
+    lanes = FP64_LANES if precision == "fp64" else FP32_LANES
+    return SMS * lanes * 2.0 * mhz * 1e6 / 1e12
+
+
+CFMS, CMUL, CRCP, ACC = 8, 6, 6, 8
+
+
+def flops_per_point(n: int, F: int = 5) -> float:
+    R0 = n - 1
+    S0 = 2 * n
+    fl = 0.0
+    # pair interpolation: 2 complex lerps (8 fma-equivalent ops) + index arithmetic
+    fl += (n * (n + 1) // 2) * 12
+    # level 0: cmul (right * 1/d) + cfms per entry, one reciprocal
+    fl += S0 * S0 * (CMUL + CFMS) + CRCP
+    levels = R0 - F if R0 > F else 0
+    Rleaf = R0 - levels
+    # tree transitions: level l -> l+1 computed 2^(l+1) times in the walk
+    for l in range(levels):
+        S2 = 2 * (R0 - l)
+        fl += 2 ** (l + 1) * (S2 * CMUL + S2 * S2 * CFMS + CRCP + CMUL)
+    # flat phase: 2^levels tree leaves x 2^Rleaf lanes
+    per_lane = 0.0
+    if Rleaf == 0:
+        per_lane = 2 * CMUL + 2 + ACC
+    else:
+        M = Rleaf + 1
+        per_lane += CRCP + CMUL + M * CMUL + (M * M - 2) * CFMS
+        for q in range(1, Rleaf):
+            p = q + 1
+            rows = 2 + (M - 1 - p)
+            per_lane += CRCP + CMUL + rows * CMUL + (rows * rows - 2) * CFMS
+        per_lane += 2 * CMUL + 2 + ACC
+    fl += 2 ** levels * 2 ** Rleaf * per_lane
+    return fl
+
+
+def w_naive(n: int) -> float:
+    """2^n (8/3)(n^3 + (n+1)^3): one LU of M_down (n x n) and of M_up per configuration."""
+    return 2.0 ** n * (8.0 / 3.0) * (n ** 3 + (n + 1) ** 3)

@@ -1,0 +1,191 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Inputs are seeded and shared byte for byte (``workloads``): synthetic
+Keldysh tables, shift words, vertex times.  Bars:
+  * integers (Sobol' words, in-domain counts): bit-exact;
+  * FP64 integrand per point: |c_gpu - c_oracle| <= 1e-12 * sum_a |term_a|
+    (the oracle's own scale of the Keldysh sum: both sides round at ~1e-16
+    relative to the largest terms, times the O(2^n) additions);
+  * FP64 coefficients per shift: relative 1e-10 (the stated target);
+  * mixed precision: the bound stated in each test.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2002_12372_gb300 import build as b
+    b.build()
+    from paper_2002_12372_gb300 import qqmc
+    qqmc.load()
+    return qqmc
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2002_12372_gb300 import workloads
+    return workloads
+
+
+def _problem(Q, W, seed=7, T=10.0, L=4096, tau=1.0):
+    gl, gg, g0, _ = W.synthetic_tables(seed, L, T)
+    p = Q.make_params(t_max=T, tau=tau, n_table=L)
+    return Q.qqmc_create_problem_tables(p, gl, gg, g0), (gl, gg, g0)
+
+
+# ------------------------------------------------------------------ points ---
+
+@pytest.mark.parametrize("order", [1, 3, 7, 12])
+def test_sobol_points_bit_exact(Q, W, oracle, order):
+    V = oracle.sobol_direction_numbers(12)
+    sh = W.shift_words(3, 1, order)[0]
+    for first, count in [(0, 4096), (2 ** 20 - 5, 77), (3_000_001, 33)]:
+        gpu = Q.qqmc_sobol_points(order, first, count, sh)
+        ref = oracle.sobol_points(order, first, count, V) ^ sh[None, :order]
+        assert np.array_equal(gpu, ref)
+
+
+@pytest.mark.parametrize("order,tau,t", [(1, 1.0, 10.0), (4, 0.95, 10.0), (10, 1.0, 10.0), (12, 1.5, 5.0)])
+def test_warp_points_match_oracle(Q, W, oracle, order, tau, t):
+    pr, _ = _problem(Q, W, T=t, tau=tau)
+    try:
+        sh = W.shift_words(5, 1, order)[0]
+        u, w, ins = Q.qqmc_warp_points(pr, order, 1000, 20000, sh)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    V = oracle.sobol_direction_numbers(12)
+    u0, w0, ins0 = oracle.warp(order, 1000, 20000, V, sh, t, tau)
+    assert np.array_equal(ins, ins0)
+    assert np.max(np.abs(u - u0)) <= 1e-13 * t
+    assert np.max(np.abs(w / w0 - 1.0)) < 1e-13
+
+
+# -------------------------------------------------------------- integrand ---
+
+@pytest.mark.parametrize("order,count", [(1, 64), (2, 64), (3, 64), (5, 48), (6, 32), (8, 16), (10, 6), (12, 2)])
+def test_integrand_fp64_matches_oracle(Q, W, oracle, order, count):
+    T = 10.0
+    pr, tabs = _problem(Q, W, seed=100 + order, T=T)
+    try:
+        u = W.ordered_times(200 + order, count, order, T)
+        gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    ref, scale = oracle.integrand(order, u, T, tabs, T, return_abs=True)
+    assert np.all(np.abs(gpu - ref) <= 1e-12 * scale), np.max(np.abs(gpu - ref) / scale)
+
+
+@pytest.mark.parametrize("order,count", [(2, 64), (5, 32), (8, 12), (10, 6)])
+def test_integrand_mixed_within_fp32_bound(Q, W, oracle, order, count):
+    """FP32 Schur updates: deviation bounded by 2^-20 (~1e-6) of the Keldysh-sum scale."""
+    T = 10.0
+    pr, tabs = _problem(Q, W, seed=300 + order, T=T)
+    try:
+        u = W.ordered_times(400 + order, count, order, T)
+        gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_MIXED)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    ref, scale = oracle.integrand(order, u, T, tabs, T, return_abs=True)
+    assert np.all(np.abs(gpu - ref) <= 2.0 ** -20 * scale), np.max(np.abs(gpu - ref) / scale)
+
+
+# ------------------------------------------------------------- integration ---
+
+@pytest.mark.parametrize("order,N,K", [(1, 4096, 4), (2, 1000, 3), (3, 2049, 3), (4, 4096, 2), (6, 517, 2),
+                                       (8, 97, 2), (1, 1, 1), (2, 31, 2), (3, 33, 2)])
+def test_integration_fp64_matches_oracle(Q, W, oracle, order, N, K):
+    T = 10.0
+    pr, tabs = _problem(Q, W, seed=order, T=T)
+    sw = W.shift_words(1000 + order, K, order)
+    try:
+        res, S = Q.qqmc_integrate(pr, order, N, K, Q.QQMC_PREC_FP64, sw)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    S0, nin = oracle.estimate(order, N, sw, T, 1.0, tabs, T)
+    assert res.n_in_domain == int(nin.sum())
+    rel = np.abs(S - S0) / np.maximum(np.abs(S0), 1e-300)
+    assert np.all(rel < 1e-10), rel
+    q0 = oracle.q_from_sums(S0).real
+    assert res.q_mean == pytest.approx(np.mean(q0), rel=1e-10, abs=1e-14)
+
+
+def test_batched_plan_equals_single_runs(Q, W, oracle):
+    """Uneven orders and point counts in one persistent launch: identical sums."""
+    T = 10.0
+    pr, tabs = _problem(Q, W, seed=21, T=T)
+    try:
+        items = [(pr, n, 2, N, W.shift_words(50 + n, 2, n)) for n, N in [(2, 3000), (5, 700), (3, 1), (7, 64)]]
+        plan = Q.Plan(items, Q.QQMC_PREC_FP64)
+        plan.launch()
+        batched = plan.results()
+        plan.launch(use_graph=True)
+        graphed = plan.results()
+        plan.close()
+        for (pr_, n, K, N, sw), (res, S), (res_g, S_g) in zip(items, batched, graphed):
+            res1, S1 = Q.qqmc_integrate(pr, n, N, K, Q.QQMC_PREC_FP64, sw)
+            assert np.array_equal(S, S1)
+            assert np.array_equal(S_g, S1)
+            assert res.n_in_domain == res1.n_in_domain
+    finally:
+        Q.qqmc_destroy_problem(pr)
+
+
+# ------------------------------------------------------------------ tables ---
+
+@pytest.mark.parametrize("eps,T", [(0.0, 10.0), (-1.0, 10.0), (1.0, 10.0), (2.5, 20.0)])
+def test_gf_table_kernel_matches_oracle(Q, oracle, eps, T):
+    L = 4096
+    p = Q.make_params(eps_d=eps, t_max=T, n_table=L)
+    pr = Q.qqmc_create_problem(p)
+    try:
+        gl, gg, g0 = Q.qqmc_problem_tables(pr, L)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    rl, rg, r0 = oracle.gf_tables(1.0, eps, T, L)
+    assert abs(g0 - r0) < 1e-15
+    assert np.max(np.abs(gl - rl)) < 1e-13
+    assert np.max(np.abs(gg - rg)) < 1e-13
+
+
+# ------------------------------------------------- physics, end to end ---
+
+def test_end_to_end_q_coefficients_match_oracle(Q, W, oracle):
+    """Each side with its own tables (GPU contour quadrature vs oracle E1 closed
+    form, agreeing to ~1e-14): Q_1..Q_4 at Gamma=1, eps_d=0, t=10, N=2^14, K=16."""
+    T, L, K, N = 10.0, 4096, 16, 2 ** 14
+    p = Q.make_params(eps_d=0.0, t_max=T, n_table=L)
+    pr = Q.qqmc_create_problem(p)
+    tabs = oracle.gf_tables(1.0, 0.0, T, L)
+    try:
+        for n in range(1, 5):
+            sw = oracle.shift_words(2002123720, K, n)
+            res, S = Q.qqmc_integrate(pr, n, N, K, Q.QQMC_PREC_FP64, None)
+            S0, nin = oracle.estimate(n, N, sw, T, 1.0, tabs, T)
+            assert res.n_in_domain == int(nin.sum())
+            assert np.max(np.abs(S - S0) / np.abs(S0)) < 1e-9
+    finally:
+        Q.qqmc_destroy_problem(pr)
+
+
+def test_single_level_flat_occupation_cancels_at_every_order(Q, W, oracle):
+    """One Lorentzian level with a flat occupation is an infinite-temperature
+    state: every interaction correction vanishes, on both sides, to roundoff."""
+    T, L = 10.0, 4096
+    gl, gg, g0, _ = W.synthetic_tables(9, L, T, components=1)
+    p = Q.make_params(t_max=T, n_table=L)
+    pr = Q.qqmc_create_problem_tables(p, gl, gg, g0)
+    try:
+        for n in (1, 2, 5):
+            u = W.ordered_times(n, 16, n, T)
+            c = Q.qqmc_integrand(pr, n, u, Q.QQMC_PREC_FP64)
+            ref, scale = oracle.integrand(n, u, T, (gl, gg, g0), T, return_abs=True)
+            assert np.all(np.abs(c) <= 1e-13 * scale)
+            assert np.all(np.abs(ref) <= 1e-13 * scale)
+    finally:
+        Q.qqmc_destroy_problem(pr)
