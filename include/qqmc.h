@@ -176,6 +176,33 @@ int qqmc_plan_timing(const qqmc_plan *plan, double *kernel_ms, double *total_ms)
 int qqmc_set_tuning(int precision, int order, int warps_per_block, int flat_vertices);
 int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_vertices);
 
+/*
+ * Allocation-free integration (the paper has no counterpart; this is a
+ * deployment convenience).  Same computation as qqmc_integrate, for callers
+ * that cannot allocate device memory where they integrate -- e.g. a host
+ * framework whose own memory pool owns the device, or a real-time loop that
+ * must not enter the driver's allocator.  All scratch (work counter, chunk
+ * partial sums, item descriptor) lives in one 16 MiB static device array
+ * inside the library, which every GPU that loads the library holds until
+ * the process exits; no cudaMalloc/cudaFree or allocating routine is called.
+ *   d_shift_words: DEVICE [n_shifts][order] uint32 (caller-owned);
+ *   d_sums: DEVICE [n_shifts][2] doubles, receives sum_i w_i c_n(u_i) per
+ *           shift, NOT divided by N (Q_n^(k) = -2i d_sums[k] / N);
+ *   d_counts: DEVICE [n_shifts] uint64 in-domain counts, or NULL;
+ *   stream: cudaStream_t or NULL.  The call only enqueues work; the outputs
+ *   are ready when the stream reaches that point.
+ * Limit: n_shifts * ceil(n_points / 32) <= 465792 (E_INVAL beyond).
+ * The first call on a device resolves the array's device address and uploads
+ * the kernels' constant tables; make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind (the
+ * work counter is cleared at the start of each call), so calls whose work
+ * overlaps on the GPU -- on different streams, or from different threads --
+ * race and must be serialised by the caller.
+ */
+int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_t n_points, int n_shifts, int precision,
+                           const uint32_t *d_shift_words, double *d_sums, unsigned long long *d_counts,
+                           void *stream);
+
 /* ---------------------------- inspection calls ---------------------------- */
 
 /* Sobol' direction words of the product generator (Joe-Kuo primitive

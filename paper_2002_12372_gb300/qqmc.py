@@ -39,6 +39,7 @@ EXPORTED = [
     "qqmc_plan_kernel_count", "qqmc_plan_timing", "qqmc_set_tuning", "qqmc_get_tuning", "qqmc_direction_numbers",
     "qqmc_shift_words", "qqmc_sobol_points", "qqmc_warp_points", "qqmc_integrand", "qqmc_server_create",
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
+    "qqmc_integrate_noalloc",
 ]
 
 
@@ -118,6 +119,7 @@ def load(path: str = LIB_PATH):
         "qqmc_cancel": [vp, ctypes.c_uint64],
         "qqmc_server_destroy": [vp],
         "qqmc_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+        "qqmc_integrate_noalloc": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -253,6 +255,17 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def qqmc_integrate_noalloc(pr: int, order: int, n_points: int, n_shifts: int, precision: int,
+                           d_shift_words: int, d_sums: int, d_counts: int = 0, stream: int = 0) -> None:
+    """Allocation-free integration: every pointer is a device address (e.g. a
+    torch tensor's data_ptr()); d_sums receives the per-shift sums not divided
+    by N.  Enqueues on `stream` and returns."""
+    _check(load().qqmc_integrate_noalloc(ctypes.c_void_p(pr), order, n_points, n_shifts, precision,
+                                         ctypes.c_void_p(d_shift_words), ctypes.c_void_p(d_sums),
+                                         ctypes.c_void_p(d_counts or None), ctypes.c_void_p(stream or None)),
+           "qqmc_integrate_noalloc")
 
 
 def qqmc_set_tuning(precision: int, order: int, warps_per_block: int, flat_vertices: int) -> None:
