@@ -75,6 +75,22 @@ def _max_over_ranks(pg, x: float) -> float:
     return float(t.item())
 
 
+def _sum_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate(pg, units: float, seconds: float):
+    """Whole-job throughput of independent replicas: the units every rank
+    processed divided by the slowest rank's time.  Returns (value, max seconds)."""
+    t = _max_over_ranks(pg, seconds)
+    return _sum_over_ranks(pg, units) / t, t
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -149,6 +165,12 @@ def run_ours(args, ws, rank, local, pg):
     _barrier(pg)
     torch.cuda.set_device(local)
     Q.load()
+    tuned = None
+    if args.tuning and os.path.exists(args.tuning):
+        from paper_2002_12372_gb300 import autotune
+        tuned = autotune.load(args.tuning)
+        if tuned:
+            autotune.install(tuned)
     prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
     stream = torch.cuda.Stream()
     problems = [Q.qqmc_create_problem(Q.make_params(GAMMA, e, T_MAX, TAU, L_TABLE, SEED)) for e in EPS]
@@ -196,9 +218,8 @@ def run_ours(args, ws, rank, local, pg):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     dev_s = sum(step_ms) / 1e3
-    dev_s_max = _max_over_ranks(pg, dev_s)
+    value, dev_s_max = aggregate(pg, pts, dev_s)
     k_s = sum(kern_ms) / 1e3
-    value = pts * ws / dev_s_max
     launches = args.steps * plans[0].kernel_count()
 
     # e2e through the public API from host parameters
@@ -222,8 +243,7 @@ def run_ours(args, ws, rank, local, pg):
         h2d += len(res) * 128 + sum(r.n_shifts * r.order * 4 for r, _ in res)
         d2h += sum(r.n_shifts * (16 + 8) for r, _ in res)
     torch.cuda.synchronize()
-    e2e_s = _max_over_ranks(pg, time.perf_counter() - te)
-    e2e_value = e2e_pts * ws / e2e_s
+    e2e_value, e2e_s = aggregate(pg, e2e_pts, time.perf_counter() - te)
 
     peak = perf.peak_tflops(args.precision)
     achieved = flops / k_s / 1e12 if k_s > 0 else None
@@ -237,10 +257,11 @@ def run_ours(args, ws, rank, local, pg):
                    "batch": "30 (eps_d, n) integrations x 2^%d indices x 32 shifts per step" % args.slice_log2,
                    "precision": args.precision, "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "tuning": {"warps_per_block": wpb, "flat_vertices": flat}},
-        "in_domain_evals_per_s": pts_in * ws / dev_s_max,
-        "keldysh_det_evals_per_s": dets * ws / dev_s_max,
-        "naive_equivalent_tflops": naive / dev_s_max / 1e12 * ws,
+                   "tuning": {"warps_per_block": wpb, "flat_vertices": flat,
+                              "source": "autotuner table" if tuned else "built-in defaults"}},
+        "in_domain_evals_per_s": _sum_over_ranks(pg, pts_in) / dev_s_max,
+        "keldysh_det_evals_per_s": _sum_over_ranks(pg, dets) / dev_s_max,
+        "naive_equivalent_tflops": _sum_over_ranks(pg, naive) / dev_s_max / 1e12,
         "wall_s": wall,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d // e2e_steps,
@@ -258,6 +279,158 @@ def run_ours(args, ws, rank, local, pg):
     for pr in problems:
         Q.qqmc_destroy_problem(pr)
     return out
+
+
+def _setup(args, local):
+    import torch
+
+    from paper_2002_12372_gb300 import build as b
+    from paper_2002_12372_gb300 import qqmc as Q
+    b.build()
+    torch.cuda.set_device(local)
+    Q.load()
+    if args.tuning and os.path.exists(args.tuning):
+        from paper_2002_12372_gb300 import autotune
+        t = autotune.load(args.tuning)
+        if t:
+            autotune.install(t)
+    return Q
+
+
+def run_batched(args, local):
+    """One persistent launch over orders 2..12 with N_n = 2^max(14, 24-n), K = 16 (CUDA graph)."""
+    import torch
+
+    Q = _setup(args, local)
+    prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
+    pr = Q.qqmc_create_problem(Q.make_params(GAMMA, 0.0, T_MAX, TAU, L_TABLE, SEED))
+    items = [(pr, n, 16, 2 ** max(14, 24 - n)) for n in range(2, 13)]
+    plan = Q.Plan(items, prec)
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        plan.launch(stream.cuda_stream, use_graph=True)
+        plan.results()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.launch(stream.cuda_stream, use_graph=True)
+        e1.record(stream)
+        res = plan.results()
+        ms.append(e0.elapsed_time(e1))
+    pts = sum(r.n_points * r.n_shifts for r, _ in res)
+    dets = sum(r.n_in_domain * 2.0 ** r.order for r, _ in res)
+    # the same items as separate launches, one per order (no graph)
+    sep = 0.0
+    for it in items:
+        p1 = Q.Plan([it], prec)
+        p1.launch(stream.cuda_stream)
+        p1.results()
+        p1.launch(stream.cuda_stream)
+        p1.results()
+        sep += p1.timing()[1]
+        p1.close()
+    plan.close()
+    Q.qqmc_destroy_problem(pr)
+    t = statistics.median(ms) / 1e3
+    return {"metric": "batched_integrand_evals_per_s", "value": pts / t, "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "one persistent launch (CUDA graph) over orders 2..12, N_n = 2^max(14,24-n), "
+                                   "16 shifts, Gamma=1, eps_d=0, t=10, tau=1, L=4096", "precision": args.precision},
+            "keldysh_det_evals_per_s": dets / t, "separate_launches_ms": sep, "batched_ms": t * 1e3,
+            "per_order": {r.order: {"q": r.q_mean, "err": r.q_err, "in_domain": r.n_in_domain} for r, _ in res}}
+
+
+def run_precision(args, local):
+    """Orders 6..12 at N = 2^log2 x 16 shifts: mixed (FP32 tables and Schur updates) against the FP64 path,
+    plus the per-point integrand error of the mixed path against the CPU oracle on identical points."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2002_12372_gb300 import workloads as W
+
+    Q = _setup(args, local)
+    N = 2 ** args.precision_log2
+    pr = Q.qqmc_create_problem(Q.make_params(GAMMA, 0.0, T_MAX, TAU, L_TABLE, SEED))
+    tabs = O.gf_tables(GAMMA, 0.0, T_MAX, L_TABLE)
+    rows = {}
+    stream = torch.cuda.Stream()
+    t_mixed = t_fp64 = 0.0
+    for n in range(6, 13):
+        out = {}
+        for prec in (Q.QQMC_PREC_MIXED, Q.QQMC_PREC_FP64):
+            plan = Q.Plan([(pr, n, 16, N)], prec)
+            plan.launch(stream.cuda_stream)
+            (r, S), = plan.results()
+            out[prec] = (r, plan.timing()[0])
+            plan.close()
+        rm, km = out[Q.QQMC_PREC_MIXED]
+        rf, kf = out[Q.QQMC_PREC_FP64]
+        t_mixed += km
+        t_fp64 += kf
+        u = W.ordered_times(900 + n, 8 if n < 11 else 3, n, T_MAX)
+        cm = Q.qqmc_integrand(pr, n, u, Q.QQMC_PREC_MIXED)
+        ref, scale = O.integrand(n, u, T_MAX, tabs, T_MAX, return_abs=True)
+        rows[n] = {"q_mixed": rm.q_mean, "q_fp64": rf.q_mean, "err_bar": rf.q_err,
+                   "abs_dev": abs(rm.q_mean - rf.q_mean), "dev_over_err": abs(rm.q_mean - rf.q_mean) / rf.q_err,
+                   "rel_dev": abs(rm.q_mean - rf.q_mean) / abs(rf.q_mean),
+                   "point_err_over_scale_max": float(np.max(np.abs(cm - ref) / scale)),
+                   "point_err_rel_median": float(np.median(np.abs(cm - ref) / np.abs(ref))),
+                   "ms_mixed": km, "ms_fp64": kf}
+    Q.qqmc_destroy_problem(pr)
+    return {"metric": "precision_study", "value": t_fp64 / t_mixed, "unit": "speedup mixed over fp64",
+            "config": {"workload": "orders 6..12, N=2^%d x 16 shifts, Gamma=1, eps_d=0, t=10, tau=1, L=4096"
+                                   % args.precision_log2}, "per_order": rows}
+
+
+def run_serving(args, local):
+    """Request sweep with Poisson arrivals through qqmc_submit / qqmc_poll (continuous batching)."""
+    import torch
+
+    from paper_2002_12372_gb300 import workloads as W
+
+    Q = _setup(args, local)
+    prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
+    reqs = W.serving_sweep(SEED, args.requests, 50.0, args.serve_log2_min, args.serve_log2_max, 16)
+    opts = Q.qqmc_server_opts(device_memory_limit=8 << 30, max_queue=4096, max_batch_items=256, precision=prec,
+                              use_graph=0, request_timeout_s=0.0)
+    srv = Q.qqmc_server_create(opts)
+    handles, done = {}, {}
+    t0 = time.perf_counter()
+    i = 0
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].arrival_s <= now:
+            r = Q.qqmc_request()
+            q = reqs[i]
+            r.params = Q.make_params(q.gamma, q.eps_d, q.t_max, 1.0 / q.gamma, L_TABLE, SEED + i)
+            r.n_max, r.n_shifts, r.n_points, r.U = q.n_max, q.n_shifts, q.n_points, q.U
+            handles[Q.qqmc_submit(srv, r)] = i
+            i += 1
+        for h, k in list(handles.items()):
+            rc, out = Q.qqmc_poll(srv, h)
+            if rc != Q.QQMC_PENDING:
+                done[k] = (rc, out)
+                del handles[h]
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    Q.qqmc_server_destroy(srv)
+    lat = sorted(out.latency_ms for rc, out in done.values() if rc == Q.QQMC_OK)
+    evals = sum(q.n_points * q.n_shifts * q.n_max for q in reqs)
+    rel_err = [out.q_err[q.n_max] / max(abs(out.q[q.n_max]), 1e-300) for q, (rc, out) in
+               zip(reqs, [done[k] for k in range(len(reqs))]) if rc == Q.QQMC_OK]
+    pct = lambda p: lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+    return {"metric": "serving", "value": evals / makespan, "unit": "evals/s", "n_gpus": 1,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "%d requests, eps_d~U[-3,3], U in {1,2,4}, t_max in {5,10,20}, n_max~U{4..10}, "
+                                   "N=2^floor(U[%d,%d]), 16 shifts, Poisson arrivals at 50/s"
+                                   % (len(reqs), args.serve_log2_min, args.serve_log2_max),
+                       "precision": args.precision},
+            "p50_latency_ms": pct(50), "p99_latency_ms": pct(99), "makespan_s": makespan,
+            "completed": len(lat), "failed": len(reqs) - len(lat),
+            "median_rel_err_at_nmax": statistics.median(rel_err) if rel_err else None}
 
 
 def cpu_oracle_sample(seconds_per_order: float = 1.5, orders=ORDERS, shift_seed: int = SEED):
@@ -319,9 +492,22 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_2002_12372_gb300", "tuning_gb300.json"),
+                    help="autotuner table (JSON keyed by GPU name); built-in defaults when absent")
     ap.add_argument("--slice-log2", type=int, default=16,
                     help="Sobol' indices per shift in one step (16: the benchmark batch; smaller for profiling)")
+    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving"], default="plain",
+                    help="plain: the benchmark workload; the others print their own study line")
+    ap.add_argument("--precision-log2", type=int, default=22)
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--serve-log2-min", type=int, default=16)
+    ap.add_argument("--serve-log2-max", type=int, default=22)
     args = ap.parse_args()
+    if args.config != "plain":
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        fn = {"batched": run_batched, "precision": run_precision, "serving": run_serving}[args.config]
+        print(json.dumps(fn(args, local)), flush=True)
+        return
     ws, rank, local, pg = _dist()
     if args.impl == "reference":
         out = run_reference(args, ws, rank, pg)

@@ -170,8 +170,11 @@ int qqmc_plan_timing(const qqmc_plan *plan, double *kernel_ms, double *total_ms)
 /*
  * Tuning of the determinant kernel (the autotuner writes these): for
  * each order, the number of warps per block and the number of vertices
- * resolved per lane in the flat (per-lane) phase.  Values <= 0 restore
- * the built-in defaults.  Applies to plans created afterwards.
+ * resolved per lane in the flat (per-lane) phase, 2..5 (the levels between
+ * the depth-first tree leaf, 5 vertices, and the flat phase are expanded
+ * breadth first).  Values <= 0 restore the built-in defaults.  Applies to
+ * plans created afterwards; a batched plan uses the tuning of its highest
+ * order.
  */
 int qqmc_set_tuning(int precision, int order, int warps_per_block, int flat_vertices);
 int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_vertices);

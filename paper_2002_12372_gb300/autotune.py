@@ -1,0 +1,127 @@
+"""Autotuner of the determinant kernel's launch shape.
+
+A batched plan runs with the tuning of its highest order, so the tuner times,
+for each highest order n, a batch holding every order 1..n of the plain dot
+(the shape of the benchmark batch and of a served request).  The candidates
+are warps per block (points in flight per block) and vertices resolved per
+lane in the flat phase (a lane's Keldysh chunk: one of 2^flat choice paths of
+the last vertices).  The fastest shape is installed with ``qqmc_set_tuning``
+and the table can be stored as JSON keyed by the GPU name.
+
+    python -m paper_2002_12372_gb300.autotune [--orders 1-12] [--out tuning.json]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+from . import qqmc as Q
+
+CANDIDATES = {
+    Q.QQMC_PREC_FP64: [(w, f) for w in (1, 2, 3, 4) for f in (2, 3, 5)],
+    Q.QQMC_PREC_MIXED: [(w, f) for w in (2, 4, 6, 8) for f in (2, 3, 4, 5)],
+}
+
+
+def _points_for(order: int, precision: int) -> int:
+    # every SM busy several times over, each candidate timed in well under a second
+    base = 2 ** 15 if precision == Q.QQMC_PREC_MIXED else 2 ** 13
+    return max(2 ** 10, base >> max(0, order - 8))
+
+
+def time_shape(pr: int, order: int, precision: int, wpb: int, flat: int, reps: int = 2) -> float:
+    Q.qqmc_set_tuning(precision, order, wpb, flat)
+    N = _points_for(order, precision)
+    plan = Q.Plan([(pr, m, 8, N) for m in range(1, order + 1)], precision)
+    try:
+        plan.launch()
+        plan.results()
+        best = float("inf")
+        for _ in range(reps):
+            plan.launch()
+            plan.results()
+            k, _a = plan.timing()
+            best = min(best, k)
+        return best
+    finally:
+        plan.close()
+
+
+def tune(orders=range(1, Q.QQMC_MAX_ORDER + 1), precisions=(Q.QQMC_PREC_FP64, Q.QQMC_PREC_MIXED), verbose=False):
+    """Returns {precision: {order: (wpb, flat, ms)}} and installs the winners."""
+    pr = Q.qqmc_create_problem(Q.make_params(eps_d=0.0, t_max=10.0))
+    table = {}
+    try:
+        for prec in precisions:
+            table[prec] = {}
+            for n in orders:
+                results = []
+                for wpb, flat in CANDIDATES[prec]:
+                    try:
+                        ms = time_shape(pr, n, prec, wpb, flat)
+                    except Q.QQMCError:
+                        continue  # shape does not fit (shared memory)
+                    results.append((ms, wpb, flat))
+                    if verbose:
+                        print("prec=%d n=%2d wpb=%d flat=%d  %.3f ms" % (prec, n, wpb, flat, ms), flush=True)
+                ms, wpb, flat = min(results)
+                table[prec][n] = (wpb, flat, ms)
+                Q.qqmc_set_tuning(prec, n, wpb, flat)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    return table
+
+
+def install(table) -> None:
+    for prec, rows in table.items():
+        for n, (wpb, flat, _ms) in rows.items():
+            Q.qqmc_set_tuning(int(prec), int(n), int(wpb), int(flat))
+
+
+def save(table, path: str) -> None:
+    import torch
+    name = torch.cuda.get_device_name(0)
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[name] = {str(p): {str(n): list(v) for n, v in rows.items()} for p, rows in table.items()}
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+
+
+def load(path: str):
+    import torch
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        data = json.load(f)
+    rows = data.get(torch.cuda.get_device_name(0))
+    if rows is None:
+        return None
+    return {int(p): {int(n): tuple(v) for n, v in r.items()} for p, r in rows.items()}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--orders", default="1-12")
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--precision", choices=["fp64", "mixed", "both"], default="both")
+    args = ap.parse_args()
+    lo, hi = (int(x) for x in args.orders.split("-"))
+    precs = {"fp64": (Q.QQMC_PREC_FP64,), "mixed": (Q.QQMC_PREC_MIXED,),
+             "both": (Q.QQMC_PREC_FP64, Q.QQMC_PREC_MIXED)}[args.precision]
+    from . import build
+    build.build()
+    t0 = time.time()
+    table = tune(range(lo, hi + 1), precs, verbose=True)
+    print(json.dumps({str(p): {str(n): v for n, v in r.items()} for p, r in table.items()}))
+    print("tuning took %.1f s" % (time.time() - t0))
+    if args.out:
+        save(table, args.out)
+
+
+if __name__ == "__main__":
+    main()

@@ -40,7 +40,11 @@ static bool g_tune_set[2][kMaxOrder + 1];
 static Tuning default_tuning(int precision, int order) {
     (void)order;
     Tuning t;
-    t.flat = 5;
+    // FP64: breadth-first expansion below the tree leaf, 2 vertices per lane
+    // (the FP64 pipe is the bound, so fewer flops win); mixed: 5 vertices per
+    // lane in registers (shared-memory traffic of cooperative updates is the
+    // FP32 bound).
+    t.flat = precision == QQMC_PREC_FP64 ? 2 : 5;
     t.warps_per_block = precision == QQMC_PREC_FP64 ? 2 : 4;
     return t;
 }
@@ -459,8 +463,8 @@ extern "C" int qqmc_set_tuning(int precision, int order, int warps_per_block, in
         g_tune_set[p][order] = false;
         return QQMC_OK;
     }
-    if (warps_per_block > 16 || flat_vertices < 3 || flat_vertices > 5)
-        return set_error(QQMC_E_INVAL, "qqmc_set_tuning: warps_per_block in 1..16, flat_vertices in 3..5");
+    if (warps_per_block > 16 || flat_vertices < 2 || flat_vertices > 5)
+        return set_error(QQMC_E_INVAL, "qqmc_set_tuning: warps_per_block in 1..16, flat_vertices in 2..5");
     g_tune[p][order].warps_per_block = warps_per_block;
     g_tune[p][order].flat = flat_vertices;
     g_tune_set[p][order] = true;

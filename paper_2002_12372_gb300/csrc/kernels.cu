@@ -140,41 +140,52 @@ struct TabT<float> {
     using V = float4;
 };
 
-// pair values for tau > 0: gl = g^<(tau), gg = g^>(tau)
+// pair values for tau > 0: gl = g^<(tau), gg = g^>(tau).  Position on the
+// mesh s = (tau + T) / h, formed as tau / h + T / h (one FP64 FMA); the blend
+// runs in R.
 template <class R>
-__device__ __forceinline__ void interp_pair(const typename TabT<R>::V *tab, double T, double h, int L, double tau,
+__device__ __forceinline__ void interp_pair(const typename TabT<R>::V *tab, double inv_h, double s0, int L, double tau,
                                             cx<R> &gl, cx<R> &gg) {
-    double s = (tau + T) / h;
-    double kf = floor(s);
-    int k = (int)kf;
+    double s = fma(tau, inv_h, s0);
+    int k = __double2int_rd(s);
     int kmin = L / 2 - 1, kmax = L - 2;
     k = k < kmin ? kmin : (k > kmax ? kmax : k);
-    double f = s - (double)k;
+    R fr = (R)(s - (double)k);
+    R g = R(1) - fr;
     typename TabT<R>::V a = tab[k - kmin];
     typename TabT<R>::V b = tab[k - kmin + 1];
-    R fr = (R)f, g = (R)(1.0 - f);
     gl = mk<R>(fmaR(fr, b.x, g * a.x), fmaR(fr, b.y, g * a.y));
     gg = mk<R>(fmaR(fr, b.z, g * a.z), fmaR(fr, b.w, g * a.w));
 }
 
 // ----------------------------------------------------------------------------
 // Per-warp shared-memory layout for the Keldysh sum.
+//
+// The depth-first tree stops when kTreeLeaf vertices remain (or earlier for
+// small n).  From there, B = Rleaf - RF levels are expanded breadth first
+// (2, 4, ... 2^B sibling matrices, all lanes cooperating), and each lane
+// resolves the last RF vertices of one node along one choice path in
+// registers: 2^B nodes x 2^RF paths = 2^Rleaf <= 32 lanes.
 // ----------------------------------------------------------------------------
+constexpr int kTreeLeaf = 5;
+
 template <class R>
 struct WarpSmem {
     cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l
-    cx<R> *wrow;    // scaled pivot row, <= 2 n_max entries
+    cx<R> *wrow;    // scaled pivot row(s): <= max(2 n_max, 64) entries
     cx<R> *P;       // P[j*(n_max+1)+k] = g^>(u_j - u_k), j < k
     cx<R> *Rr;      // Rr[...]          = g^<(u_j - u_k)
-    cx<R> *detD;    // per level
+    cx<R> *detD;    // per tree level
+    cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
+    cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
+    cx<R> *bip;     // pivot reciprocal per child of the level being built (32)
     double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t)
-    double *wpt;    // [32] weights
 };
 
-__host__ __device__ inline size_t stack_entries(int n_max, int F) {
+__host__ __device__ inline size_t stack_entries(int n_max) {
     size_t tot = 0;
     int R0 = n_max - 1;
-    int levels = R0 > F ? R0 - F : 0;
+    int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
     for (int l = 0; l <= levels; ++l) {
         size_t S = 2 * (size_t)(R0 - l) + 2;
         tot += S * S;
@@ -182,32 +193,59 @@ __host__ __device__ inline size_t stack_entries(int n_max, int F) {
     return tot;
 }
 
+// entries of the breadth-first levels below a tree leaf of Rleaf vertices
+__host__ __device__ inline size_t bfs_entries(int Rleaf, int RF) {
+    size_t tot = 0;
+    int B = Rleaf > RF ? Rleaf - RF : 0;
+    for (int b = 1; b <= B; ++b) {
+        size_t S = 2 * (size_t)(Rleaf - b) + 2;
+        tot += ((size_t)1 << b) * S * S;
+    }
+    return tot;
+}
+
+__host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
+    size_t m = 0;
+    for (int Rl = 0; Rl <= kTreeLeaf && Rl <= n_max - 1; ++Rl) {
+        size_t e = bfs_entries(Rl, RF);
+        m = e > m ? e : m;
+    }
+    return m;
+}
+
 template <class R>
-__host__ __device__ inline size_t warp_smem_bytes(int n_max, int F) {
-    size_t c = stack_entries(n_max, F) + 2 * (size_t)n_max + 2 * (size_t)(n_max + 1) * (n_max + 1) + n_max + 1;
+__host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF) {
+    size_t wr = 2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64;
+    size_t c = stack_entries(n_max) + wr + 2 * (size_t)(n_max + 1) * (n_max + 1) + n_max + 1 +
+               bfs_max_entries(n_max, RF) + 64 + 32;
     size_t bytes = c * sizeof(cx<R>);
     bytes = (bytes + 15) & ~(size_t)15;
-    bytes += (32 * (size_t)(n_max + 1) + 32) * sizeof(double);
+    bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
     return (bytes + 127) & ~(size_t)127;
 }
 
 template <class R>
-__device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int F) {
+__device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int RF) {
     WarpSmem<R> w;
     cx<R> *p = reinterpret_cast<cx<R> *>(base);
     w.stack = p;
-    p += stack_entries(n_max, F);
+    p += stack_entries(n_max);
     w.wrow = p;
-    p += 2 * n_max;
+    p += 2 * n_max > 64 ? 2 * n_max : 64;
     w.P = p;
     p += (n_max + 1) * (n_max + 1);
     w.Rr = p;
     p += (n_max + 1) * (n_max + 1);
     w.detD = p;
     p += n_max + 1;
+    w.bfs = p;
+    p += bfs_max_entries(n_max, RF);
+    w.bdet = p;
+    p += 64;
+    w.bip = p;
+    p += 32;
     size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
     w.upt = reinterpret_cast<double *>(base + off);
-    w.wpt = w.upt + 32 * (n_max + 1);
     return w;
 }
 
@@ -220,15 +258,15 @@ __device__ __forceinline__ cx<R> G(const WarpSmem<R> &ws, int NP, cx<R> d, int v
     return av ? nconj(ws.P[w * NP + v]) : nconj(ws.Rr[w * NP + v]);
 }
 
-// Flat phase: one lane per choice path of the F remaining vertices of the tree
-// leaf matrix E (size S = 2F + 2).  The first elimination is fused with the
-// gather; the rest runs on an (F+1) x (F+1) register matrix whose rows and
-// columns are {copy a_1 = 0, copy a_1 = 1, remaining vertices}.
+// Flat phase: one lane resolves the F remaining vertices of node matrix E
+// (size S = 2F + 2) along the choice path `path` (bit q = Keldysh index of the
+// q-th remaining vertex).  The first elimination is fused with the gather;
+// the rest runs on an (F+1) x (F+1) register matrix whose rows and columns
+// are {copy a_1 = 0, copy a_1 = 1, remaining vertices}.
 template <class R, int F>
-__device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parity, int lane, Acc<R> &acc_re,
+__device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &acc_re,
                                            Acc<R> &acc_im) {
     constexpr int S = 2 * F + 2;
-    if (lane >= (1 << F)) return;
     if (F == 0) {
         cx<R> dd = cmul(detD, detD);
         cx<R> diff = mk<R>(E[0].re - E[S + 1].re, E[0].im - E[S + 1].im);
@@ -243,8 +281,8 @@ __device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parit
     idx[0] = 0;
     idx[1] = 1;
 #pragma unroll
-    for (int q = 1; q < F; ++q) idx[q + 1] = 2 + 2 * q + ((lane >> q) & 1);
-    const int p0 = 2 + (lane & 1);
+    for (int q = 1; q < F; ++q) idx[q + 1] = 2 + 2 * q + ((path >> q) & 1);
+    const int p0 = 2 + (path & 1);
     cx<R> piv = E[p0 * S + p0];
     detD = cmul(detD, piv);
     cx<R> ip = crcp(piv);
@@ -284,66 +322,186 @@ __device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parit
     cx<R> dd = cmul(detD, detD);
     cx<R> diff = mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im);
     cx<R> term = cmul(dd, diff);
-    parity ^= __popc(lane) & 1;
+    parity ^= __popc(path) & 1;
     if (parity) term = mk<R>(-term.re, -term.im);
     acc_re.add(term.re);
     acc_im.add(term.im);
 }
 
-template <class R, int F>
-__device__ __forceinline__ void flat_dispatch(int Rleaf, const cx<R> *E, cx<R> detD, int parity, int lane,
-                                              Acc<R> &ar, Acc<R> &ai) {
-    // Rleaf <= F
-    switch (Rleaf) {
-        case 0: flat_phase<R, 0>(E, detD, parity, lane, ar, ai); break;
-        case 1: flat_phase<R, 1>(E, detD, parity, lane, ar, ai); break;
-        case 2: flat_phase<R, 2>(E, detD, parity, lane, ar, ai); break;
-        case 3: flat_phase<R, 3>(E, detD, parity, lane, ar, ai); break;
-        case 4: if (F >= 4) flat_phase<R, (F >= 4 ? 4 : 0)>(E, detD, parity, lane, ar, ai); break;
-        default: if (F >= 5) flat_phase<R, (F >= 5 ? 5 : 0)>(E, detD, parity, lane, ar, ai); break;
+template <class R, int RF>
+__device__ __forceinline__ void flat_dispatch(int Rf, const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &ar,
+                                              Acc<R> &ai) {
+    switch (Rf) {  // Rf <= RF
+        case 0: flat_phase<R, 0>(E, detD, parity, path, ar, ai); break;
+        case 1: flat_phase<R, 1>(E, detD, parity, path, ar, ai); break;
+        case 2: flat_phase<R, 2>(E, detD, parity, path, ar, ai); break;
+        case 3: if (RF >= 3) flat_phase<R, (RF >= 3 ? 3 : 0)>(E, detD, parity, path, ar, ai); break;
+        case 4: if (RF >= 4) flat_phase<R, (RF >= 4 ? 4 : 0)>(E, detD, parity, path, ar, ai); break;
+        default: if (RF >= 5) flat_phase<R, (RF >= 5 ? 5 : 0)>(E, detD, parity, path, ar, ai); break;
     }
 }
 
-// Keldysh sum for one point whose times are in ws.upt[src] (u_0 = t first).
+// One cooperative elimination: child(ren) of S x S parent matrices.  Child j
+// of the new level comes from parent j >> 1 with Keldysh index a = j & 1 on the
+// parent's first remaining vertex (pivot row/column 2 + a).  The new matrices
+// are (S-2) x (S-2), all children contiguous in `out`.
+template <class R>
+__device__ __forceinline__ void expand_level(const cx<R> *__restrict__ in, int S, int nchild, int first_a,
+                                             cx<R> *__restrict__ out, const cx<R> *detD_in, cx<R> *detD_out,
+                                             cx<R> *__restrict__ wrow, cx<R> *ip_buf, int lane) {
+    const int S2 = S - 2;
+    // child pivots: reciprocal and running det M_down
+    for (int j = lane; j < nchild; j += 32) {
+        const int a = nchild == 1 ? first_a : (j & 1);
+        const int pj = nchild == 1 ? 0 : (j >> 1);
+        const int pr = 2 + a;
+        cx<R> piv = in[(size_t)pj * S * S + pr * S + pr];
+        ip_buf[j] = crcp(piv);
+        detD_out[j] = cmul(detD_in[pj], piv);
+    }
+    __syncwarp();
+    // scaled pivot rows
+    for (int q = lane; q < nchild * S2; q += 32) {
+        const int j = q / S2, c2 = q - j * S2;
+        const int a = nchild == 1 ? first_a : (j & 1);
+        const int pj = nchild == 1 ? 0 : (j >> 1);
+        const int pr = 2 + a;
+        const int c = c2 < 2 ? c2 : c2 + 2;
+        wrow[q] = cmul(in[(size_t)pj * S * S + pr * S + c], ip_buf[j]);
+    }
+    __syncwarp();
+    // lane -> (child j, row r2, column c2) stepped by 32 entries without divisions
+    const int dr = 32 / S2, dc = 32 - dr * S2;
+    int r2 = lane / S2, c2 = lane - r2 * S2, j = 0;
+    while (r2 >= S2) { r2 -= S2; ++j; }
+    const int total = nchild * S2 * S2;
+    cx<R> *o = out + lane;
+    for (int e = lane; e < total; e += 32, o += 32) {
+        const int a = nchild == 1 ? first_a : (j & 1);
+        const int pj = nchild == 1 ? 0 : (j >> 1);
+        const int pr = 2 + a;
+        const int r = r2 < 2 ? r2 : r2 + 2;
+        const int c = c2 < 2 ? c2 : c2 + 2;
+        const cx<R> *P = in + (size_t)pj * S * S;
+        *o = cfms(P[r * S + c], P[r * S + pr], wrow[j * S2 + c2]);
+        c2 += dc;
+        r2 += dr;
+        if (c2 >= S2) { c2 -= S2; ++r2; }
+        while (r2 >= S2) { r2 -= S2; ++j; }
+    }
+    __syncwarp();
+}
+
+// Float-float or double-double style butterfly of the lane accumulators:
+// combines (s, c) pairs with two-sum in R, then returns s + c in double.
+template <class R>
+__device__ __forceinline__ void two_sum_r(R a, R b, R &s, R &e) {
+    s = a + b;
+    R z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+template <class R>
+__device__ __forceinline__ double warp_total(Acc<R> acc) {
+    R s = acc.s, c = acc.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        R s2 = __shfl_xor_sync(FULL, s, o);
+        R c2 = __shfl_xor_sync(FULL, c, o);
+        R t, e;
+        int lo = ((threadIdx.x & 31) & o) == 0;
+        if (lo) two_sum_r<R>(s, s2, t, e); else two_sum_r<R>(s2, s, t, e);
+        s = t;
+        c = lo ? (c + c2) + e : (c2 + c) + e;
+    }
+    return (double)s + (double)c;
+}
+
+// Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
 // Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
-template <class R, int F>
+template <class R, int RF>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d,
-                                  const typename TabT<R>::V *tab, double T, double h, int L, int lane) {
+                                  const typename TabT<R>::V *tab, double inv_h, double s0, int L, int lane) {
     const int NP = n_max + 1;
     // 1. pair interpolation, 0 <= j < k <= n
     const int npairs = n * (n + 1) / 2;
     for (int p = lane; p < npairs; p += 32) {
-        int k = (int)((1.0 + sqrt(8.0 * p + 1.0)) * 0.5);
+        int k = (int)((1.0f + sqrtf(8.0f * p + 1.0f)) * 0.5f);
         while (k * (k - 1) / 2 > p) --k;
         while ((k + 1) * k / 2 <= p) ++k;
         int j = p - k * (k - 1) / 2;
         cx<R> gl, gg;
-        interp_pair<R>(tab, T, h, L, u[j] - u[k], gl, gg);
+        interp_pair<R>(tab, inv_h, s0, L, u[j] - u[k], gl, gg);
         ws.P[j * NP + k] = gg;
         ws.Rr[j * NP + k] = gl;
     }
     __syncwarp();
-    // 2. level 0: vertex 1 eliminated (both a_1 kept in the two measurement copies)
+    // 2. level 0: vertex 1 eliminated (both a_1 kept in the two measurement copies).
+    // Built by 2x2 blocks: block row/column 0 = the measurement copies, block
+    // q >= 1 = vertex q+1 with its two Keldysh indices.  Within a block the
+    // entry is base(ai, aj) - left(ai) right(aj), with left = M(., vertex 1),
+    // right = M(vertex 1, .) / d.
     const int R0 = n - 1;
     const int S0 = 2 * R0 + 2;
     const cx<R> id = crcp(d);
-    for (int e = lane; e < S0 * S0; e += 32) {
-        int r = e / S0, c = e - r * S0;
-        int vr, ar, vc, ac, er, ec;
-        if (r < 2) { vr = 0; ar = 0; er = r; } else { vr = 2 + ((r - 2) >> 1); ar = (r - 2) & 1; er = 0; }
-        if (c < 2) { vc = 0; ac = 1; ec = c; } else { vc = 2 + ((c - 2) >> 1); ac = (c - 2) & 1; ec = 0; }
-        cx<R> base = G<R>(ws, NP, d, vr, ar, vc, ac);
-        cx<R> left = G<R>(ws, NP, d, vr, ar, 1, er);
-        cx<R> right = cmul(G<R>(ws, NP, d, 1, ec, vc, ac), id);
-        ws.stack[e] = cfms(base, left, right);
+    {
+        // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
+        const cx<R> P01 = ws.P[1], R01 = ws.Rr[1];
+        const cx<R> r1[2] = {P01, R01};
+        const cx<R> c1d[2] = {cmul(nconj(R01), id), cmul(nconj(P01), id)};
+        for (int bid = lane; bid < n * n; bid += 32) {
+            const int bx = bid / n, by = bid - bx * n;
+            cx<R> base[2][2], left[2], right[2];
+            if (bx == 0) {
+                left[0] = r1[0];
+                left[1] = r1[1];
+            } else {  // vertex i = bx + 1 > 1, lower entries of column vertex 1
+                const int i = bx + 1;
+                left[0] = nconj(ws.Rr[1 * NP + i]);
+                left[1] = nconj(ws.P[1 * NP + i]);
+            }
+            if (by == 0) {
+                right[0] = c1d[0];
+                right[1] = c1d[1];
+            } else {  // vertex j = by + 1 > 1, upper entries of row vertex 1
+                const int j = by + 1;
+                right[0] = cmul(ws.P[1 * NP + j], id);
+                right[1] = cmul(ws.Rr[1 * NP + j], id);
+            }
+            if (bx == by) {
+                base[0][0] = base[0][1] = base[1][0] = base[1][1] = d;
+            } else if (bx == 0) {  // measurement row: r_j(aj)
+                const int j = by + 1;
+                base[0][0] = base[1][0] = ws.P[j];
+                base[0][1] = base[1][1] = ws.Rr[j];
+            } else if (by == 0) {  // measurement column: c_i(ai)
+                const int i = bx + 1;
+                base[0][0] = base[0][1] = nconj(ws.Rr[i]);
+                base[1][0] = base[1][1] = nconj(ws.P[i]);
+            } else if (bx < by) {  // upper: depends on aj
+                const int i = bx + 1, j = by + 1;
+                base[0][0] = base[1][0] = ws.P[i * NP + j];
+                base[0][1] = base[1][1] = ws.Rr[i * NP + j];
+            } else {  // lower: depends on ai
+                const int i = bx + 1, j = by + 1;
+                base[0][0] = base[0][1] = nconj(ws.Rr[j * NP + i]);
+                base[1][0] = base[1][1] = nconj(ws.P[j * NP + i]);
+            }
+            cx<R> *o = ws.stack + (2 * bx) * S0 + 2 * by;
+#pragma unroll
+            for (int x = 0; x < 2; ++x)
+#pragma unroll
+                for (int y = 0; y < 2; ++y) o[x * S0 + y] = cfms(base[x][y], left[x], right[y]);
+        }
     }
     if (lane == 0) ws.detD[0] = d;
     __syncwarp();
-    // 3. tree over a_2 .. a_{levels+1}, flat phase on the remaining vertices
-    const int levels = R0 > F ? R0 - F : 0;
+    // 3. depth-first tree over a_2 .. a_{levels+1}
+    const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
     const int Rleaf = R0 - levels;
-    // offsets of each level
+    const int B = Rleaf > RF ? Rleaf - RF : 0;
+    const int Rf = Rleaf - B;
     int off[kMaxOrder];
     {
         int o = 0;
@@ -357,39 +515,43 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     ar.init();
     ai.init();
     const int nleaf = 1 << levels;
+    const int node = lane >> Rf;
+    const int path = lane & ((1 << Rf) - 1);
+    const bool active = lane < (1 << Rleaf);
     for (int b = 0; b < nleaf; ++b) {
         int from = (b == 0) ? 0 : levels - (__ffs(b) - 1) - 1;
         for (int l = from; l < levels; ++l) {
             const int a = (b >> (levels - 1 - l)) & 1;
             const int S = 2 * (R0 - l) + 2;
-            const int S2 = S - 2;
-            const cx<R> *E = ws.stack + off[l];
-            cx<R> *E2 = ws.stack + off[l + 1];
-            const int pr = 2 + a;
-            cx<R> piv = E[pr * S + pr];
-            cx<R> ip = crcp(piv);
-            for (int c2 = lane; c2 < S2; c2 += 32) {
-                int c = c2 < 2 ? c2 : c2 + 2;
-                ws.wrow[c2] = cmul(E[pr * S + c], ip);
-            }
-            if (lane == 0) ws.detD[l + 1] = cmul(ws.detD[l], piv);
-            __syncwarp();
-            for (int e = lane; e < S2 * S2; e += 32) {
-                int r2 = e / S2, c2 = e - r2 * S2;
-                int r = r2 < 2 ? r2 : r2 + 2;
-                int c = c2 < 2 ? c2 : c2 + 2;
-                E2[e] = cfms(E[r * S + c], E[r * S + pr], ws.wrow[c2]);
-            }
-            __syncwarp();
+            expand_level<R>(ws.stack + off[l], S, 1, a, ws.stack + off[l + 1], ws.detD + l, ws.detD + l + 1,
+                            ws.wrow, ws.bip, lane);
         }
-        const int parity = __popc(b) & 1;
-        flat_dispatch<R, F>(Rleaf, ws.stack + off[levels], ws.detD[levels], parity, lane, ar, ai);
+        const int tparity = __popc(b) & 1;
+        // 4. breadth-first expansion of B levels below the tree leaf
+        const cx<R> *E = ws.stack + off[levels];
+        int S = 2 * Rleaf + 2;
+        const cx<R> *ndet = ws.detD + levels;
+        cx<R> *dbuf = ws.bdet;
+        size_t bo = 0;
+        for (int lb = 0; lb < B; ++lb) {
+            const int nparent = 1 << lb;
+            cx<R> *out = ws.bfs + bo;
+            expand_level<R>(E, S, 2 * nparent, 0, out, ndet, dbuf, ws.wrow, ws.bip, lane);
+            bo += (size_t)(2 * nparent) * (S - 2) * (S - 2);
+            E = out;
+            S -= 2;
+            ndet = dbuf;
+            dbuf = (dbuf == ws.bdet) ? ws.bdet + 32 : ws.bdet;
+        }
+        // 5. per-lane flat phase on the last Rf vertices
+        if (active) {
+            const cx<R> *En = E + (size_t)node * S * S;
+            const int parity = tparity ^ (__popc(node) & 1);
+            flat_dispatch<R, RF>(Rf, En, ndet[B > 0 ? node : 0], parity, path, ar, ai);
+        }
         __syncwarp();
     }
-    double sr = (double)ar.s, cr = (double)ar.c, si = (double)ai.s, ci = (double)ai.c;
-    warp_reduce_pair(sr, cr);
-    warp_reduce_pair(si, ci);
-    return mk<double>(sr + cr, si + ci);
+    return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
 }
 
 // i^n * z
@@ -409,16 +571,35 @@ __device__ __forceinline__ const dbl4 *item_table<double>(const ItemDev &it) { r
 template <>
 __device__ __forceinline__ const float4 *item_table<float>(const ItemDev &it) { return it.table32; }
 
+// Gap v = -tau log(1 - x) of the exponential warp, x = y 2^-32.  FP64 for the
+// FP64 path; FP32 for the mixed path (log1p for x < 1/2, log of the exactly
+// formed 1 - x above), with the times accumulated in FP64 either way.
+__device__ __forceinline__ void warp_gap(double, uint32_t y, double tau, double &v, double &omx) {
+    double x = (double)y * 0x1p-32;
+    v = -tau * log1p(-x);
+    omx = 1.0 - x;
+}
+__device__ __forceinline__ void warp_gap(float, uint32_t y, double tau, double &v, double &omx) {
+    float l;
+    if (y < 0x80000000u) {
+        l = log1pf(-(float)y * 0x1p-32f);
+    } else {
+        l = logf((float)(0x100000000ull - (unsigned long long)y) * 0x1p-32f);
+    }
+    v = (double)(-(float)tau * l);
+    omx = (double)((float)(0x100000000ull - (unsigned long long)y) * 0x1p-32f);
+}
+
 // ----------------------------------------------------------------------------
 // Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
 // ----------------------------------------------------------------------------
-template <class R, int F>
+template <class R, int RF>
 __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
                               unsigned long long *counter, int n_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, F), n_max, F);
+    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF), n_max, RF);
     const int NU = n_max + 1;
     while (true) {
         unsigned long long c = 0;
@@ -434,7 +615,7 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
         const long long blk = local - (long long)k * I.chunks_per_shift;
         const long long idx = blk * kChunk + lane;
         const bool valid = idx < I.n_points;
-        // point generation and warp (FP64; Sobol' integers are exact)
+        // point generation and warp (Sobol' integers are exact)
         bool inside = false;
         double w = 0.0;
         if (valid) {
@@ -443,26 +624,29 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             ws.upt[lane * NU] = I.t;
             for (int m = 0; m < n; ++m) {
                 uint32_t y = sobol_word(m, i) ^ I.shifts[k * n + m];
-                double x = (double)y * 0x1p-32;
-                double v = -I.tau * log1p(-x);
+                double v, omx;
+                warp_gap(R(0), y, I.tau, v, omx);
                 uprev = uprev - v;
                 ws.upt[lane * NU + 1 + m] = uprev;
-                prod *= (1.0 - x);
+                prod *= omx;
             }
             inside = uprev > 0.0;
-            w = pow(I.tau, (double)n) / prod;
+            double tn = 1.0;
+            for (int m = 0; m < n; ++m) tn *= I.tau;
+            w = tn / prod;
         }
-        ws.wpt[lane] = w;
         unsigned mask = __ballot_sync(FULL, inside);
         __syncwarp();
         cx<double> myval = mk<double>(0.0, 0.0);
         const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
         const typename TabT<R>::V *tab = item_table<R>(I);
+        const double inv_h = 1.0 / I.h;
+        const double s0 = I.T * inv_h;
         unsigned mm = mask;
         while (mm) {
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
-            cx<double> s = keldysh_sum<R, F>(ws, ws.upt + src * NU, n, n_max, d, tab, I.T, I.h, I.L, lane);
+            cx<double> s = keldysh_sum<R, RF>(ws, ws.upt + src * NU, n, n_max, d, tab, inv_h, s0, I.L, lane);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -564,14 +748,13 @@ __global__ void warp_kernel(int order, uint64_t first, uint64_t count, const uin
 }
 
 // One warp per caller point.
-template <class R, int F>
+template <class R, int RF>
 __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, double *out, int n_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, F), n_max, F);
+    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF), n_max, RF);
     const int n = I.order;
-    const int NU = n_max + 1;
     uint64_t q = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
     if (q >= count) return;
     if (lane == 0) {
@@ -580,13 +763,13 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     }
     __syncwarp();
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
-    cx<double> s = keldysh_sum<R, F>(ws, ws.upt, n, n_max, d, item_table<R>(I), I.T, I.h, I.L, lane);
+    const double inv_h = 1.0 / I.h;
+    cx<double> s = keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, item_table<R>(I), inv_h, I.T * inv_h, I.L, lane);
     if (lane == 0) {
         cx<double> cval = times_i_pow(s, n);
         out[2 * q] = cval.re;
         out[2 * q + 1] = cval.im;
     }
-    (void)NU;
 }
 
 // ----------------------------------------------------------------------------
@@ -742,6 +925,7 @@ template <class R, int F>
 static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, cudaStream_t s) {
     size_t smem = warp_smem_bytes<R>(n_max, F) * wpb;
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(detsum_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -763,12 +947,14 @@ cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_c
     const int wpb = tune.warps_per_block;
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
+            case 2: return launch_detsum_t<double, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
             case 3: return launch_detsum_t<double, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
             case 4: return launch_detsum_t<double, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
             default: return launch_detsum_t<double, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
         }
     }
     switch (tune.flat) {
+        case 2: return launch_detsum_t<float, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
         case 3: return launch_detsum_t<float, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
         case 4: return launch_detsum_t<float, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
         default: return launch_detsum_t<float, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
@@ -815,12 +1001,14 @@ cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *
     if (count == 0) return cudaSuccess;
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
+            case 2: return launch_integrand_t<double, 2>(item, count, d_u, d_out, s);
             case 3: return launch_integrand_t<double, 3>(item, count, d_u, d_out, s);
             case 4: return launch_integrand_t<double, 4>(item, count, d_u, d_out, s);
             default: return launch_integrand_t<double, 5>(item, count, d_u, d_out, s);
         }
     }
     switch (tune.flat) {
+        case 2: return launch_integrand_t<float, 2>(item, count, d_u, d_out, s);
         case 3: return launch_integrand_t<float, 3>(item, count, d_u, d_out, s);
         case 4: return launch_integrand_t<float, 4>(item, count, d_u, d_out, s);
         default: return launch_integrand_t<float, 5>(item, count, d_u, d_out, s);

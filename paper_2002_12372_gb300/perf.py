@@ -30,34 +30,46 @@ def peak_tflops(precision: str, mhz: float = SM_MAX_MHZ) -> float:
 CFMS, CMUL, CRCP, ACC = 8, 6, 6, 8
 
 
-def flops_per_point(n: int, F: int = 5) -> float:
+TREE_LEAF = 5
+
+
+def _flat_lane(Rf: int) -> float:
+    """One lane resolving Rf vertices of a node along one choice path."""
+    if Rf == 0:
+        return 2 * CMUL + 2 + ACC
+    M = Rf + 1
+    fl = CRCP + CMUL + M * CMUL + (M * M - 2) * CFMS
+    for q in range(1, Rf):
+        p = q + 1
+        rows = 2 + (M - 1 - p)
+        fl += CRCP + CMUL + rows * CMUL + (rows * rows - 2) * CFMS
+    return fl + 2 * CMUL + 2 + ACC
+
+
+def flops_per_point(n: int, RF: int = 2) -> float:
+    """Real flops per in-domain point of order n with RF vertices per lane."""
     R0 = n - 1
     S0 = 2 * n
     fl = 0.0
-    # pair interpolation: 2 complex lerps (8 fma-equivalent ops) + index arithmetic
+    # pair interpolation: 2 complex lerps + position arithmetic
     fl += (n * (n + 1) // 2) * 12
     # level 0: cmul (right * 1/d) + cfms per entry, one reciprocal
     fl += S0 * S0 * (CMUL + CFMS) + CRCP
-    levels = R0 - F if R0 > F else 0
+    levels = R0 - TREE_LEAF if R0 > TREE_LEAF else 0
     Rleaf = R0 - levels
-    # tree transitions: level l -> l+1 computed 2^(l+1) times in the walk
+    # depth-first tree: level l -> l+1 computed 2^(l+1) times in the walk
     for l in range(levels):
         S2 = 2 * (R0 - l)
         fl += 2 ** (l + 1) * (S2 * CMUL + S2 * S2 * CFMS + CRCP + CMUL)
-    # flat phase: 2^levels tree leaves x 2^Rleaf lanes
-    per_lane = 0.0
-    if Rleaf == 0:
-        per_lane = 2 * CMUL + 2 + ACC
-    else:
-        M = Rleaf + 1
-        per_lane += CRCP + CMUL + M * CMUL + (M * M - 2) * CFMS
-        for q in range(1, Rleaf):
-            p = q + 1
-            rows = 2 + (M - 1 - p)
-            per_lane += CRCP + CMUL + rows * CMUL + (rows * rows - 2) * CFMS
-        per_lane += 2 * CMUL + 2 + ACC
-    fl += 2 ** levels * 2 ** Rleaf * per_lane
-    return fl
+    # below each tree leaf: breadth-first levels, then the per-lane flat phase
+    B = Rleaf - RF if Rleaf > RF else 0
+    Rf = Rleaf - B
+    leaf = 0.0
+    for lb in range(B):
+        S2 = 2 * (Rleaf - lb)
+        leaf += 2 ** (lb + 1) * (CRCP + CMUL + S2 * CMUL + S2 * S2 * CFMS)
+    leaf += 2 ** Rleaf * _flat_lane(Rf)
+    return fl + 2 ** levels * leaf
 
 
 def w_naive(n: int) -> float:

@@ -189,3 +189,20 @@ def test_single_level_flat_occupation_cancels_at_every_order(Q, W, oracle):
             assert np.all(np.abs(ref) <= 1e-13 * scale)
     finally:
         Q.qqmc_destroy_problem(pr)
+
+
+@pytest.mark.parametrize("order,N", [(3, 4096), (6, 2048), (9, 512)])
+def test_integration_mixed_within_stated_bound_of_fp64(Q, W, oracle, order, N):
+    """Mixed precision (FP32 tables and Schur updates, compensated FP32 leaf sums,
+    FP64 point and shift sums) against the FP64 path on the same shifts:
+    per-shift sums within 1e-4 relative, the shift mean within 5% of its error bar."""
+    T, K = 10.0, 8
+    pr, tabs = _problem(Q, W, seed=40 + order, T=T)
+    sw = W.shift_words(2000 + order, K, order)
+    try:
+        r64, S64 = Q.qqmc_integrate(pr, order, N, K, Q.QQMC_PREC_FP64, sw)
+        r32, S32 = Q.qqmc_integrate(pr, order, N, K, Q.QQMC_PREC_MIXED, sw)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    assert np.all(np.abs(S32 - S64) <= 1e-4 * np.abs(S64)), np.abs(S32 - S64) / np.abs(S64)
+    assert abs(r32.q_mean - r64.q_mean) <= 0.05 * r64.q_err
