@@ -168,11 +168,24 @@ int qqmc_plan_kernel_count(const qqmc_plan *plan);
 int qqmc_plan_timing(const qqmc_plan *plan, double *kernel_ms, double *total_ms);
 
 /*
+ * Partial sums of single chunks of the last launch (after qqmc_plan_results):
+ * for item `item` (caller order), shifted sequence `shift` and chunks
+ * chunk[0..count-1] (chunk c holds Sobol' indices first_index + 32c ..
+ * first_index + 32c + 31 of that sequence), out[4*q..4*q+3] = (sum.re,
+ * sum.im, compensation.re, compensation.im) of w_i c_n(u_i) over the chunk's
+ * in-domain points, as the determinant kernel wrote it.  For checking a
+ * full-size launch point by point against a reference.  E_INVAL on bad
+ * indices.
+ */
+int qqmc_plan_chunk_sums(const qqmc_plan *plan, int item, int shift, const int64_t *chunk, int count, double *out);
+
+/*
  * Tuning of the determinant kernel (the autotuner writes these): for
  * each order, the number of warps per block and the number of vertices
  * resolved per lane in the flat (per-lane) phase, 2..5 (the levels between
  * the depth-first tree leaf, 5 vertices, and the flat phase are expanded
- * breadth first).  Values <= 0 restore the built-in defaults.  Applies to
+ * breadth first), or 1 for one point per lane (orders <= 4: each lane runs
+ * the whole Keldysh sum of its own point).  Values <= 0 restore the built-in defaults.  Applies to
  * plans created afterwards; a batched plan uses the tuning of its highest
  * order.
  */

@@ -23,18 +23,24 @@ CANDIDATES = {
     Q.QQMC_PREC_FP64: [(w, f) for w in (1, 2, 3, 4) for f in (2, 3, 5)],
     Q.QQMC_PREC_MIXED: [(w, f) for w in (2, 4, 6, 8) for f in (2, 3, 4, 5)],
 }
+# flat 1 = one point per lane (orders <= 4)
+LANE_CANDIDATES = {
+    Q.QQMC_PREC_FP64: [(w, 1) for w in (1, 2, 4)],
+    Q.QQMC_PREC_MIXED: [(w, 1) for w in (2, 4, 8)],
+}
 
 
 def _points_for(order: int, precision: int) -> int:
-    # every SM busy several times over, each candidate timed in well under a second
-    base = 2 ** 15 if precision == Q.QQMC_PREC_MIXED else 2 ** 13
-    return max(2 ** 10, base >> max(0, order - 8))
+    # Large enough that the grid drains the way a full batch does (tens of
+    # chunks per resident warp), small enough to time each shape in ~0.1 s.
+    base = 2 ** 17 if precision == Q.QQMC_PREC_MIXED else 2 ** 15
+    return max(2 ** 12, base >> max(0, order - 7))
 
 
 def time_shape(pr: int, order: int, precision: int, wpb: int, flat: int, reps: int = 2) -> float:
     Q.qqmc_set_tuning(precision, order, wpb, flat)
     N = _points_for(order, precision)
-    plan = Q.Plan([(pr, m, 8, N) for m in range(1, order + 1)], precision)
+    plan = Q.Plan([(pr, m, 16, N) for m in range(1, order + 1)], precision)
     try:
         plan.launch()
         plan.results()
@@ -58,7 +64,8 @@ def tune(orders=range(1, Q.QQMC_MAX_ORDER + 1), precisions=(Q.QQMC_PREC_FP64, Q.
             table[prec] = {}
             for n in orders:
                 results = []
-                for wpb, flat in CANDIDATES[prec]:
+                cands = CANDIDATES[prec] + (LANE_CANDIDATES[prec] if n <= 4 else [])
+                for wpb, flat in cands:
                     try:
                         ms = time_shape(pr, n, prec, wpb, flat)
                     except Q.QQMCError:

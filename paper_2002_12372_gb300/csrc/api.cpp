@@ -3,6 +3,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -45,6 +46,7 @@ static Tuning default_tuning(int precision, int order) {
     // lane in registers (shared-memory traffic of cooperative updates is the
     // FP32 bound).
     t.flat = precision == QQMC_PREC_FP64 ? 2 : 5;
+    t.flat_min = t.flat;
     t.warps_per_block = precision == QQMC_PREC_FP64 ? 2 : 4;
     return t;
 }
@@ -175,8 +177,9 @@ extern "C" int qqmc_problem_tables(const qqmc_problem *pr, double *gl, double *g
 
 // ---------------------------------------------------------------- plans
 struct qqmc_plan {
-    std::vector<qqmc_item> items;
-    std::vector<ItemDev> hitems;
+    std::vector<qqmc_item> items;   // caller order
+    std::vector<ItemDev> hitems;    // device order: highest order first (longest work first)
+    std::vector<int> perm;          // device position -> caller index
     int precision = 0;
     int n_max = 0;
     long long total_chunks = 0;
@@ -246,7 +249,7 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         pl->total_shifts += it.n_shifts;
     }
     pl->total_chunks = (long long)chunk_total;
-    pl->tune = get_tuning(precision, pl->n_max);
+    pl->tune = get_tuning(precision, pl->n_max);  // warps per block of the highest order
     cudaError_t e = cudaMalloc(&pl->d_items, sizeof(ItemDev) * n_items);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_shifts, sizeof(uint32_t) * shift_words_total);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_partials, sizeof(double) * 4 * chunk_total);
@@ -258,17 +261,26 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         free_plan(pl);
         return set_error(QQMC_E_NOMEM, std::string("device allocation of the plan failed: ") + cudaGetErrorString(e));
     }
+    // Device order: highest order first, then more points first, so the
+    // longest items start early and the persistent grid drains evenly.
+    pl->perm.resize(n_items);
+    for (int i = 0; i < n_items; ++i) pl->perm[i] = i;
+    std::stable_sort(pl->perm.begin(), pl->perm.end(), [&](int a, int b) {
+        if (items[a].order != items[b].order) return items[a].order > items[b].order;
+        return items[a].n_points > items[b].n_points;
+    });
+    int flat_max = 0, flat_min = 99;
     std::vector<uint32_t> hs(shift_words_total);
     size_t so = 0, co = 0;
     pl->hitems.resize(n_items);
-    for (int i = 0; i < n_items; ++i) {
-        const qqmc_item &it = items[i];
+    for (int q = 0; q < n_items; ++q) {
+        const qqmc_item &it = items[pl->perm[q]];
         const qqmc_problem *pr = it.problem;
         if (it.shift_words)
             memcpy(hs.data() + so, it.shift_words, sizeof(uint32_t) * it.n_shifts * it.order);
         else
             shift_words(pr->params.seed, it.n_shifts, it.order, hs.data() + so);
-        ItemDev &d = pl->hitems[i];
+        ItemDev &d = pl->hitems[q];
         d.table = pr->d_table;
         d.table32 = pr->d_table32;
         d.shifts = pl->d_shifts + so;
@@ -288,9 +300,21 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         d.n_shifts = it.n_shifts;
         d.L = pr->L;
         d.chunks_per_shift = (int)cps;
+        // one point per lane where this order's tuning asks for it (orders <= 4);
+        // every other item uses the plan-wide flat depth set below
+        d.flat = (it.order <= 4 && get_tuning(precision, it.order).flat == 1) ? 1 : 0;
         so += (size_t)it.n_shifts * it.order;
         co += cps * it.n_shifts;
     }
+    // Plan-wide flat depth of the warp-per-point items: the tuning of the
+    // highest order (one kernel instantiation, shared memory sized for it).
+    int plan_flat = pl->tune.flat >= 2 ? pl->tune.flat : 2;
+    for (ItemDev &d : pl->hitems)
+        if (d.flat != 1) d.flat = plan_flat;
+    pl->tune.flat = plan_flat;
+    pl->tune.flat_min = plan_flat;
+    (void)flat_max;
+    (void)flat_min;
     e = cudaMemcpy(pl->d_shifts, hs.data(), sizeof(uint32_t) * shift_words_total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(pl->d_items, pl->hitems.data(), sizeof(ItemDev) * n_items, cudaMemcpyHostToDevice);
@@ -416,16 +440,42 @@ extern "C" int qqmc_plan_results(qqmc_plan *pl, qqmc_result *results, double *pe
     if (e == cudaSuccess)
         e = cudaMemcpy(cnt.data(), pl->d_counts, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "result download");
+    // per-shift outputs are in device order; caller offsets for per_shift
+    const size_t n_items = pl->items.size();
+    std::vector<size_t> user_off(n_items + 1, 0);
+    for (size_t i = 0; i < n_items; ++i) user_off[i + 1] = user_off[i] + pl->items[i].n_shifts;
     size_t g = 0;
-    for (size_t i = 0; i < pl->items.size(); ++i) {
+    for (size_t q = 0; q < n_items; ++q) {
+        const int i = pl->perm[q];
         const qqmc_item &it = pl->items[i];
         if (results) finish_result(it, S.data() + 2 * g, cnt.data() + g, ms, &results[i]);
         if (per_shift)
             for (int k = 0; k < it.n_shifts; ++k) {
-                per_shift[2 * (g + k)] = S[2 * (g + k)] / (double)it.n_points;
-                per_shift[2 * (g + k) + 1] = S[2 * (g + k) + 1] / (double)it.n_points;
+                per_shift[2 * (user_off[i] + k)] = S[2 * (g + k)] / (double)it.n_points;
+                per_shift[2 * (user_off[i] + k) + 1] = S[2 * (g + k) + 1] / (double)it.n_points;
             }
         g += it.n_shifts;
+    }
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_plan_chunk_sums(const qqmc_plan *pl, int item, int shift, const int64_t *chunk, int count,
+                                    double *out) {
+    if (!pl || !pl->launched) return set_error(QQMC_E_INVAL, "plan is NULL or was not launched");
+    if (item < 0 || item >= (int)pl->items.size() || !chunk || !out || count < 0)
+        return set_error(QQMC_E_INVAL, "qqmc_plan_chunk_sums: bad item or buffers");
+    int q = 0;
+    while (pl->perm[q] != item) ++q;
+    const ItemDev &d = pl->hitems[q];
+    if (shift < 0 || shift >= d.n_shifts) return set_error(QQMC_E_INVAL, "qqmc_plan_chunk_sums: bad shift");
+    cudaError_t e = cudaEventSynchronize(pl->ev1);
+    if (e != cudaSuccess) return cuda_error(e, "plan execution");
+    for (int i = 0; i < count; ++i) {
+        if (chunk[i] < 0 || chunk[i] >= d.chunks_per_shift)
+            return set_error(QQMC_E_INVAL, "qqmc_plan_chunk_sums: chunk index out of range");
+        const double *src = d.partials + 4 * ((size_t)shift * d.chunks_per_shift + (size_t)chunk[i]);
+        e = cudaMemcpy(out + 4 * i, src, 4 * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_error(e, "chunk download");
     }
     return QQMC_OK;
 }
@@ -463,10 +513,11 @@ extern "C" int qqmc_set_tuning(int precision, int order, int warps_per_block, in
         g_tune_set[p][order] = false;
         return QQMC_OK;
     }
-    if (warps_per_block > 16 || flat_vertices < 2 || flat_vertices > 5)
-        return set_error(QQMC_E_INVAL, "qqmc_set_tuning: warps_per_block in 1..16, flat_vertices in 2..5");
+    if (warps_per_block > 16 || flat_vertices > 5)
+        return set_error(QQMC_E_INVAL, "qqmc_set_tuning: warps_per_block in 1..16, flat_vertices in 1..5");
     g_tune[p][order].warps_per_block = warps_per_block;
     g_tune[p][order].flat = flat_vertices;
+    g_tune[p][order].flat_min = flat_vertices;
     g_tune_set[p][order] = true;
     return QQMC_OK;
 }
@@ -569,7 +620,10 @@ extern "C" int qqmc_integrand(const qqmc_problem *pr, int order, uint64_t count,
     it.h = pr->h;
     it.L = pr->L;
     it.order = order;
-    if (e == cudaSuccess) e = launch_integrand(it, count, d_u.p, d_out.p, precision, get_tuning(precision, order), 0);
+    Tuning tu = get_tuning(precision, order);
+    if (tu.flat < 2) tu.flat = tu.flat_min = 2;  // the check kernel runs one warp per point
+    it.flat = tu.flat;
+    if (e == cudaSuccess) e = launch_integrand(it, count, d_u.p, d_out.p, precision, tu, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out, d_out.p, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrand");
     return QQMC_OK;

@@ -190,7 +190,10 @@ __host__ __device__ inline size_t stack_entries(int n_max) {
         size_t S = 2 * (size_t)(R0 - l) + 2;
         tot += S * S;
     }
-    return tot;
+    // one-point-per-lane mode (orders <= 4) reuses this region: 32 level-0 matrices
+    const int nl = n_max < 4 ? n_max : 4;
+    const size_t lane = 32 * (size_t)(2 * nl) * (2 * nl);
+    return tot > lane ? tot : lane;
 }
 
 // entries of the breadth-first levels below a tree leaf of Rleaf vertices
@@ -263,13 +266,13 @@ __device__ __forceinline__ cx<R> G(const WarpSmem<R> &ws, int NP, cx<R> d, int v
 // q-th remaining vertex).  The first elimination is fused with the gather;
 // the rest runs on an (F+1) x (F+1) register matrix whose rows and columns
 // are {copy a_1 = 0, copy a_1 = 1, remaining vertices}.
-template <class R, int F>
+template <class R, int F, int STRIDE = 1>
 __device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &acc_re,
                                            Acc<R> &acc_im) {
     constexpr int S = 2 * F + 2;
     if (F == 0) {
         cx<R> dd = cmul(detD, detD);
-        cx<R> diff = mk<R>(E[0].re - E[S + 1].re, E[0].im - E[S + 1].im);
+        cx<R> diff = mk<R>(E[0].re - E[(S + 1) * STRIDE].re, E[0].im - E[(S + 1) * STRIDE].im);
         cx<R> term = cmul(dd, diff);
         if (parity) term = mk<R>(-term.re, -term.im);
         acc_re.add(term.re);
@@ -283,20 +286,20 @@ __device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parit
 #pragma unroll
     for (int q = 1; q < F; ++q) idx[q + 1] = 2 + 2 * q + ((path >> q) & 1);
     const int p0 = 2 + (path & 1);
-    cx<R> piv = E[p0 * S + p0];
+    cx<R> piv = E[(p0 * S + p0) * STRIDE];
     detD = cmul(detD, piv);
     cx<R> ip = crcp(piv);
     cx<R> m[M][M];
     cx<R> prow[M];
 #pragma unroll
-    for (int y = 0; y < M; ++y) prow[y] = cmul(E[p0 * S + idx[y]], ip);
+    for (int y = 0; y < M; ++y) prow[y] = cmul(E[(p0 * S + idx[y]) * STRIDE], ip);
 #pragma unroll
     for (int x = 0; x < M; ++x) {
-        cx<R> cf = E[idx[x] * S + p0];
+        cx<R> cf = E[(idx[x] * S + p0) * STRIDE];
 #pragma unroll
         for (int y = 0; y < M; ++y) {
             if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
-            m[x][y] = cfms(E[idx[x] * S + idx[y]], cf, prow[y]);
+            m[x][y] = cfms(E[(idx[x] * S + idx[y]) * STRIDE], cf, prow[y]);
         }
     }
 #pragma unroll
@@ -420,9 +423,9 @@ __device__ __forceinline__ double warp_total(Acc<R> acc) {
 // Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
 // Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
-template <class R, int RF>
+template <class R, int RFMAX>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d,
-                                  const typename TabT<R>::V *tab, double inv_h, double s0, int L, int lane) {
+                                  const typename TabT<R>::V *tab, double inv_h, double s0, int L, int RF, int lane) {
     const int NP = n_max + 1;
     // 1. pair interpolation, 0 <= j < k <= n
     const int npairs = n * (n + 1) / 2;
@@ -547,11 +550,93 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         if (active) {
             const cx<R> *En = E + (size_t)node * S * S;
             const int parity = tparity ^ (__popc(node) & 1);
-            flat_dispatch<R, RF>(Rf, En, ndet[B > 0 ? node : 0], parity, path, ar, ai);
+            flat_dispatch<R, RFMAX>(Rf, En, ndet[B > 0 ? node : 0], parity, path, ar, ai);
         }
         __syncwarp();
     }
     return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+}
+
+// One point per lane (small orders): the lane interpolates its own pairs
+// into registers, writes the level-0 matrix (vertex 1 eliminated, both a_1
+// kept) into its own strided shared-memory slice, and resolves every choice
+// path of the remaining N-1 vertices with the flat phase.
+constexpr int kLaneMaxOrder = 4;
+
+template <class R, int N>
+__device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d, const typename TabT<R>::V *tab,
+                                                       double inv_h, double s0, int L, cx<R> *E) {
+    constexpr int S0 = 2 * N;
+    cx<R> P[N + 1][N + 1], Rr[N + 1][N + 1];
+    double uu[N + 1];
+#pragma unroll
+    for (int m = 0; m <= N; ++m) uu[m] = u[m];
+#pragma unroll
+    for (int k = 1; k <= N; ++k)
+#pragma unroll
+        for (int j = 0; j < k; ++j) interp_pair<R>(tab, inv_h, s0, L, uu[j] - uu[k], Rr[j][k], P[j][k]);
+    const cx<R> id = crcp(d);
+    const cx<R> r1[2] = {P[0][1], Rr[0][1]};
+    const cx<R> c1d[2] = {cmul(nconj(Rr[0][1]), id), cmul(nconj(P[0][1]), id)};
+#pragma unroll
+    for (int bx = 0; bx < N; ++bx) {
+        cx<R> left[2];
+        if (bx == 0) {
+            left[0] = r1[0];
+            left[1] = r1[1];
+        } else {
+            left[0] = nconj(Rr[1][bx + 1]);
+            left[1] = nconj(P[1][bx + 1]);
+        }
+#pragma unroll
+        for (int by = 0; by < N; ++by) {
+            cx<R> base[2][2], right[2];
+            if (by == 0) {
+                right[0] = c1d[0];
+                right[1] = c1d[1];
+            } else {
+                right[0] = cmul(P[1][by + 1], id);
+                right[1] = cmul(Rr[1][by + 1], id);
+            }
+            if (bx == by) {
+                base[0][0] = base[0][1] = base[1][0] = base[1][1] = d;
+            } else if (bx == 0) {
+                base[0][0] = base[1][0] = P[0][by + 1];
+                base[0][1] = base[1][1] = Rr[0][by + 1];
+            } else if (by == 0) {
+                base[0][0] = base[0][1] = nconj(Rr[0][bx + 1]);
+                base[1][0] = base[1][1] = nconj(P[0][bx + 1]);
+            } else if (bx < by) {
+                base[0][0] = base[1][0] = P[bx + 1][by + 1];
+                base[0][1] = base[1][1] = Rr[bx + 1][by + 1];
+            } else {
+                base[0][0] = base[0][1] = nconj(Rr[by + 1][bx + 1]);
+                base[1][0] = base[1][1] = nconj(P[by + 1][bx + 1]);
+            }
+#pragma unroll
+            for (int x = 0; x < 2; ++x)
+#pragma unroll
+                for (int y = 0; y < 2; ++y)
+                    E[((2 * bx + x) * S0 + 2 * by + y) * 32] = cfms(base[x][y], left[x], right[y]);
+        }
+    }
+    Acc<R> ar, ai;
+    ar.init();
+    ai.init();
+    for (int path = 0; path < (1 << (N - 1)); ++path) flat_phase<R, N - 1, 32>(E, d, 0, path, ar, ai);
+    return mk<double>((double)ar.s + (double)ar.c, (double)ai.s + (double)ai.c);
+}
+
+template <class R>
+__device__ __forceinline__ cx<double> lane_keldysh_dispatch(int n, const double *u, cx<R> d,
+                                                            const typename TabT<R>::V *tab, double inv_h, double s0,
+                                                            int L, cx<R> *E) {
+    switch (n) {
+        case 1: return lane_keldysh_sum<R, 1>(u, d, tab, inv_h, s0, L, E);
+        case 2: return lane_keldysh_sum<R, 2>(u, d, tab, inv_h, s0, L, E);
+        case 3: return lane_keldysh_sum<R, 3>(u, d, tab, inv_h, s0, L, E);
+        default: return lane_keldysh_sum<R, 4>(u, d, tab, inv_h, s0, L, E);
+    }
 }
 
 // i^n * z
@@ -593,13 +678,13 @@ __device__ __forceinline__ void warp_gap(float, uint32_t y, double tau, double &
 // ----------------------------------------------------------------------------
 // Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
 // ----------------------------------------------------------------------------
-template <class R, int RF>
+template <class R, int RFMAX>
 __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
-                              unsigned long long *counter, int n_max) {
+                              unsigned long long *counter, int n_max, int rf_min) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF), n_max, RF);
+    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, rf_min), n_max, rf_min);
     const int NU = n_max + 1;
     while (true) {
         unsigned long long c = 0;
@@ -643,10 +728,20 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
         const double inv_h = 1.0 / I.h;
         const double s0 = I.T * inv_h;
         unsigned mm = mask;
+        if (I.flat == 1 && n <= kLaneMaxOrder) {  // one point per lane
+            if (inside) {
+                cx<double> s = lane_keldysh_dispatch<R>(n, ws.upt + lane * NU, d, tab, inv_h, s0, I.L, ws.stack + lane);
+                cx<double> cval = times_i_pow(s, n);
+                myval = mk<double>(w * cval.re, w * cval.im);
+            }
+            mm = 0;
+            __syncwarp();
+        }
         while (mm) {
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
-            cx<double> s = keldysh_sum<R, RF>(ws, ws.upt + src * NU, n, n_max, d, tab, inv_h, s0, I.L, lane);
+            const int rf = I.flat < rf_min ? rf_min : (I.flat > RFMAX ? RFMAX : I.flat);
+            cx<double> s = keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, tab, inv_h, s0, I.L, rf, lane);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -764,7 +859,7 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     __syncwarp();
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
     const double inv_h = 1.0 / I.h;
-    cx<double> s = keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, item_table<R>(I), inv_h, I.T * inv_h, I.L, lane);
+    cx<double> s = keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, item_table<R>(I), inv_h, I.T * inv_h, I.L, RF, lane);
     if (lane == 0) {
         cx<double> cval = times_i_pow(s, n);
         out[2 * q] = cval.re;
@@ -916,15 +1011,15 @@ int launch_gf_table(const Problem &pr, cudaStream_t s) {
 }
 
 size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
-    size_t per = precision == QQMC_PREC_FP64 ? warp_smem_bytes<double>(n_max, tune.flat)
-                                             : warp_smem_bytes<float>(n_max, tune.flat);
+    size_t per = precision == QQMC_PREC_FP64 ? warp_smem_bytes<double>(n_max, tune.flat_min)
+                                             : warp_smem_bytes<float>(n_max, tune.flat_min);
     return per * tune.warps_per_block;
 }
 
 template <class R, int F>
 static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
-                                   unsigned long long *d_counter, int n_max, int wpb, cudaStream_t s) {
-    size_t smem = warp_smem_bytes<R>(n_max, F) * wpb;
+                                   unsigned long long *d_counter, int n_max, int wpb, int rf_min, cudaStream_t s) {
+    size_t smem = warp_smem_bytes<R>(n_max, rf_min) * wpb;
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(detsum_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -938,26 +1033,28 @@ static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long lon
     long long grid = (long long)sms * per_sm;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    detsum_kernel<R, F><<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max);
+    detsum_kernel<R, F><<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max,
+                                                                rf_min);
     return cudaGetLastError();
 }
 
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                           int n_max, int precision, const Tuning &tune, cudaStream_t s) {
     const int wpb = tune.warps_per_block;
+    const int rf_min = tune.flat_min < 2 ? 2 : (tune.flat_min > tune.flat ? tune.flat : tune.flat_min);
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
-            case 2: return launch_detsum_t<double, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
-            case 3: return launch_detsum_t<double, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
-            case 4: return launch_detsum_t<double, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
-            default: return launch_detsum_t<double, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+            case 2: return launch_detsum_t<double, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+            case 3: return launch_detsum_t<double, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+            case 4: return launch_detsum_t<double, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+            default: return launch_detsum_t<double, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
         }
     }
     switch (tune.flat) {
-        case 2: return launch_detsum_t<float, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
-        case 3: return launch_detsum_t<float, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
-        case 4: return launch_detsum_t<float, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
-        default: return launch_detsum_t<float, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, s);
+        case 2: return launch_detsum_t<float, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+        case 3: return launch_detsum_t<float, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+        case 4: return launch_detsum_t<float, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+        default: return launch_detsum_t<float, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
     }
 }
 

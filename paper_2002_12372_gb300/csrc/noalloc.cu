@@ -100,6 +100,10 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     it.n_shifts = n_shifts;
     it.L = P->L;
     it.chunks_per_shift = (int)cps;
+    Tuning tu = get_tuning(precision, order);
+    it.flat = tu.flat;
+    if (it.flat < 2 && order > 4) it.flat = 2;
+    if (tu.flat < 2) tu.flat = tu.flat_min = 2;
 
     ItemDev *d_item = reinterpret_cast<ItemDev *>(base + kItemOff);
     unsigned long long *d_counter = reinterpret_cast<unsigned long long *>(base + kCounterOff);
@@ -108,8 +112,7 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     cudaError_t e = cudaMemcpyAsync(d_item, &it, sizeof(ItemDev), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-        e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision,
-                          get_tuning(precision, order), s);
+        e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, s);
     if (e == cudaSuccess) e = launch_reduce(d_item, 1, n_shifts, d_sums, counts, s);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrate_noalloc");
     return QQMC_OK;

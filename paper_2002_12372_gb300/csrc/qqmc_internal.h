@@ -38,11 +38,13 @@ struct ItemDev {
     long long n_points;
     long long chunk_begin;   // first global chunk of this item
     int order, n_shifts, L, chunks_per_shift;
+    int flat;                // vertices resolved per lane for this item (its order's tuning)
 };
 
 struct Tuning {
     int warps_per_block;
-    int flat;
+    int flat;      // largest flat depth of the launch (kernel template)
+    int flat_min;  // smallest flat depth (sizes the breadth-first buffers)
 };
 
 // Error reporting (thread-local message).

@@ -39,7 +39,7 @@ EXPORTED = [
     "qqmc_plan_kernel_count", "qqmc_plan_timing", "qqmc_set_tuning", "qqmc_get_tuning", "qqmc_direction_numbers",
     "qqmc_shift_words", "qqmc_sobol_points", "qqmc_warp_points", "qqmc_integrand", "qqmc_server_create",
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
-    "qqmc_integrate_noalloc",
+    "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums",
 ]
 
 
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
         "qqmc_server_destroy": [vp],
         "qqmc_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "qqmc_integrate_noalloc": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
+        "qqmc_plan_chunk_sums": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -241,6 +242,16 @@ class Plan:
         _check(load().qqmc_plan_timing(ctypes.c_void_p(self.handle), ctypes.byref(k), ctypes.byref(a)),
                "qqmc_plan_timing")
         return k.value, a.value
+
+    def chunk_sums(self, item: int, shift: int, chunks) -> np.ndarray:
+        """Complex per-chunk sums (sum + compensation) of the last launch."""
+        ch = np.ascontiguousarray(np.asarray(chunks, dtype=np.int64))
+        out = np.zeros(4 * ch.size)
+        _check(load().qqmc_plan_chunk_sums(ctypes.c_void_p(self.handle), item, shift,
+                                           ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ch.size,
+                                           _ptr(out, ctypes.c_double)), "qqmc_plan_chunk_sums")
+        o = out.reshape(-1, 4)
+        return (o[:, 0] + o[:, 2]) + 1j * (o[:, 1] + o[:, 3])
 
     def kernel_count(self) -> int:
         return load().qqmc_plan_kernel_count(ctypes.c_void_p(self.handle))

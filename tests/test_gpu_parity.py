@@ -116,7 +116,9 @@ def test_integration_fp64_matches_oracle(Q, W, oracle, order, N, K):
 
 
 def test_batched_plan_equals_single_runs(Q, W, oracle):
-    """Uneven orders and point counts in one persistent launch: identical sums."""
+    """Uneven orders and point counts in one persistent launch: the same sums
+    (bit-identical when every order runs the same kernel shape, as with the
+    built-in tuning here; to rounding otherwise)."""
     T = 10.0
     pr, tabs = _problem(Q, W, seed=21, T=T)
     try:
@@ -206,3 +208,54 @@ def test_integration_mixed_within_stated_bound_of_fp64(Q, W, oracle, order, N):
         Q.qqmc_destroy_problem(pr)
     assert np.all(np.abs(S32 - S64) <= 1e-4 * np.abs(S64)), np.abs(S32 - S64) / np.abs(S64)
     assert abs(r32.q_mean - r64.q_mean) <= 0.05 * r64.q_err
+
+
+@pytest.mark.slow
+def test_full_size_bench_launch_sampled_chunks(Q, W, oracle):
+    """The benchmark's launch shape at full size (three problems, n = 1..10, N = 2^20 x 32 shifts,
+    one persistent launch with the installed tuning) on identical synthetic tables: the in-domain
+    counts are exact, and sampled chunks of 32 points match the oracle's sums over the same
+    indices (FP64, relative 1e-10)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2002_12372_gb300 import autotune
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    t = autotune.load(os.path.join(root, "paper_2002_12372_gb300", "tuning_gb300.json"))
+    if t:
+        autotune.install(t)
+    N, K, T, L = 2 ** 20, 32, 10.0, 4096
+    tables = [W.synthetic_tables(51 + j, L, T) for j in range(3)]
+    probs = [Q.qqmc_create_problem_tables(Q.make_params(t_max=T, n_table=L), gl, gg, g0)
+             for gl, gg, g0, _ in tables]
+    rng = np.random.default_rng(5)
+    V = oracle.sobol_direction_numbers(12)
+    try:
+        items, shifts = [], {}
+        for j, pr in enumerate(probs):
+            for n in range(1, 11):
+                sw = W.shift_words(7000 + 16 * j + n, K, n)
+                shifts[(j, n)] = sw
+                items.append((pr, n, K, N, sw))
+        plan = Q.Plan(items, Q.QQMC_PREC_FP64)
+        plan.launch()
+        res = plan.results()
+        for idx, (r, S) in enumerate(res):
+            j, n = divmod(idx, 10)
+            n += 1
+            sw = shifts[(j, n)]
+            if j == 0 and n in (6, 10):
+                with ThreadPoolExecutor(16) as ex:
+                    cnt = ex.map(lambda k: int(oracle.warp(n, 0, N, V, sw[k], T, 1.0)[2].sum()), range(K))
+                assert r.n_in_domain == sum(cnt)
+            gl, gg, g0, _ = tables[j]
+            k = int(rng.integers(K))
+            chunks = rng.integers(0, N // 32, size=2 if n >= 9 else 4)
+            got = plan.chunk_sums(idx, k, chunks)
+            for c, g in zip(chunks, got):
+                S0, _ = oracle.estimate(n, 32, sw[k:k + 1], T, 1.0, (gl, gg, g0), T, i0=int(c) * 32, threads=1)
+                ref = S0[0] * 32
+                assert abs(g - ref) <= 1e-10 * abs(ref), (n, c, g, ref)
+        plan.close()
+    finally:
+        for pr in probs:
+            Q.qqmc_destroy_problem(pr)
