@@ -87,6 +87,13 @@ def install(table) -> None:
             Q.qqmc_set_tuning(int(prec), int(n), int(wpb), int(flat))
 
 
+def reset() -> None:
+    """Restore the built-in defaults for every (precision, order)."""
+    for prec in (Q.QQMC_PREC_FP64, Q.QQMC_PREC_MIXED):
+        for n in range(1, Q.QQMC_MAX_ORDER + 1):
+            Q.qqmc_set_tuning(prec, n, 0, 0)
+
+
 def save(table, path: str) -> None:
     import torch
     name = torch.cuda.get_device_name(0)

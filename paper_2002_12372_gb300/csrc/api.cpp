@@ -180,6 +180,8 @@ struct qqmc_plan {
     std::vector<qqmc_item> items;   // caller order
     std::vector<ItemDev> hitems;    // device order: highest order first (longest work first)
     std::vector<int> perm;          // device position -> caller index
+    int n_warp = 0;                 // items [0, n_warp) run one warp per point, the rest one lane per point
+    long long chunks_warp = 0, chunks_lane = 0;
     int precision = 0;
     int n_max = 0;
     long long total_chunks = 0;
@@ -254,27 +256,37 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_shifts, sizeof(uint32_t) * shift_words_total);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_partials, sizeof(double) * 4 * chunk_total);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_inside, sizeof(unsigned int) * chunk_total);
-    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counter, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_out, sizeof(double) * 2 * pl->total_shifts);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_counts, sizeof(unsigned long long) * pl->total_shifts);
     if (e != cudaSuccess) {
         free_plan(pl);
         return set_error(QQMC_E_NOMEM, std::string("device allocation of the plan failed: ") + cudaGetErrorString(e));
     }
-    // Device order: highest order first, then more points first, so the
-    // longest items start early and the persistent grid drains evenly.
+    // Device order: the warp-per-point items, then the one-point-per-lane items
+    // (orders <= 4 whose tuning asks for it); within each group highest order
+    // first, then more points first, so the longest items start early and the
+    // persistent grid drains evenly.  Each group has its own chunk numbering.
+    auto lane_mode = [&](int i) {
+        return items[i].order <= kLaneMaxOrder && get_tuning(precision, items[i].order).flat == 1;
+    };
     pl->perm.resize(n_items);
     for (int i = 0; i < n_items; ++i) pl->perm[i] = i;
     std::stable_sort(pl->perm.begin(), pl->perm.end(), [&](int a, int b) {
+        if (lane_mode(a) != lane_mode(b)) return !lane_mode(a);
         if (items[a].order != items[b].order) return items[a].order > items[b].order;
         return items[a].n_points > items[b].n_points;
     });
-    int flat_max = 0, flat_min = 99;
+    // plan-wide flat depth of the warp-per-point items: the highest order's tuning
+    const int plan_flat = pl->tune.flat >= 2 ? pl->tune.flat : 2;
     std::vector<uint32_t> hs(shift_words_total);
     size_t so = 0, co = 0;
+    long long cw = 0, cl = 0;
     pl->hitems.resize(n_items);
     for (int q = 0; q < n_items; ++q) {
-        const qqmc_item &it = items[pl->perm[q]];
+        const int ci = pl->perm[q];
+        const qqmc_item &it = items[ci];
+        const bool lm = lane_mode(ci);
         const qqmc_problem *pr = it.problem;
         if (it.shift_words)
             memcpy(hs.data() + so, it.shift_words, sizeof(uint32_t) * it.n_shifts * it.order);
@@ -295,26 +307,26 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         d.h = pr->h;
         d.first_index = (long long)it.first_index;
         d.n_points = (long long)it.n_points;
-        d.chunk_begin = (long long)co;
         d.order = it.order;
         d.n_shifts = it.n_shifts;
         d.L = pr->L;
         d.chunks_per_shift = (int)cps;
-        // one point per lane where this order's tuning asks for it (orders <= 4);
-        // every other item uses the plan-wide flat depth set below
-        d.flat = (it.order <= 4 && get_tuning(precision, it.order).flat == 1) ? 1 : 0;
+        d.flat = lm ? 1 : plan_flat;
+        if (lm) {
+            d.chunk_begin = cl;
+            cl += (long long)cps * it.n_shifts;
+        } else {
+            d.chunk_begin = cw;
+            cw += (long long)cps * it.n_shifts;
+            ++pl->n_warp;
+        }
         so += (size_t)it.n_shifts * it.order;
         co += cps * it.n_shifts;
     }
-    // Plan-wide flat depth of the warp-per-point items: the tuning of the
-    // highest order (one kernel instantiation, shared memory sized for it).
-    int plan_flat = pl->tune.flat >= 2 ? pl->tune.flat : 2;
-    for (ItemDev &d : pl->hitems)
-        if (d.flat != 1) d.flat = plan_flat;
+    pl->chunks_warp = cw;
+    pl->chunks_lane = cl;
     pl->tune.flat = plan_flat;
     pl->tune.flat_min = plan_flat;
-    (void)flat_max;
-    (void)flat_min;
     e = cudaMemcpy(pl->d_shifts, hs.data(), sizeof(uint32_t) * shift_words_total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(pl->d_items, pl->hitems.data(), sizeof(ItemDev) * n_items, cudaMemcpyHostToDevice);
@@ -331,12 +343,20 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
 }
 
 static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
-    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (timed && (e = cudaEventRecord(pl->ek0, s)) != cudaSuccess) return e;
-    e = launch_detsum(pl->d_items, (int)pl->items.size(), pl->total_chunks, pl->d_counter, pl->n_max, pl->precision,
-                      pl->tune, s);
-    if (e != cudaSuccess) return e;
+    if (pl->n_warp > 0) {
+        int nmax_warp = 0;
+        for (int q = 0; q < pl->n_warp; ++q) nmax_warp = pl->hitems[q].order > nmax_warp ? pl->hitems[q].order : nmax_warp;
+        e = launch_detsum(pl->d_items, pl->n_warp, pl->chunks_warp, pl->d_counter, nmax_warp, pl->precision, pl->tune, s);
+        if (e != cudaSuccess) return e;
+    }
+    const int n_lane = (int)pl->items.size() - pl->n_warp;
+    if (n_lane > 0) {
+        e = launch_lane(pl->d_items + pl->n_warp, n_lane, pl->chunks_lane, pl->d_counter + 1, pl->precision, s);
+        if (e != cudaSuccess) return e;
+    }
     if (timed && (e = cudaEventRecord(pl->ek1, s)) != cudaSuccess) return e;
     return launch_reduce(pl->d_items, (int)pl->items.size(), pl->total_shifts, pl->d_out, pl->d_counts, s);
 }
@@ -385,7 +405,10 @@ extern "C" int qqmc_plan_launch(qqmc_plan *pl, void *stream, int use_graph) {
     return QQMC_OK;
 }
 
-extern "C" int qqmc_plan_kernel_count(const qqmc_plan *pl) { return pl ? 2 : 0; }
+extern "C" int qqmc_plan_kernel_count(const qqmc_plan *pl) {
+    if (!pl) return 0;
+    return 1 + (pl->n_warp > 0 ? 1 : 0) + ((int)pl->items.size() > pl->n_warp ? 1 : 0);
+}
 
 extern "C" int qqmc_plan_timing(const qqmc_plan *pl, double *kernel_ms, double *total_ms) {
     if (!pl || !pl->launched) return set_error(QQMC_E_INVAL, "plan is NULL or was not launched");

@@ -190,10 +190,7 @@ __host__ __device__ inline size_t stack_entries(int n_max) {
         size_t S = 2 * (size_t)(R0 - l) + 2;
         tot += S * S;
     }
-    // one-point-per-lane mode (orders <= 4) reuses this region: 32 level-0 matrices
-    const int nl = n_max < 4 ? n_max : 4;
-    const size_t lane = 32 * (size_t)(2 * nl) * (2 * nl);
-    return tot > lane ? tot : lane;
+    return tot;
 }
 
 // entries of the breadth-first levels below a tree leaf of Rleaf vertices
@@ -557,16 +554,21 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
 }
 
-// One point per lane (small orders): the lane interpolates its own pairs
-// into registers, writes the level-0 matrix (vertex 1 eliminated, both a_1
-// kept) into its own strided shared-memory slice, and resolves every choice
-// path of the remaining N-1 vertices with the flat phase.
-constexpr int kLaneMaxOrder = 4;
+// One point per lane (small orders), registers only: the lane interpolates
+// its own pairs, and for every choice path of vertices 2..N builds the path's
+// (N+1) x (N+1) matrix -- rows/columns {copy a_1 = 0, copy a_1 = 1, vertices
+// 2..N with their chosen Keldysh index}, vertex 1 already eliminated -- from
+// the pair values, then eliminates vertices 2..N.  All loops are unrolled, so
+// every array index is static.
+template <class R>
+__device__ __forceinline__ cx<R> sel(int bit, cx<R> one, cx<R> zero) {
+    return mk<R>(bit ? one.re : zero.re, bit ? one.im : zero.im);
+}
 
 template <class R, int N>
 __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d, const typename TabT<R>::V *tab,
-                                                       double inv_h, double s0, int L, cx<R> *E) {
-    constexpr int S0 = 2 * N;
+                                                       double inv_h, double s0, int L) {
+    constexpr int M = N + 1;
     cx<R> P[N + 1][N + 1], Rr[N + 1][N + 1];
     double uu[N + 1];
 #pragma unroll
@@ -576,66 +578,84 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
 #pragma unroll
         for (int j = 0; j < k; ++j) interp_pair<R>(tab, inv_h, s0, L, uu[j] - uu[k], Rr[j][k], P[j][k]);
     const cx<R> id = crcp(d);
+    // row/column factors of vertex 1 (eliminated first, pivot d)
     const cx<R> r1[2] = {P[0][1], Rr[0][1]};
     const cx<R> c1d[2] = {cmul(nconj(Rr[0][1]), id), cmul(nconj(P[0][1]), id)};
-#pragma unroll
-    for (int bx = 0; bx < N; ++bx) {
-        cx<R> left[2];
-        if (bx == 0) {
-            left[0] = r1[0];
-            left[1] = r1[1];
-        } else {
-            left[0] = nconj(Rr[1][bx + 1]);
-            left[1] = nconj(P[1][bx + 1]);
-        }
-#pragma unroll
-        for (int by = 0; by < N; ++by) {
-            cx<R> base[2][2], right[2];
-            if (by == 0) {
-                right[0] = c1d[0];
-                right[1] = c1d[1];
-            } else {
-                right[0] = cmul(P[1][by + 1], id);
-                right[1] = cmul(Rr[1][by + 1], id);
-            }
-            if (bx == by) {
-                base[0][0] = base[0][1] = base[1][0] = base[1][1] = d;
-            } else if (bx == 0) {
-                base[0][0] = base[1][0] = P[0][by + 1];
-                base[0][1] = base[1][1] = Rr[0][by + 1];
-            } else if (by == 0) {
-                base[0][0] = base[0][1] = nconj(Rr[0][bx + 1]);
-                base[1][0] = base[1][1] = nconj(P[0][bx + 1]);
-            } else if (bx < by) {
-                base[0][0] = base[1][0] = P[bx + 1][by + 1];
-                base[0][1] = base[1][1] = Rr[bx + 1][by + 1];
-            } else {
-                base[0][0] = base[0][1] = nconj(Rr[by + 1][bx + 1]);
-                base[1][0] = base[1][1] = nconj(P[by + 1][bx + 1]);
-            }
-#pragma unroll
-            for (int x = 0; x < 2; ++x)
-#pragma unroll
-                for (int y = 0; y < 2; ++y)
-                    E[((2 * bx + x) * S0 + 2 * by + y) * 32] = cfms(base[x][y], left[x], right[y]);
-        }
-    }
     Acc<R> ar, ai;
     ar.init();
     ai.init();
-    for (int path = 0; path < (1 << (N - 1)); ++path) flat_phase<R, N - 1, 32>(E, d, 0, path, ar, ai);
+#pragma unroll
+    for (int path = 0; path < (1 << (N - 1)); ++path) {
+        // position x: 0, 1 = copies; x >= 2 = vertex v = x with Keldysh index a_v = bit (x-2) of path
+        cx<R> left[M], right[M], m[M][M];
+#pragma unroll
+        for (int x = 0; x < M; ++x) {
+            if (x < 2) {
+                left[x] = r1[x];
+                right[x] = c1d[x];
+            } else {
+                const int a = (path >> (x - 2)) & 1;
+                left[x] = nconj(sel<R>(a, P[1][x], Rr[1][x]));
+                right[x] = cmul(sel<R>(a, Rr[1][x], P[1][x]), id);
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < M; ++x)
+#pragma unroll
+            for (int y = 0; y < M; ++y) {
+                if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
+                cx<R> base;
+                if (x == y) {
+                    base = d;
+                } else if (x < 2) {  // measurement row, vertex y
+                    base = sel<R>((path >> (y - 2)) & 1, Rr[0][y], P[0][y]);
+                } else if (y < 2) {  // vertex x, measurement column
+                    base = nconj(sel<R>((path >> (x - 2)) & 1, P[0][x], Rr[0][x]));
+                } else if (x < y) {  // upper: index of the column vertex
+                    base = sel<R>((path >> (y - 2)) & 1, Rr[x][y], P[x][y]);
+                } else {  // lower: index of the row vertex
+                    base = nconj(sel<R>((path >> (x - 2)) & 1, P[y][x], Rr[y][x]));
+                }
+                m[x][y] = cfms(base, left[x], right[y]);
+            }
+        cx<R> detD = d;
+#pragma unroll
+        for (int p = 2; p < M; ++p) {
+            cx<R> pv = m[p][p];
+            detD = cmul(detD, pv);
+            cx<R> iq = crcp(pv);
+#pragma unroll
+            for (int y = 0; y < M; ++y)
+                if (y < 2 || y > p) m[p][y] = cmul(m[p][y], iq);
+#pragma unroll
+            for (int x = 0; x < M; ++x) {
+                if (!(x < 2 || x > p)) continue;
+#pragma unroll
+                for (int y = 0; y < M; ++y) {
+                    if (!(y < 2 || y > p)) continue;
+                    if (x < 2 && y < 2 && x != y) continue;
+                    m[x][y] = cfms(m[x][y], m[x][p], m[p][y]);
+                }
+            }
+        }
+        cx<R> dd = cmul(detD, detD);
+        cx<R> term = cmul(dd, mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im));
+        if (__popc(path) & 1) term = mk<R>(-term.re, -term.im);
+        ar.add(term.re);
+        ai.add(term.im);
+    }
     return mk<double>((double)ar.s + (double)ar.c, (double)ai.s + (double)ai.c);
 }
 
 template <class R>
 __device__ __forceinline__ cx<double> lane_keldysh_dispatch(int n, const double *u, cx<R> d,
                                                             const typename TabT<R>::V *tab, double inv_h, double s0,
-                                                            int L, cx<R> *E) {
+                                                            int L) {
     switch (n) {
-        case 1: return lane_keldysh_sum<R, 1>(u, d, tab, inv_h, s0, L, E);
-        case 2: return lane_keldysh_sum<R, 2>(u, d, tab, inv_h, s0, L, E);
-        case 3: return lane_keldysh_sum<R, 3>(u, d, tab, inv_h, s0, L, E);
-        default: return lane_keldysh_sum<R, 4>(u, d, tab, inv_h, s0, L, E);
+        case 1: return lane_keldysh_sum<R, 1>(u, d, tab, inv_h, s0, L);
+        case 2: return lane_keldysh_sum<R, 2>(u, d, tab, inv_h, s0, L);
+        case 3: return lane_keldysh_sum<R, 3>(u, d, tab, inv_h, s0, L);
+        default: return lane_keldysh_sum<R, 4>(u, d, tab, inv_h, s0, L);
     }
 }
 
@@ -728,20 +748,11 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
         const double inv_h = 1.0 / I.h;
         const double s0 = I.T * inv_h;
         unsigned mm = mask;
-        if (I.flat == 1 && n <= kLaneMaxOrder) {  // one point per lane
-            if (inside) {
-                cx<double> s = lane_keldysh_dispatch<R>(n, ws.upt + lane * NU, d, tab, inv_h, s0, I.L, ws.stack + lane);
-                cx<double> cval = times_i_pow(s, n);
-                myval = mk<double>(w * cval.re, w * cval.im);
-            }
-            mm = 0;
-            __syncwarp();
-        }
         while (mm) {
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
-            const int rf = I.flat < rf_min ? rf_min : (I.flat > RFMAX ? RFMAX : I.flat);
-            cx<double> s = keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, tab, inv_h, s0, I.L, rf, lane);
+            // every warp-per-point item of a launch shares the launch's flat depth
+            cx<double> s = keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, tab, inv_h, s0, I.L, RFMAX, lane);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -749,6 +760,78 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             __syncwarp();
         }
         double sr = myval.re, cr = 0.0, si = myval.im, ci = 0.0;
+        warp_reduce_pair(sr, cr);
+        warp_reduce_pair(si, ci);
+        if (lane == 0) {
+            double *pp = I.partials + 4 * (size_t)local;
+            pp[0] = sr;
+            pp[1] = si;
+            pp[2] = cr;
+            pp[3] = ci;
+            I.inside[local] = __popc(mask);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// One-point-per-lane kernel for small orders (items whose tuning asks for it):
+// persistent warps pull chunks of 32 Sobol' indices, every lane generates,
+// warps and sums its own point entirely in registers; no shared memory.
+// ----------------------------------------------------------------------------
+template <class R, int N>
+__device__ __forceinline__ cx<double> lane_point(const ItemDev &I, int k, uint64_t i, bool &inside) {
+    double u[N + 1];
+    double uprev = I.t, prod = 1.0, tn = 1.0;
+    u[0] = I.t;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        uint32_t y = sobol_word(m, i) ^ I.shifts[k * N + m];
+        double v, omx;
+        warp_gap(R(0), y, I.tau, v, omx);
+        uprev = uprev - v;
+        u[m + 1] = uprev;
+        prod *= omx;
+        tn *= I.tau;
+    }
+    inside = uprev > 0.0;
+    if (!inside) return mk<double>(0.0, 0.0);
+    const double w = tn / prod;
+    const double inv_h = 1.0 / I.h;
+    const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
+    cx<double> s = lane_keldysh_sum<R, N>(u, d, item_table<R>(I), inv_h, I.T * inv_h, I.L);
+    cx<double> c = times_i_pow(s, N);
+    return mk<double>(w * c.re, w * c.im);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) lane_kernel(const ItemDev *__restrict__ items, int n_items,
+                                                   long long total_chunks, unsigned long long *counter) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(counter, 1ull);
+        c = __shfl_sync(FULL, c, 0);
+        if ((long long)c >= total_chunks) break;
+        int it = 0;
+        while (it + 1 < n_items && items[it + 1].chunk_begin <= (long long)c) ++it;
+        const ItemDev &I = items[it];
+        const long long local = (long long)c - I.chunk_begin;
+        const int k = (int)(local / I.chunks_per_shift);
+        const long long blk = local - (long long)k * I.chunks_per_shift;
+        const long long idx = blk * kChunk + lane;
+        bool inside = false;
+        cx<double> v = mk<double>(0.0, 0.0);
+        if (idx < I.n_points) {
+            const uint64_t i = (uint64_t)(I.first_index + idx);
+            switch (I.order) {
+                case 1: v = lane_point<R, 1>(I, k, i, inside); break;
+                case 2: v = lane_point<R, 2>(I, k, i, inside); break;
+                case 3: v = lane_point<R, 3>(I, k, i, inside); break;
+                default: v = lane_point<R, 4>(I, k, i, inside); break;
+            }
+        }
+        const unsigned mask = __ballot_sync(FULL, inside);
+        double sr = v.re, cr = 0.0, si = v.im, ci = 0.0;
         warp_reduce_pair(sr, cr);
         warp_reduce_pair(si, ci);
         if (lane == 0) {
@@ -1019,8 +1102,11 @@ size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
 template <class R, int F>
 static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, int rf_min, cudaStream_t s) {
-    size_t smem = warp_smem_bytes<R>(n_max, rf_min) * wpb;
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    // fewer warps per block when the shared memory of the requested shape does not fit
+    const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min);
+    if (per_warp > 227 * 1024) return cudaErrorInvalidConfiguration;
+    while (wpb > 1 && per_warp * wpb > 227 * 1024) --wpb;
+    size_t smem = per_warp * wpb;
     cudaError_t e = cudaFuncSetAttribute(detsum_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -1056,6 +1142,30 @@ cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_c
         case 4: return launch_detsum_t<float, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
         default: return launch_detsum_t<float, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
     }
+}
+
+template <class R>
+static cudaError_t launch_lane_t(const ItemDev *d_items, int n_items, long long total_chunks,
+                                 unsigned long long *d_counter, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lane_kernel<R>, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long want = (total_chunks + 3) / 4;
+    long long grid = (long long)sms * per_sm;
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    lane_kernel<R><<<(unsigned)grid, 128, 0, s>>>(d_items, n_items, total_chunks, d_counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
+                        int precision, cudaStream_t s) {
+    if (n_items < 1 || total_chunks < 1) return cudaSuccess;
+    return precision == QQMC_PREC_FP64 ? launch_lane_t<double>(d_items, n_items, total_chunks, d_counter, s)
+                                       : launch_lane_t<float>(d_items, n_items, total_chunks, d_counter, s);
 }
 
 cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out,

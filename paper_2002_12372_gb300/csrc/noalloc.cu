@@ -111,8 +111,12 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
 
     cudaError_t e = cudaMemcpyAsync(d_item, &it, sizeof(ItemDev), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess)
-        e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, s);
+    if (e == cudaSuccess) {
+        if (it.flat == 1 && order <= kLaneMaxOrder)
+            e = launch_lane(d_item, 1, (long long)(cps * n_shifts), d_counter, precision, s);
+        else
+            e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, s);
+    }
     if (e == cudaSuccess) e = launch_reduce(d_item, 1, n_shifts, d_sums, counts, s);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrate_noalloc");
     return QQMC_OK;

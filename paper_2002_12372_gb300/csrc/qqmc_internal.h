@@ -61,6 +61,9 @@ int upload_direction_numbers();
 int launch_gf_table(const Problem &pr, cudaStream_t s);
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                           int n_max, int precision, const Tuning &tune, cudaStream_t s);
+cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
+                        int precision, cudaStream_t s);
+constexpr int kLaneMaxOrder = 4;  // orders that may run one point per lane
 cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out, unsigned long long *d_counts,
                           cudaStream_t s);
 size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune);

@@ -259,3 +259,86 @@ def test_full_size_bench_launch_sampled_chunks(Q, W, oracle):
     finally:
         for pr in probs:
             Q.qqmc_destroy_problem(pr)
+        autotune.reset()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_one_point_per_lane_mode_matches(Q, W, oracle, precision):
+    """Orders <= 4 tuned to one point per lane run in their own kernel: FP64 within 1e-10 of the
+    oracle per shift, mixed within 1e-4 of FP64; a plan mixing both kernels returns the same sums
+    as single runs."""
+    from paper_2002_12372_gb300 import autotune
+    T, K = 10.0, 4
+    pr, tabs = _problem(Q, W, seed=61, T=T)
+    try:
+        for n in range(1, 5):
+            Q.qqmc_set_tuning(precision, n, 2, 1)
+        ref = {}
+        for n, N in [(1, 3001), (2, 2048), (3, 999), (4, 1500)]:
+            sw = W.shift_words(3000 + n, K, n)
+            res, S = Q.qqmc_integrate(pr, n, N, K, precision, sw)
+            S0, nin = oracle.estimate(n, N, sw, T, 1.0, tabs, T)
+            if precision == 0:
+                assert res.n_in_domain == int(nin.sum())
+                assert np.all(np.abs(S - S0) <= 1e-10 * np.abs(S0))
+            else:
+                assert np.all(np.abs(S - S0) <= 1e-4 * np.abs(S0))
+            ref[n] = (N, sw, S)
+        items = [(pr, n, K, ref[n][0], ref[n][1]) for n in (4, 2)] + [(pr, 6, K, 300, W.shift_words(77, K, 6))]
+        plan = Q.Plan(items, precision)
+        assert plan.kernel_count() == 3
+        plan.launch()
+        out = plan.results()
+        plan.close()
+        for (_, n, _, _, _), (r, S) in zip(items[:2], out[:2]):
+            assert np.allclose(S, ref[n][2], rtol=1e-12, atol=0)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+        autotune.reset()
+
+
+def test_checkpoint_resume_by_index_cursor(Q, W, oracle):
+    """A run split at an index cursor (first_index) adds up to the uninterrupted run: the
+    per-(order, shift) sums plus the cursor are a complete checkpoint."""
+    T, K, N = 10.0, 3, 4096
+    pr, tabs = _problem(Q, W, seed=71, T=T)
+    try:
+        for n in (2, 7):
+            sw = W.shift_words(90 + n, K, n)
+            plan = Q.Plan([(pr, n, K, N, sw, 0)], Q.QQMC_PREC_FP64)
+            plan.launch()
+            (r_full, S_full), = plan.results()
+            plan.close()
+            parts, n_in = [], 0
+            for first, cnt in [(0, 1536), (1536, 2560)]:
+                p2 = Q.Plan([(pr, n, K, cnt, sw, first)], Q.QQMC_PREC_FP64)
+                p2.launch()
+                (r, S), = p2.results()
+                p2.close()
+                parts.append(S * cnt)
+                n_in += r.n_in_domain
+            assert n_in == r_full.n_in_domain
+            assert np.allclose((parts[0] + parts[1]) / N, S_full, rtol=1e-12, atol=0)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+
+
+@pytest.mark.parametrize("order", [13, 14, 16])
+def test_high_orders_match_oracle(Q, W, oracle, order):
+    """Orders beyond the benchmark table (the paper reaches 22): integrand parity at a few points
+    and, at order 13, a small integration against the oracle."""
+    T = 10.0
+    pr, tabs = _problem(Q, W, seed=200 + order, T=T)
+    try:
+        u = W.ordered_times(300 + order, 2 if order < 16 else 1, order, T)
+        gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)
+        ref, scale = oracle.integrand(order, u, T, tabs, T, return_abs=True)
+        assert np.all(np.abs(gpu - ref) <= 1e-12 * scale), np.max(np.abs(gpu - ref) / scale)
+        if order == 13:
+            sw = W.shift_words(13, 1, order)
+            res, S = Q.qqmc_integrate(pr, order, 48, 1, Q.QQMC_PREC_FP64, sw)
+            S0, nin = oracle.estimate(order, 48, sw, T, 1.0, tabs, T)
+            assert res.n_in_domain == int(nin.sum())
+            assert np.all(np.abs(S - S0) <= 1e-10 * np.abs(S0))
+    finally:
+        Q.qqmc_destroy_problem(pr)
