@@ -244,6 +244,22 @@ int qqmc_warp_points(const qqmc_problem *pr, int order, uint64_t first_index, ui
 int qqmc_integrand(const qqmc_problem *pr, int order, uint64_t count, const double *u, int precision,
                    double *out);
 
+/*
+ * Conformal resummation of a truncated perturbation series F(U) =
+ * sum_{n=0}^{N} a_n U^n beyond its radius of convergence, paper App. H
+ * (parabola transform W = -tan^2(sqrt(U/p)) with a real negative parameter
+ * p; for U >= 0 this is W = tanh^2(sqrt(U/|p|)) in [0, 1)).  The series is
+ * re-expanded in powers of W through U(W) = |p| artanh^2(sqrt W), truncated at
+ * W^N and evaluated at W(U).  invert != 0 resums 1/F (a_0 != 0) and returns
+ * the reciprocal.  a_err (optional, host [N+1]): standard errors of the a_n,
+ * propagated linearly into *err; *tail (optional) = |b_N W^N|, the size of
+ * the last re-expanded term, a truncation estimate.  Host-only, no device.
+ * Errors: E_INVAL (N outside 0..QQMC_MAX_ORDER, p >= 0, U < 0, a_0 = 0 with
+ * invert).
+ */
+int qqmc_resum_parabola(const double *a, const double *a_err, int n, double p, double U, int invert, double *value,
+                        double *err, double *tail);
+
 /* ------------------------------- serving ---------------------------------- */
 
 typedef struct qqmc_server qqmc_server;

@@ -354,3 +354,45 @@ def shift_words(seed: int, K: int, n_dims: int) -> np.ndarray:
         for d in range(n_dims):
             out[k, d] = splitmix64((seed ^ (k * 65536 + d)) & ((1 << 64) - 1)) >> 32
     return out
+
+
+# --------------------------------------------------------------------------
+# Series resummation (App. H): parabola conformal map
+# --------------------------------------------------------------------------
+
+def resum_parabola(a, p: float, U: float, invert: bool = False):
+    """Conformal resummation of F(U) = sum_n a_n U^n with the parabola transform
+    W = -tan^2(sqrt(U/p)), p < 0 (App. H), i.e. W = tanh^2(sqrt(U/|p|)) for U >= 0.
+
+    The inverse map U(W) = |p| atanh(sqrt W)^2 is expanded symbolically (sympy),
+    F(U(W)) is re-expanded in W and truncated at the order N of the input, and the
+    truncated series is evaluated at W(U).  invert: resum 1/F and return its
+    reciprocal.  Returns the value.
+    """
+    import sympy as sp
+
+    a = [float(x) for x in a]
+    N = len(a) - 1
+    if invert:  # power series of 1/F by long division
+        f = [1.0 / a[0]]
+        for k in range(1, N + 1):
+            f.append(-sum(a[j] * f[k - j] for j in range(1, k + 1)) / a[0])
+    else:
+        f = list(a)
+    Wsym = sp.Symbol("W", positive=True)
+    ser = sp.series(sp.atanh(sp.sqrt(Wsym)) ** 2, Wsym, 0, N + 1).removeO()
+    poly = sp.Poly(sp.expand(ser), Wsym)
+    c = np.zeros(N + 1)
+    for (deg,), coef in poly.terms():
+        if deg <= N:
+            c[deg] = float(coef) * abs(p)
+    b = np.zeros(N + 1)
+    power = np.zeros(N + 1)
+    power[0] = 1.0
+    for k in range(N + 1):
+        b += f[k] * power
+        power = np.polynomial.polynomial.polymul(power, c)[: N + 1]
+        power = np.pad(power, (0, N + 1 - power.size))
+    W = math.tanh(math.sqrt(U / abs(p))) ** 2
+    val = float(np.polynomial.polynomial.polyval(W, b))
+    return 1.0 / val if invert else val

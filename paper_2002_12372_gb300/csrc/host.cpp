@@ -1,5 +1,6 @@
 // Host-side generators of the product path: Sobol' direction words, digital
 // shift words, error reporting.
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -85,6 +86,93 @@ void shift_words(uint64_t seed, int n_shifts, int n_dims, uint32_t *out) {
 }
 
 }  // namespace qqmc
+
+namespace qqmc {
+
+// Parabola-map resummation (see qqmc_resum_parabola).  U = |p| artanh^2(sqrt W)
+// = |p| sum_{m>=1} c_m W^m with c_m = sum_{j=0}^{m-1} 1 / ((2j+1)(2(m-1-j)+1)).
+static double resum_value(const double *a, int n, double p, double U, int invert, double *tail) {
+    double f[QQMC_MAX_ORDER + 1];
+    if (invert) {  // power series of 1 / F
+        f[0] = 1.0 / a[0];
+        for (int k = 1; k <= n; ++k) {
+            double acc = 0.0;
+            for (int j = 1; j <= k; ++j) acc += a[j] * f[k - j];
+            f[k] = -acc / a[0];
+        }
+    } else {
+        for (int k = 0; k <= n; ++k) f[k] = a[k];
+    }
+    const double ap = fabs(p);
+    double c[QQMC_MAX_ORDER + 1];
+    c[0] = 0.0;
+    for (int m = 1; m <= n; ++m) {
+        double acc = 0.0;
+        for (int j = 0; j <= m - 1; ++j) acc += 1.0 / ((2.0 * j + 1.0) * (2.0 * (m - 1 - j) + 1.0));
+        c[m] = ap * acc;
+    }
+    // b(W) = sum_k f_k U(W)^k, truncated at W^n
+    double b[QQMC_MAX_ORDER + 1], pw[QQMC_MAX_ORDER + 1], tmp[QQMC_MAX_ORDER + 1];
+    for (int k = 0; k <= n; ++k) {
+        b[k] = 0.0;
+        pw[k] = 0.0;
+    }
+    pw[0] = 1.0;  // U(W)^0
+    b[0] = f[0];
+    for (int k = 1; k <= n; ++k) {
+        for (int i = 0; i <= n; ++i) tmp[i] = 0.0;
+        for (int i = 0; i <= n; ++i)
+            if (pw[i] != 0.0)
+                for (int m = 1; i + m <= n; ++m) tmp[i + m] += pw[i] * c[m];
+        for (int i = 0; i <= n; ++i) {
+            pw[i] = tmp[i];
+            b[i] += f[k] * pw[i];
+        }
+    }
+    const double th = tanh(sqrt(U / ap));
+    const double W = th * th;
+    double val = 0.0, Wk = 1.0, last = 0.0;
+    for (int k = 0; k <= n; ++k) {
+        last = b[k] * Wk;
+        val += last;
+        Wk *= W;
+    }
+    if (tail) *tail = fabs(last);
+    return invert ? 1.0 / val : val;
+}
+
+}  // namespace qqmc
+
+extern "C" int qqmc_resum_parabola(const double *a, const double *a_err, int n, double p, double U, int invert,
+                                   double *value, double *err, double *tail) {
+    if (!a || !value || n < 0 || n > qqmc::kMaxOrder || !(p < 0.0) || !(U >= 0.0) || !isfinite(p) || !isfinite(U))
+        return qqmc::set_error(QQMC_E_INVAL, "qqmc_resum_parabola: need a, value, 0 <= n <= QQMC_MAX_ORDER, p < 0, U >= 0");
+    if (invert && a[0] == 0.0) return qqmc::set_error(QQMC_E_INVAL, "qqmc_resum_parabola: 1/F needs a_0 != 0");
+    double t = 0.0;
+    const double v = qqmc::resum_value(a, n, p, U, invert, &t);
+    *value = v;
+    if (tail) *tail = t;
+    if (err) {  // linear propagation of the coefficient errors (central differences)
+        double e2 = 0.0;
+        if (a_err) {
+            double ac[qqmc::kMaxOrder + 1];
+            for (int k = 0; k <= n; ++k) ac[k] = a[k];
+            for (int k = 0; k <= n; ++k) {
+                if (!(a_err[k] > 0.0)) continue;
+                const double hstep = a_err[k];
+                ac[k] = a[k] + hstep;
+                const double vp = qqmc::resum_value(ac, n, p, U, invert, nullptr);
+                ac[k] = a[k] - hstep;
+                const double vm = qqmc::resum_value(ac, n, p, U, invert, nullptr);
+                ac[k] = a[k];
+                const double d = 0.5 * (vp - vm);
+                e2 += d * d;
+            }
+        }
+        *err = sqrt(e2);
+    }
+    return QQMC_OK;
+}
 
 extern "C" int qqmc_last_error(char *buf, size_t len) {
     if (!buf || len == 0) return QQMC_E_INVAL;

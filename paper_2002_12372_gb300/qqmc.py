@@ -39,7 +39,7 @@ EXPORTED = [
     "qqmc_plan_kernel_count", "qqmc_plan_timing", "qqmc_set_tuning", "qqmc_get_tuning", "qqmc_direction_numbers",
     "qqmc_shift_words", "qqmc_sobol_points", "qqmc_warp_points", "qqmc_integrand", "qqmc_server_create",
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
-    "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums",
+    "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola",
 ]
 
 
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         "qqmc_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "qqmc_integrate_noalloc": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
         "qqmc_plan_chunk_sums": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, dp],
+        "qqmc_resum_parabola": [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -326,6 +327,17 @@ def qqmc_integrand(pr: int, order: int, u: np.ndarray, precision: int = QQMC_PRE
     _check(load().qqmc_integrand(ctypes.c_void_p(pr), order, u.shape[0], _ptr(u, ctypes.c_double), precision,
                                  _ptr(out, ctypes.c_double)), "qqmc_integrand")
     return out.view(np.complex128)
+
+
+def qqmc_resum_parabola(a, p: float, U: float, a_err=None, invert: bool = False):
+    """Returns (value, propagated error, last-term size) of the parabola-map resummation."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    e = None if a_err is None else np.ascontiguousarray(np.asarray(a_err, dtype=np.float64))
+    v, er, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().qqmc_resum_parabola(_ptr(a, ctypes.c_double), _ptr(e, ctypes.c_double), a.size - 1, p, U,
+                                      int(invert), ctypes.byref(v), ctypes.byref(er), ctypes.byref(t)),
+           "qqmc_resum_parabola")
+    return v.value, er.value, t.value
 
 
 def qqmc_server_create(opts: qqmc_server_opts) -> int:
