@@ -74,6 +74,9 @@ typedef struct qqmc_params {
     int32_t n_table; /* L, number of table nodes; even, 4 <= L <= 2^20 */
     int32_t reserved;
     uint64_t seed;   /* digital-shift seed (used when no shift words are given) */
+    double alpha;    /* quadratic shift of the interaction, U (n_up - alpha)(n_dn - alpha) (App. E):
+                        the diagonal of every Wick determinant becomes g^<(0) - i alpha, except the
+                        entry of the measurement pair; 0 for the plain expansion */
 } qqmc_params;
 
 typedef struct qqmc_problem qqmc_problem;
@@ -107,6 +110,33 @@ int qqmc_destroy_problem(qqmc_problem *pr);
 /* Copy the problem's tables to host: 2*L doubles each, full [-t_max, t_max]
  * mesh (negative nodes filled by g(-tau) = -conj g(tau)). */
 int qqmc_problem_tables(const qqmc_problem *pr, double *g_lesser, double *g_greater, double *g0);
+
+/*
+ * Learned warp (paper App. F, "learning h from the integrand"): a second
+ * change of variables w -> x on top of the exponential one, with
+ * w_m = 1 - exp(-v_m / tau) in [0, 1).  Per dimension m the density of w_m is
+ * piecewise constant on `cells` equal cells; cdf (host [order][cells + 1],
+ * cdf[m][0] = 0, cdf[m][cells] = 1, non-decreasing) is its cumulative
+ * distribution.  A Sobol' coordinate x is mapped to w by inverting the CDF and
+ * the point weight gains prod_m dw_m/dx_m.  Installed per (problem, order):
+ * every later integration of that order on the problem uses it (plans capture
+ * it at creation).  cdf = NULL or cells <= 0 restores the plain warp.
+ */
+int qqmc_set_projection(qqmc_problem *pr, int order, const double *cdf, int cells);
+
+/*
+ * Learn and install the warp above from M integrand samples: the first M
+ * Sobol' points shifted by the words of shift index 65535 of the problem's
+ * seed, plain exponential warp; |w c_n(u)| of the in-domain points (FP64,
+ * device) is binned in each w_m into n_bins bins (the projection of the
+ * integrand onto dimension m), smoothed with the Gaussian kernel
+ * exp(-(w - w')^2 / lambda^2) onto the cells, floored at floor_frac times its
+ * maximum (every region keeps a sampling density), and accumulated into the
+ * CDF.  cdf_out (optional, host [order][cells + 1]) receives the table.
+ * The paper uses N_b = 100..250 bins, M = 2e4..1e5, lambda = 0.05.
+ */
+int qqmc_learn_projection(qqmc_problem *pr, int order, uint64_t M, int n_bins, double lambda, double floor_frac,
+                          int cells, double *cdf_out);
 
 /* Result of one order-n integration. */
 typedef struct qqmc_result {

@@ -80,14 +80,18 @@ def lib():
         u32p = ctypes.POINTER(ctypes.c_uint32)
         i64 = ctypes.c_int64
         L.oracle_integrand.argtypes = [ctypes.c_int, i64, dp, ctypes.c_double, dp, dp, ctypes.c_int,
-                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double]
         L.oracle_sobol.argtypes = [ctypes.c_int, i64, i64, u32p, u32p]
         L.oracle_estimate.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
                                       ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64)]
+                                      ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64), ctypes.c_double]
         L.oracle_warp.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
                                   ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int32)]
         L.oracle_det.argtypes = [ctypes.c_int, dp, dp]
+        L.oracle_estimate_proj.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double, ctypes.c_double,
+                                           dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64),
+                                           ctypes.c_double]
         L.oracle_table_at.argtypes = [dp, ctypes.c_int, ctypes.c_double, i64, dp, dp]
         _lib = L
     return _lib
@@ -242,8 +246,9 @@ def _tab(a: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
 
 
-def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: bool = False):
-    """c(u) of App. E Eq. (integral_gf) at each row of u ([count, n], any time order)."""
+def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: bool = False, alpha: float = 0.0):
+    """c(u) of App. E Eq. (integral_gf) at each row of u ([count, n], any time order);
+    alpha: quadratic shift of the vertex diagonals (App. E)."""
     gl, gg, gl0 = tables
     u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)).reshape(-1, n))
     count = u.shape[0]
@@ -252,7 +257,7 @@ def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: boo
     out = np.zeros(2 * count)
     ab = np.zeros(count)
     rc = lib().oracle_integrand(n, count, _dp(u), t, _dp(gl_t), _dp(gg_t), L, T,
-                                float(np.real(gl0)), float(np.imag(gl0)), _dp(out), _dp(ab))
+                                float(np.real(gl0)), float(np.imag(gl0)), _dp(out), _dp(ab), float(alpha))
     if rc != 0:
         raise ValueError("oracle_integrand rejected its arguments")
     val = out[0::2] + 1j * out[1::2]
@@ -278,11 +283,12 @@ def table_at(table: np.ndarray, T: float, tau: np.ndarray) -> np.ndarray:
 
 
 def _estimate_chunk(args):
-    n, i0, i1, Vc, S, t, tau, gl_t, gg_t, L, T, gl0 = args
+    n, i0, i1, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha = args
     res = np.zeros(4)
     n_in = ctypes.c_int64(0)
     rc = lib().oracle_estimate(n, i0, i1, _u32p(Vc), _u32p(S), t, tau, _dp(gl_t), _dp(gg_t), L, T,
-                               float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in))
+                               float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in),
+                               float(alpha))
     if rc != 0:
         raise ValueError("oracle_estimate rejected its arguments")
     return res, n_in.value
@@ -290,7 +296,7 @@ def _estimate_chunk(args):
 
 def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T: float,
              V: np.ndarray | None = None, threads: int | None = None, i0: int = 0,
-             chunk: int = 4096):
+             chunk: int = 4096, alpha: float = 0.0):
     """Per-shift estimates S_k = (1/N) sum_{i=i0}^{i0+N-1} w_i c(u_i), Eq. (warped_int2).
 
     shifts: uint32 [K, >= n] digital-shift words.  Returns (S [K] complex,
@@ -311,7 +317,7 @@ def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T
         S = np.ascontiguousarray(shifts[k, :n])
         for a in range(i0, i0 + N, chunk):
             b = min(a + chunk, i0 + N)
-            jobs.append((k, (n, a, b, Vc, S, t, tau, gl_t, gg_t, L, T, gl0)))
+            jobs.append((k, (n, a, b, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha)))
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(max_workers=threads) as ex:
         results = list(ex.map(_estimate_chunk, [j[1] for j in jobs]))
@@ -396,3 +402,87 @@ def resum_parabola(a, p: float, U: float, invert: bool = False):
     W = math.tanh(math.sqrt(U / abs(p))) ** 2
     val = float(np.polynomial.polynomial.polyval(W, b))
     return 1.0 / val if invert else val
+
+
+# --------------------------------------------------------------------------
+# Learned warp (App. F: learning h from the integrand)
+# --------------------------------------------------------------------------
+
+def learn_projection(n: int, M: int, seed: int, t: float, tau: float, tables, T: float, n_bins: int = 100,
+                     lam: float = 0.05, floor_frac: float = 1e-3, cells: int = 1024, V=None) -> np.ndarray:
+    """Per-dimension CDF tables [n, cells + 1] of the learned warp.
+
+    Samples: the first M Sobol' points shifted by shift_words(seed, 65536, n)[65535]
+    (the learning sequence), plain exponential warp; value |w c_n(u)| of the
+    in-domain points.  Projection onto each w_m: histogram with n_bins bins
+    (sum of values / M per bin).  Smoothing: Gaussian kernel
+    exp(-(w - w_l)^2 / lam^2) over the bin centres w_l, evaluated at the cell
+    centres; floor at floor_frac x maximum; CDF by cumulative sum.
+    """
+    if V is None:
+        V = sobol_direction_numbers(max(n, 1))
+    S = np.array([splitmix64((seed ^ (65535 * 65536 + d)) & ((1 << 64) - 1)) >> 32 for d in range(n)],
+                 dtype=np.uint32)
+    u, w, ins = warp(n, 0, M, V, S, t, tau)
+    x = ((sobol_points(n, 0, M, V) ^ S[None, :]).astype(np.float64)) * 2.0 ** -32
+    vals = np.zeros(M)
+    if ins.any():
+        c = integrand(n, u[ins], t, tables, T)
+        vals[ins] = w[ins] * np.abs(c) / M
+    centers = (np.arange(n_bins) + 0.5) / n_bins
+    z = (np.arange(cells) + 0.5) / cells
+    K = np.exp(-((z[:, None] - centers[None, :]) ** 2) / lam ** 2)
+    out = np.zeros((n, cells + 1))
+    for d in range(n):
+        b = np.clip((x[:, d] * n_bins).astype(np.int64), 0, n_bins - 1)
+        hist = np.bincount(b, weights=vals, minlength=n_bins)
+        h = (K @ hist) / K.sum(axis=1)
+        hmax = h.max()
+        h = np.ones(cells) if hmax <= 0 else np.maximum(h, floor_frac * hmax)
+        cdf = np.concatenate([[0.0], np.cumsum(h) / h.sum()])
+        cdf[-1] = 1.0
+        out[d] = cdf
+    return out
+
+
+def _estimate_proj_chunk(args):
+    n, i0, i1, Vc, S, t, tau, cdf, cells, gl_t, gg_t, L, T, gl0, alpha = args
+    res = np.zeros(4)
+    n_in = ctypes.c_int64(0)
+    rc = lib().oracle_estimate_proj(n, i0, i1, _u32p(Vc), _u32p(S), t, tau, _dp(cdf), cells, _dp(gl_t), _dp(gg_t),
+                                    L, T, float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in),
+                                    float(alpha))
+    if rc != 0:
+        raise ValueError("oracle_estimate_proj rejected its arguments")
+    return res, n_in.value
+
+
+def estimate_proj(n: int, N: int, shifts: np.ndarray, t: float, tau: float, cdf: np.ndarray, tables, T: float,
+                  V: np.ndarray | None = None, threads: int | None = None, chunk: int = 4096, alpha: float = 0.0):
+    """Per-shift estimates with the learned warp (same contract as ``estimate``)."""
+    if V is None:
+        V = sobol_direction_numbers(max(n, 1))
+    Vc = np.ascontiguousarray(V[:n], dtype=np.uint32)
+    cdf = np.ascontiguousarray(np.asarray(cdf, dtype=np.float64)[:n])
+    cells = cdf.shape[1] - 1
+    gl, gg, gl0 = tables
+    gl_t, gg_t = _tab(gl), _tab(gg)
+    L = gl_t.size // 2
+    shifts = np.atleast_2d(np.asarray(shifts, dtype=np.uint32))
+    K = shifts.shape[0]
+    jobs = []
+    for k in range(K):
+        S = np.ascontiguousarray(shifts[k, :n])
+        for a in range(0, N, chunk):
+            jobs.append((k, (n, a, min(a + chunk, N), Vc, S, t, tau, cdf, cells, gl_t, gg_t, L, T, gl0, alpha)))
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        results = list(ex.map(_estimate_proj_chunk, [j[1] for j in jobs]))
+    re_parts = [[] for _ in range(K)]
+    im_parts = [[] for _ in range(K)]
+    n_in = np.zeros(K, dtype=np.int64)
+    for (k, _), (res, cnt) in zip(jobs, results):
+        re_parts[k].extend([res[0], res[2]])
+        im_parts[k].extend([res[1], res[3]])
+        n_in[k] += cnt
+    S = np.array([complex(math.fsum(re_parts[k]), math.fsum(im_parts[k])) / N for k in range(K)])
+    return S, n_in

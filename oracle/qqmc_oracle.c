@@ -57,7 +57,8 @@ typedef struct {
     const double *gg; /* g^> table */
     int L;
     double T;         /* table covers [-T, T] */
-    cplx gl0;         /* g^<(0): the equal-time, same-vertex value */
+    cplx gl0;         /* g^<(0): the equal-time value of the measurement pair */
+    cplx dv;          /* diagonal of a vertex: g^<(0) - i alpha (App. E, quadratic shift alpha) */
 } gf_t;
 
 /*
@@ -65,11 +66,13 @@ typedef struct {
  * and (u', a'), App. E: the 2x2 matrix [[g^T, g^<], [g^>, g^Tbar]]_{a a'} with
  *   g^T(u,u')    = theta(u-u') g^>(u-u') + theta(u'-u) g^<(u-u'),
  *   g^Tbar(u,u') = theta(u'-u) g^>(u-u') + theta(u-u') g^<(u-u').
- * `same` marks a point paired with itself (a vertex on the diagonal, or the
- * measurement pair): the equal-time value g^<(0) is used there.
+ * `same` marks a point paired with itself: 1 = the measurement pair, whose
+ * entry is g^<(0); 2 = a vertex on the diagonal, g^<(0) shifted by -i alpha
+ * (App. E: every diagonal except the one of the measurement point).
  */
 static cplx keldysh_g(const gf_t *g, double u, int a, double up, int ap, int same) {
-    if (same) return g->gl0;
+    if (same == 1) return g->gl0;
+    if (same == 2) return g->dv;
     double tau = u - up;
     if (a == 0 && ap == 1) return table_at(g->gl, g->L, g->T, tau);
     if (a == 1 && ap == 0) return table_at(g->gg, g->L, g->T, tau);
@@ -119,6 +122,7 @@ static cplx det_lu(cplx *A, int m) {
  * ((n+1)x(n+1), row 0 / column 0 = the measurement points), the right one is
  * spin-down (n x n).  Both are formed from scratch for every a.
  * Also returns sum_a |term| (before the i^n factor) in *abs_sum if non-NULL.
+ * With alpha != 0 the vertex diagonals are shifted (see keldysh_g).
  */
 static cplx integrand(const gf_t *g, int n, const double *u, double t, double *abs_sum) {
     cplx up[(ORACLE_MAX_ORDER + 1) * (ORACLE_MAX_ORDER + 1)];
@@ -137,12 +141,12 @@ static cplx integrand(const gf_t *g, int n, const double *u, double t, double *a
             for (int c = 0; c < m; ++c) {
                 double uc = (c == 0) ? t : u[c - 1];
                 int ac = (c == 0) ? 1 : a[c - 1];
-                up[r * m + c] = keldysh_g(g, ur, ar, uc, ac, r == c);
+                up[r * m + c] = keldysh_g(g, ur, ar, uc, ac, r == c ? (r == 0 ? 1 : 2) : 0);
             }
         }
         for (int r = 0; r < n; ++r)
             for (int c = 0; c < n; ++c)
-                dn[r * n + c] = keldysh_g(g, u[r], a[r], u[c], a[c], r == c);
+                dn[r * n + c] = keldysh_g(g, u[r], a[r], u[c], a[c], r == c ? 2 : 0);
         cplx term = det_lu(up, m) * det_lu(dn, n);
         if (parity) term = -term;
         asum += cabs(term);
@@ -167,9 +171,9 @@ static cplx integrand(const gf_t *g, int n, const double *u, double t, double *a
  * out: 2*count doubles (re, im) of c(u); abs_out (optional): sum_a |term|. */
 int oracle_integrand(int n, int64_t count, const double *u, double t,
                      const double *gl, const double *gg, int L, double T,
-                     double gl0_re, double gl0_im, double *out, double *abs_out) {
+                     double gl0_re, double gl0_im, double *out, double *abs_out, double alpha) {
     if (n < 0 || n > ORACLE_MAX_ORDER || L < 2 || count < 0) return -1;
-    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im};
+    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im, gl0_re + I * (gl0_im - alpha)};
     for (int64_t i = 0; i < count; ++i) {
         double as;
         cplx v = integrand(&g, n, u + i * n, t, &as);
@@ -209,9 +213,9 @@ int oracle_sobol(int n, int64_t i0, int64_t count, const uint32_t *V, uint32_t *
  */
 int oracle_estimate(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint32_t *S,
                     double t, double tau, const double *gl, const double *gg, int L,
-                    double T, double gl0_re, double gl0_im, double *result, int64_t *n_in) {
+                    double T, double gl0_re, double gl0_im, double *result, int64_t *n_in, double alpha) {
     if (n < 1 || n > ORACLE_MAX_ORDER || L < 2) return -1;
-    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im};
+    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im, gl0_re + I * (gl0_im - alpha)};
     double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
     int64_t inside = 0;
     uint32_t X[ORACLE_MAX_ORDER];
@@ -285,5 +289,63 @@ int oracle_table_at(const double *tab, int L, double T, int64_t count, const dou
         out[2 * i] = creal(v);
         out[2 * i + 1] = cimag(v);
     }
+    return 0;
+}
+
+/*
+ * Learned warp (App. F, learning h from the integrand): w_m in [0,1) has a
+ * piecewise-constant density on `cells` equal cells with cumulative values
+ * cdf[m*(cells+1) + k].  x -> w: the cell k with cdf[k] <= x < cdf[k+1]
+ * (scanned from below), w = (k + (x - cdf[k]) / (cdf[k+1] - cdf[k])) / cells,
+ * dw/dx = 1 / (cells (cdf[k+1] - cdf[k])).  Then v = -tau log(1 - w) as in the
+ * plain warp, and the weight is C/p_n(u) times prod_m dw_m/dx_m.
+ */
+static double learned_w(const double *cdf, int cells, double x, double *jac) {
+    int k = 0;
+    while (k + 1 < cells && cdf[k + 1] <= x) ++k;
+    double dc = cdf[k + 1] - cdf[k];
+    *jac = 1.0 / ((double)cells * dc);
+    return ((double)k + (x - cdf[k]) / dc) / (double)cells;
+}
+
+int oracle_estimate_proj(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint32_t *S, double t,
+                         double tau, const double *cdf, int cells, const double *gl, const double *gg, int L,
+                         double T, double gl0_re, double gl0_im, double *result, int64_t *n_in,
+                         double alpha) {
+    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || cells < 1) return -1;
+    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im, gl0_re + I * (gl0_im - alpha)};
+    double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
+    int64_t inside = 0;
+    uint32_t X[ORACLE_MAX_ORDER];
+    double u[ORACLE_MAX_ORDER];
+    for (int64_t i = i0; i < i1; ++i) {
+        oracle_sobol(n, i, 1, V, X);
+        double uprev = t, vsum = 0.0, jt = 1.0;
+        for (int m = 0; m < n; ++m) {
+            double x = (double)(X[m] ^ S[m]) * 0x1p-32;
+            double jac;
+            double w = learned_w(cdf + (size_t)m * (cells + 1), cells, x, &jac);
+            double v = -tau * log1p(-w);
+            vsum += v;
+            jt *= jac;
+            u[m] = uprev - v;
+            uprev = u[m];
+        }
+        if (!(u[n - 1] > 0.0)) continue;
+        ++inside;
+        double wgt = pow(tau, (double)n) / exp(-vsum / tau) * jt;
+        cplx val = wgt * integrand(&g, n, u, t, NULL);
+        double x = creal(val), s = re_acc + x;
+        re_c += (fabs(re_acc) >= fabs(x)) ? (re_acc - s) + x : (x - s) + re_acc;
+        re_acc = s;
+        x = cimag(val); s = im_acc + x;
+        im_c += (fabs(im_acc) >= fabs(x)) ? (im_acc - s) + x : (x - s) + im_acc;
+        im_acc = s;
+    }
+    result[0] = re_acc;
+    result[1] = im_acc;
+    result[2] = re_c;
+    result[3] = im_c;
+    *n_in = inside;
     return 0;
 }

@@ -66,6 +66,7 @@ static bool valid_params(const qqmc_params *p, std::string &why) {
     if (!isfinite(p->eps_d)) { why = "eps_d must be finite"; return false; }
     if (!(p->t_max > 0) || !isfinite(p->t_max)) { why = "t_max must be > 0"; return false; }
     if (!(p->tau > 0) || !isfinite(p->tau)) { why = "tau must be > 0"; return false; }
+    if (!isfinite(p->alpha)) { why = "alpha must be finite"; return false; }
     if (p->n_table < 4 || p->n_table > (1 << 20) || (p->n_table & 1)) {
         why = "n_table must be even and in 4..2^20";
         return false;
@@ -149,6 +150,7 @@ extern "C" int qqmc_destroy_problem(qqmc_problem *pr) {
     if (!pr) return QQMC_OK;
     cudaFree(pr->d_table);
     cudaFree(pr->d_table32);
+    for (int n = 0; n <= kMaxOrder; ++n) cudaFree(pr->d_proj[n]);
     delete pr;
     return QQMC_OK;
 }
@@ -312,6 +314,9 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         d.L = pr->L;
         d.chunks_per_shift = (int)cps;
         d.flat = lm ? 1 : plan_flat;
+        d.alpha = pr->params.alpha;
+        d.proj = pr->d_proj[it.order];
+        d.proj_cells = pr->proj_cells[it.order];
         if (lm) {
             d.chunk_begin = cl;
             cl += (long long)cps * it.n_shifts;
@@ -643,11 +648,164 @@ extern "C" int qqmc_integrand(const qqmc_problem *pr, int order, uint64_t count,
     it.h = pr->h;
     it.L = pr->L;
     it.order = order;
+    it.alpha = pr->params.alpha;
     Tuning tu = get_tuning(precision, order);
     if (tu.flat < 2) tu.flat = tu.flat_min = 2;  // the check kernel runs one warp per point
     it.flat = tu.flat;
     if (e == cudaSuccess) e = launch_integrand(it, count, d_u.p, d_out.p, precision, tu, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out, d_out.p, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrand");
+    return QQMC_OK;
+}
+
+// ---------------------------------------------------------------- learned warp
+extern "C" int qqmc_set_projection(qqmc_problem *pr, int order, const double *cdf, int cells) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    if (order < 1 || order > kMaxOrder) return set_error(QQMC_E_RANGE, "order outside 1..QQMC_MAX_ORDER");
+    if (!cdf || cells <= 0) {  // back to the plain exponential warp
+        cudaFree(pr->d_proj[order]);
+        pr->d_proj[order] = nullptr;
+        pr->proj_cells[order] = 0;
+        return QQMC_OK;
+    }
+    if (cells > (1 << 20)) return set_error(QQMC_E_INVAL, "cells must be <= 2^20");
+    for (int m = 0; m < order; ++m) {
+        const double *c = cdf + (size_t)m * (cells + 1);
+        if (c[0] != 0.0 || c[cells] != 1.0)
+            return set_error(QQMC_E_INVAL, "each CDF must start at 0 and end at 1");
+        for (int k = 0; k < cells; ++k)
+            if (!(c[k + 1] >= c[k])) return set_error(QQMC_E_INVAL, "each CDF must be non-decreasing");
+    }
+    int rc = ensure_device();
+    if (rc != QQMC_OK) return rc;
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * order * (size_t)(cells + 1);
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(d, cdf, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_error(e, "projection table upload");
+    }
+    cudaFree(pr->d_proj[order]);
+    pr->d_proj[order] = d;
+    pr->proj_cells[order] = cells;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_learn_projection(qqmc_problem *pr, int order, uint64_t M, int n_bins, double lambda,
+                                     double floor_frac, int cells, double *cdf_out) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    if (order < 1 || order > kMaxOrder) return set_error(QQMC_E_RANGE, "order outside 1..QQMC_MAX_ORDER");
+    if (M < 1 || M > (1ull << 24) || n_bins < 1 || n_bins > 65536 || !(lambda > 0) || !(floor_frac >= 0) ||
+        !(floor_frac < 1) || cells < 1 || cells > (1 << 20))
+        return set_error(QQMC_E_INVAL, "qqmc_learn_projection: bad M, n_bins, lambda, floor or cells");
+    int rc = ensure_device();
+    if (rc != QQMC_OK) return rc;
+    const int n = order;
+    // 1. M points of the learning sequence (Sobol' shifted by the words of shift index 65535),
+    //    plain exponential warp, host FP64
+    std::vector<uint32_t> V(32 * kMaxOrder), S(n);
+    direction_numbers(kMaxOrder, V.data());
+    for (int d = 0; d < n; ++d)
+        S[d] = (uint32_t)(splitmix64(pr->params.seed ^ ((uint64_t)65535 * 65536u + (uint64_t)d)) >> 32);
+    const double t = pr->params.t_max, tau = pr->params.tau;
+    std::vector<double> xs((size_t)M * n), wts, us;
+    std::vector<uint64_t> idx_in;
+    for (uint64_t a = 0; a < M; ++a) {
+        const uint64_t g = a ^ (a >> 1);
+        double uprev = t, prod = 1.0, tn = 1.0;
+        std::vector<double> u(n);
+        for (int d = 0; d < n; ++d) {
+            uint32_t X = 0;
+            for (int j = 0; j < 32; ++j)
+                if ((g >> j) & 1u) X ^= V[32 * d + j];
+            const double x = (double)(X ^ S[d]) * 0x1p-32;
+            xs[a * n + d] = x;
+            uprev -= -tau * log1p(-x);
+            u[d] = uprev;
+            prod *= (1.0 - x);
+            tn *= tau;
+        }
+        if (uprev > 0.0) {
+            idx_in.push_back(a);
+            wts.push_back(tn / prod);
+            us.insert(us.end(), u.begin(), u.end());
+        }
+    }
+    // 2. integrand at the in-domain points on the device (FP64, same code as the integration)
+    const uint64_t nin = idx_in.size();
+    std::vector<double> c(2 * nin);
+    if (nin) {
+        double *d_u = nullptr, *d_c = nullptr;
+        cudaError_t e = cudaMalloc(&d_u, sizeof(double) * us.size());
+        if (e == cudaSuccess) e = cudaMalloc(&d_c, sizeof(double) * c.size());
+        if (e == cudaSuccess) e = cudaMemcpy(d_u, us.data(), sizeof(double) * us.size(), cudaMemcpyHostToDevice);
+        ItemDev it{};
+        it.table = pr->d_table;
+        it.table32 = pr->d_table32;
+        it.g0_re = pr->g0_re;
+        it.g0_im = pr->g0_im;
+        it.t = t;
+        it.tau = tau;
+        it.T = t;
+        it.h = pr->h;
+        it.L = pr->L;
+        it.order = n;
+        it.alpha = pr->params.alpha;
+        Tuning tu = get_tuning(QQMC_PREC_FP64, n);
+        if (tu.flat < 2) tu.flat = tu.flat_min = 2;
+        it.flat = tu.flat;
+        if (e == cudaSuccess) e = launch_integrand(it, nin, d_u, d_c, QQMC_PREC_FP64, tu, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(c.data(), d_c, sizeof(double) * c.size(), cudaMemcpyDeviceToHost);
+        cudaFree(d_u);
+        cudaFree(d_c);
+        if (e != cudaSuccess) return cuda_error(e, "qqmc_learn_projection sampling");
+    }
+    // 3. projection of |integrand| onto each dimension (histogram of N_b bins)
+    std::vector<double> hist((size_t)n * n_bins, 0.0);
+    for (uint64_t q = 0; q < nin; ++q) {
+        const double val = wts[q] * hypot(c[2 * q], c[2 * q + 1]) / (double)M;
+        const uint64_t a = idx_in[q];
+        for (int d = 0; d < n; ++d) {
+            int b = (int)(xs[a * n + d] * n_bins);
+            b = b < 0 ? 0 : (b >= n_bins ? n_bins - 1 : b);
+            hist[(size_t)d * n_bins + b] += val;
+        }
+    }
+    // 4. Gaussian kernel smoothing onto the cells, floor, cumulative distribution
+    std::vector<double> cdf((size_t)n * (cells + 1));
+    for (int d = 0; d < n; ++d) {
+        std::vector<double> h(cells);
+        double hmax = 0.0;
+        for (int k = 0; k < cells; ++k) {
+            const double z = (k + 0.5) / cells;
+            double num = 0.0, den = 0.0;
+            for (int l = 0; l < n_bins; ++l) {
+                const double y = (l + 0.5) / n_bins;
+                const double K = exp(-(z - y) * (z - y) / (lambda * lambda));
+                num += K * hist[(size_t)d * n_bins + l];
+                den += K;
+            }
+            h[k] = den > 0 ? num / den : 0.0;
+            hmax = h[k] > hmax ? h[k] : hmax;
+        }
+        double tot = 0.0;
+        for (int k = 0; k < cells; ++k) {
+            if (hmax <= 0.0) h[k] = 1.0;  // no signal: uniform
+            else if (h[k] < floor_frac * hmax) h[k] = floor_frac * hmax;
+            tot += h[k];
+        }
+        double *cd = cdf.data() + (size_t)d * (cells + 1);
+        cd[0] = 0.0;
+        double acc = 0.0;
+        for (int k = 0; k < cells; ++k) {
+            acc += h[k];
+            cd[k + 1] = acc / tot;
+        }
+        cd[cells] = 1.0;
+    }
+    rc = qqmc_set_projection(pr, order, cdf.data(), cells);
+    if (rc != QQMC_OK) return rc;
+    if (cdf_out) memcpy(cdf_out, cdf.data(), sizeof(double) * cdf.size());
     return QQMC_OK;
 }

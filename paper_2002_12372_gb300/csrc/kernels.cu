@@ -421,7 +421,7 @@ __device__ __forceinline__ double warp_total(Acc<R> acc) {
 // Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
 template <class R, int RFMAX>
-__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d,
+__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, double inv_h, double s0, int L, int RF, int lane) {
     const int NP = n_max + 1;
     // 1. pair interpolation, 0 <= j < k <= n
@@ -444,7 +444,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     // right = M(vertex 1, .) / d.
     const int R0 = n - 1;
     const int S0 = 2 * R0 + 2;
-    const cx<R> id = crcp(d);
+    const cx<R> id = crcp(dv);  // pivot of vertex 1
     {
         // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
         const cx<R> P01 = ws.P[1], R01 = ws.Rr[1];
@@ -469,8 +469,9 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
                 right[0] = cmul(ws.P[1 * NP + j], id);
                 right[1] = cmul(ws.Rr[1 * NP + j], id);
             }
-            if (bx == by) {
-                base[0][0] = base[0][1] = base[1][0] = base[1][1] = d;
+            if (bx == by) {  // measurement pair (bx = 0) or a vertex with itself
+                const cx<R> dd = bx == 0 ? d : dv;
+                base[0][0] = base[0][1] = base[1][0] = base[1][1] = dd;
             } else if (bx == 0) {  // measurement row: r_j(aj)
                 const int j = by + 1;
                 base[0][0] = base[1][0] = ws.P[j];
@@ -495,7 +496,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
                 for (int y = 0; y < 2; ++y) o[x * S0 + y] = cfms(base[x][y], left[x], right[y]);
         }
     }
-    if (lane == 0) ws.detD[0] = d;
+    if (lane == 0) ws.detD[0] = dv;
     __syncwarp();
     // 3. depth-first tree over a_2 .. a_{levels+1}
     const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
@@ -566,8 +567,9 @@ __device__ __forceinline__ cx<R> sel(int bit, cx<R> one, cx<R> zero) {
 }
 
 template <class R, int N>
-__device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d, const typename TabT<R>::V *tab,
-                                                       double inv_h, double s0, int L) {
+__device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d, cx<R> dv,
+                                                       const typename TabT<R>::V *tab, double inv_h, double s0,
+                                                       int L) {
     constexpr int M = N + 1;
     cx<R> P[N + 1][N + 1], Rr[N + 1][N + 1];
     double uu[N + 1];
@@ -577,8 +579,8 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
     for (int k = 1; k <= N; ++k)
 #pragma unroll
         for (int j = 0; j < k; ++j) interp_pair<R>(tab, inv_h, s0, L, uu[j] - uu[k], Rr[j][k], P[j][k]);
-    const cx<R> id = crcp(d);
-    // row/column factors of vertex 1 (eliminated first, pivot d)
+    const cx<R> id = crcp(dv);
+    // row/column factors of vertex 1 (eliminated first, pivot dv)
     const cx<R> r1[2] = {P[0][1], Rr[0][1]};
     const cx<R> c1d[2] = {cmul(nconj(Rr[0][1]), id), cmul(nconj(P[0][1]), id)};
     Acc<R> ar, ai;
@@ -606,7 +608,7 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
                 if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
                 cx<R> base;
                 if (x == y) {
-                    base = d;
+                    base = x < 2 ? d : dv;
                 } else if (x < 2) {  // measurement row, vertex y
                     base = sel<R>((path >> (y - 2)) & 1, Rr[0][y], P[0][y]);
                 } else if (y < 2) {  // vertex x, measurement column
@@ -618,7 +620,7 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
                 }
                 m[x][y] = cfms(base, left[x], right[y]);
             }
-        cx<R> detD = d;
+        cx<R> detD = dv;
 #pragma unroll
         for (int p = 2; p < M; ++p) {
             cx<R> pv = m[p][p];
@@ -645,18 +647,6 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
         ai.add(term.im);
     }
     return mk<double>((double)ar.s + (double)ar.c, (double)ai.s + (double)ai.c);
-}
-
-template <class R>
-__device__ __forceinline__ cx<double> lane_keldysh_dispatch(int n, const double *u, cx<R> d,
-                                                            const typename TabT<R>::V *tab, double inv_h, double s0,
-                                                            int L) {
-    switch (n) {
-        case 1: return lane_keldysh_sum<R, 1>(u, d, tab, inv_h, s0, L);
-        case 2: return lane_keldysh_sum<R, 2>(u, d, tab, inv_h, s0, L);
-        case 3: return lane_keldysh_sum<R, 3>(u, d, tab, inv_h, s0, L);
-        default: return lane_keldysh_sum<R, 4>(u, d, tab, inv_h, s0, L);
-    }
 }
 
 // i^n * z
@@ -695,6 +685,36 @@ __device__ __forceinline__ void warp_gap(float, uint32_t y, double tau, double &
     omx = (double)((float)(0x100000000ull - (unsigned long long)y) * 0x1p-32f);
 }
 
+// Learned (projection) warp, paper App. F "learning h from the integrand": the
+// density of w_m in [0, 1) is piecewise constant on `cells` equal cells with
+// CDF values cdf[0] = 0 .. cdf[cells] = 1; x -> w inverts the CDF (bisection
+// for the cell, linear inside it) and dw/dx = 1 / (cells (cdf[k+1] - cdf[k])).
+__device__ __forceinline__ double proj_map(const double *cdf, int cells, double x, double &jac) {
+    int lo = 0, hi = cells;  // cdf[lo] <= x < cdf[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(cdf + mid) <= x) lo = mid; else hi = mid;
+    }
+    const double c0 = __ldg(cdf + lo), dc = __ldg(cdf + lo + 1) - c0;
+    jac = 1.0 / ((double)cells * dc);
+    return ((double)lo + (x - c0) / dc) / (double)cells;
+}
+
+// Gap and weight factors of dimension m for the plain or the learned warp.
+template <class R>
+__device__ __forceinline__ void point_gap(const ItemDev &I, int m, uint32_t y, double &v, double &omx,
+                                          double &jac) {
+    if (I.proj) {
+        const double x = (double)y * 0x1p-32;
+        const double w = proj_map(I.proj + (size_t)m * (I.proj_cells + 1), I.proj_cells, x, jac);
+        v = -I.tau * log1p(-w);
+        omx = 1.0 - w;
+    } else {
+        jac = 1.0;
+        warp_gap(R(0), y, I.tau, v, omx);
+    }
+}
+
 // ----------------------------------------------------------------------------
 // Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
 // ----------------------------------------------------------------------------
@@ -727,23 +747,26 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             const uint64_t i = (uint64_t)(I.first_index + idx);
             double uprev = I.t, prod = 1.0;
             ws.upt[lane * NU] = I.t;
+            double jt = 1.0;
             for (int m = 0; m < n; ++m) {
                 uint32_t y = sobol_word(m, i) ^ I.shifts[k * n + m];
-                double v, omx;
-                warp_gap(R(0), y, I.tau, v, omx);
+                double v, omx, jac;
+                point_gap<R>(I, m, y, v, omx, jac);
                 uprev = uprev - v;
                 ws.upt[lane * NU + 1 + m] = uprev;
                 prod *= omx;
+                jt *= jac;
             }
             inside = uprev > 0.0;
             double tn = 1.0;
             for (int m = 0; m < n; ++m) tn *= I.tau;
-            w = tn / prod;
+            w = tn / prod * jt;
         }
         unsigned mask = __ballot_sync(FULL, inside);
         __syncwarp();
         cx<double> myval = mk<double>(0.0, 0.0);
         const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
+        const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
         const typename TabT<R>::V *tab = item_table<R>(I);
         const double inv_h = 1.0 / I.h;
         const double s0 = I.T * inv_h;
@@ -752,7 +775,8 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
             // every warp-per-point item of a launch shares the launch's flat depth
-            cx<double> s = keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, tab, inv_h, s0, I.L, RFMAX, lane);
+            cx<double> s =
+                keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, inv_h, s0, I.L, RFMAX, lane);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -781,24 +805,26 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
 template <class R, int N>
 __device__ __forceinline__ cx<double> lane_point(const ItemDev &I, int k, uint64_t i, bool &inside) {
     double u[N + 1];
-    double uprev = I.t, prod = 1.0, tn = 1.0;
+    double uprev = I.t, prod = 1.0, tn = 1.0, jt = 1.0;
     u[0] = I.t;
 #pragma unroll
     for (int m = 0; m < N; ++m) {
         uint32_t y = sobol_word(m, i) ^ I.shifts[k * N + m];
-        double v, omx;
-        warp_gap(R(0), y, I.tau, v, omx);
+        double v, omx, jac;
+        point_gap<R>(I, m, y, v, omx, jac);
         uprev = uprev - v;
         u[m + 1] = uprev;
         prod *= omx;
         tn *= I.tau;
+        jt *= jac;
     }
     inside = uprev > 0.0;
     if (!inside) return mk<double>(0.0, 0.0);
-    const double w = tn / prod;
+    const double w = tn / prod * jt;
     const double inv_h = 1.0 / I.h;
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
-    cx<double> s = lane_keldysh_sum<R, N>(u, d, item_table<R>(I), inv_h, I.T * inv_h, I.L);
+    const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
+    cx<double> s = lane_keldysh_sum<R, N>(u, d, dv, item_table<R>(I), inv_h, I.T * inv_h, I.L);
     cx<double> c = times_i_pow(s, N);
     return mk<double>(w * c.re, w * c.im);
 }
@@ -941,8 +967,10 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     }
     __syncwarp();
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
+    const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
     const double inv_h = 1.0 / I.h;
-    cx<double> s = keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, item_table<R>(I), inv_h, I.T * inv_h, I.L, RF, lane);
+    cx<double> s =
+        keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), inv_h, I.T * inv_h, I.L, RF, lane);
     if (lane == 0) {
         cx<double> cval = times_i_pow(s, n);
         out[2 * q] = cval.re;
@@ -1193,8 +1221,10 @@ cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_
 template <class R, int F>
 static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
                                       cudaStream_t s) {
-    const int wpb = 2;
-    size_t smem = warp_smem_bytes<R>(item.order, F) * wpb;
+    const size_t per_warp = warp_smem_bytes<R>(item.order, F);
+    if (per_warp > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const int wpb = per_warp * 2 <= 227 * 1024 ? 2 : 1;
+    size_t smem = per_warp * wpb;
     cudaError_t e =
         cudaFuncSetAttribute(integrand_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -100,6 +100,9 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     it.n_shifts = n_shifts;
     it.L = P->L;
     it.chunks_per_shift = (int)cps;
+    it.alpha = P->params.alpha;
+    it.proj = P->d_proj[order];
+    it.proj_cells = P->proj_cells[order];
     Tuning tu = get_tuning(precision, order);
     it.flat = tu.flat;
     if (it.flat < 2 && order > 4) it.flat = 2;

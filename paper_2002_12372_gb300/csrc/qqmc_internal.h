@@ -24,6 +24,8 @@ struct Problem {
     dbl4 *d_table = nullptr;  // [L/2 + 1]: (gl.re, gl.im, gg.re, gg.im) at nodes k = L/2-1 .. L-1
     float4 *d_table32 = nullptr; // same, FP32 (mixed precision)
     int device = 0;
+    double *d_proj[kMaxOrder + 1] = {};  // learned warp per order: [order][proj_cells[order] + 1]
+    int proj_cells[kMaxOrder + 1] = {};
 };
 
 // One item as the device sees it.
@@ -39,6 +41,9 @@ struct ItemDev {
     long long chunk_begin;   // first global chunk of this item
     int order, n_shifts, L, chunks_per_shift;
     int flat;                // vertices resolved per lane for this item (its order's tuning)
+    const double *proj;      // learned warp: [order][proj_cells + 1] CDF per dimension, or null (plain)
+    int proj_cells;
+    double alpha;            // quadratic shift: vertex diagonals are g^<(0) - i alpha
 };
 
 struct Tuning {

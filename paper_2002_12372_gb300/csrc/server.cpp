@@ -295,7 +295,8 @@ extern "C" int qqmc_submit(qqmc_server *s, const qqmc_request *r, uint64_t *hand
     if (r->n_points < 1 || r->n_points > (1ull << QQMC_MAX_POINTS_LOG2))
         return set_error(QQMC_E_INVAL, "n_points must be in 1..2^30");
     const qqmc_params &p = r->params;
-    if (!(p.gamma > 0) || !(p.t_max > 0) || !(p.tau > 0) || p.n_table < 4 || (p.n_table & 1) || !isfinite(p.eps_d))
+    if (!(p.gamma > 0) || !(p.t_max > 0) || !(p.tau > 0) || p.n_table < 4 || (p.n_table & 1) || !isfinite(p.eps_d) ||
+        !isfinite(p.alpha))
         return set_error(QQMC_E_INVAL, "malformed request parameters");
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return set_error(QQMC_E_CANCELLED, "server is shutting down");

@@ -39,14 +39,15 @@ EXPORTED = [
     "qqmc_plan_kernel_count", "qqmc_plan_timing", "qqmc_set_tuning", "qqmc_get_tuning", "qqmc_direction_numbers",
     "qqmc_shift_words", "qqmc_sobol_points", "qqmc_warp_points", "qqmc_integrand", "qqmc_server_create",
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
-    "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola",
+    "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola", "qqmc_set_projection",
+    "qqmc_learn_projection",
 ]
 
 
 class qqmc_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("eps_d", ctypes.c_double), ("t_max", ctypes.c_double),
                 ("tau", ctypes.c_double), ("n_table", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("alpha", ctypes.c_double)]
 
 
 class qqmc_result(ctypes.Structure):
@@ -122,6 +123,9 @@ def load(path: str = LIB_PATH):
         "qqmc_integrate_noalloc": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
         "qqmc_plan_chunk_sums": [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, dp],
         "qqmc_resum_parabola": [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp],
+        "qqmc_set_projection": [vp, ctypes.c_int, dp, ctypes.c_int],
+        "qqmc_learn_projection": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -340,6 +344,25 @@ def qqmc_resum_parabola(a, p: float, U: float, a_err=None, invert: bool = False)
     return v.value, er.value, t.value
 
 
+def qqmc_set_projection(pr: int, order: int, cdf=None) -> None:
+    """Install a learned warp (cdf [order, cells + 1]) or, with None, restore the plain warp."""
+    if cdf is None:
+        _check(load().qqmc_set_projection(ctypes.c_void_p(pr), order, None, 0), "qqmc_set_projection")
+        return
+    c = np.ascontiguousarray(np.asarray(cdf, dtype=np.float64))
+    _check(load().qqmc_set_projection(ctypes.c_void_p(pr), order, _ptr(c, ctypes.c_double), c.shape[1] - 1),
+           "qqmc_set_projection")
+
+
+def qqmc_learn_projection(pr: int, order: int, M: int = 20000, n_bins: int = 100, lam: float = 0.05,
+                          floor_frac: float = 1e-3, cells: int = 1024) -> np.ndarray:
+    """Learn, install and return the warp table [order, cells + 1]."""
+    out = np.zeros((order, cells + 1))
+    _check(load().qqmc_learn_projection(ctypes.c_void_p(pr), order, M, n_bins, lam, floor_frac, cells,
+                                        _ptr(out, ctypes.c_double)), "qqmc_learn_projection")
+    return out
+
+
 def qqmc_server_create(opts: qqmc_server_opts) -> int:
     out = ctypes.c_void_p()
     _check(load().qqmc_server_create(ctypes.byref(opts), ctypes.byref(out)), "qqmc_server_create")
@@ -369,5 +392,6 @@ def qqmc_server_destroy(server: int) -> None:
     load().qqmc_server_destroy(ctypes.c_void_p(server))
 
 
-def make_params(gamma=1.0, eps_d=0.0, t_max=10.0, tau=1.0, n_table=4096, seed=2002123720) -> qqmc_params:
-    return qqmc_params(gamma, eps_d, t_max, tau, n_table, 0, seed)
+def make_params(gamma=1.0, eps_d=0.0, t_max=10.0, tau=1.0, n_table=4096, seed=2002123720,
+                alpha=0.0) -> qqmc_params:
+    return qqmc_params(gamma, eps_d, t_max, tau, n_table, 0, seed, alpha)

@@ -134,3 +134,18 @@ def serving_sweep(seed: int = SEED, n_requests: int = 256, rate_hz: float = 50.0
                            n_points=int(2 ** math.floor(rng.uniform(log2_min, log2_max + 1e-9))),
                            n_shifts=n_shifts))
     return out
+
+
+def synthetic_projection(seed: int, n: int, cells: int = 1024) -> np.ndarray:
+    """Seeded warp tables [n, cells + 1]: per dimension the cumulative sums of a
+    positive smooth density on `cells` equal cells (1 + a sin(2 pi (f z + phi))
+    with a in [0.3, 0.9]), normalised to end at 1."""
+    rng = np.random.default_rng(seed)
+    z = (np.arange(cells) + 0.5) / cells
+    out = np.zeros((n, cells + 1))
+    for d in range(n):
+        a, f, phi = rng.uniform(0.3, 0.9), rng.uniform(0.5, 3.0), rng.uniform(0.0, 1.0)
+        h = 1.0 + a * np.sin(2 * np.pi * (f * z + phi))
+        out[d, 1:] = np.cumsum(h) / h.sum()
+        out[d, -1] = 1.0
+    return out

@@ -1,0 +1,125 @@
+"""Quadratic shift alpha of the interaction (App. E): U n_up n_down is written
+U (n_up - alpha)(n_down - alpha), which moves every vertex diagonal of the
+Keldysh matrices from g^<(0) to g^<(0) - i alpha and leaves the measurement
+pair alone.
+
+CPU pins of the oracle against things other than itself, then parity of the
+CUDA path with the oracle at alpha != 0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+# ------------------------------------------------------------ oracle pins ---
+
+@pytest.mark.parametrize("eps", [0.0, 0.7])
+def test_alpha_at_the_occupation_removes_order_one(oracle, eps):
+    """alpha = <n_sigma> = Im g^<(0): the shifted vertex density vanishes, so the
+    one-vertex spin-down determinant is zero and c_1(u) = 0 at every u."""
+    T = 10.0
+    tabs = oracle.gf_tables(1.0, eps, T, 4096)
+    n0 = float(np.imag(tabs[2]))
+    u = np.linspace(0.0, T, 257).reshape(-1, 1)
+    c0 = oracle.integrand(1, u, T, tabs, T)
+    c = oracle.integrand(1, u, T, tabs, T, alpha=n0)
+    assert np.max(np.abs(c0)) > 1e-3
+    assert np.max(np.abs(c)) <= 1e-15
+
+
+def _q1_quadrature(oracle, tabs, t, alpha):
+    """-2i int_0^t c_1(u) du by Gauss-Legendre on panels graded towards u = t."""
+    x, w = np.polynomial.legendre.leggauss(20)
+    edges = np.unique(np.concatenate([np.linspace(0.0, t - 4.0, 27), t - 4.0 + np.linspace(0.0, 4.0, 129)]))
+    pts, wts = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        pts.append(0.5 * (b - a) * x + 0.5 * (a + b))
+        wts.append(0.5 * (b - a) * w)
+    pts, wts = np.concatenate(pts), np.concatenate(wts)
+    c = oracle.integrand(1, pts.reshape(-1, 1), t, tabs, t, alpha=alpha)
+    return float(np.sum(wts * (-2j * c).real))
+
+
+@pytest.mark.parametrize("eps,gamma,alpha", [(0.0, 1.0, 0.3), (0.8, 1.0, -0.45), (-0.5, 0.7, 0.5)])
+def test_alpha_moves_q1_by_the_static_charge_susceptibility(oracle, eps, gamma, alpha):
+    """U (n_up - a)(n_down - a) = U n_up n_down - U a (n_up + n_down) + const: at first
+    order in U the shift is a level shift eps_d -> eps_d - U a, so in the steady state
+    Q_1(a) - Q_1(0) = -a dQ_0/d eps_d = 2 a / (pi Gamma (1 + (eps_d / Gamma)^2)) with
+    Q_0 = 1 - 2 arctan(eps_d / Gamma) / pi.  At t = 30 / Gamma the transient is below 1e-6."""
+    t = 30.0 / gamma
+    tabs = oracle.gf_tables(gamma, eps, t, 65536)
+    d = _q1_quadrature(oracle, tabs, t, alpha) - _q1_quadrature(oracle, tabs, t, 0.0)
+    exact = 2.0 * alpha / (math.pi * gamma * (1.0 + (eps / gamma) ** 2))
+    assert abs(d - exact) < 2e-5 * abs(exact), (d, exact)
+
+
+def test_alpha_is_linear_in_the_keldysh_sum_at_order_one(oracle):
+    """At order 1 the alpha^2 term of det M_up det M_down does not depend on the Keldysh
+    index and cancels in the signed sum: c_1 is affine in alpha."""
+    T = 10.0
+    tabs = oracle.gf_tables(1.0, 0.3, T, 4096)
+    u = np.linspace(0.05, T, 61).reshape(-1, 1)
+    c = [oracle.integrand(1, u, T, tabs, T, alpha=a) for a in (0.0, 0.5, 1.0)]
+    second = c[2] - 2.0 * c[1] + c[0]
+    assert np.max(np.abs(second)) <= 1e-14 * np.max(np.abs(c[0]))
+
+
+# ------------------------------------------------------------- GPU parity ---
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2002_12372_gb300 import build as b
+    b.build()
+    from paper_2002_12372_gb300 import qqmc
+    qqmc.load()
+    return qqmc
+
+
+def _problem(Q, seed, T, alpha, L=4096):
+    from paper_2002_12372_gb300 import workloads as W
+    gl, gg, g0, _ = W.synthetic_tables(seed, L, T)
+    p = Q.make_params(t_max=T, n_table=L, alpha=alpha)
+    return Q.qqmc_create_problem_tables(p, gl, gg, g0), (gl, gg, g0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order,count", [(1, 64), (2, 64), (4, 32), (6, 16), (9, 6), (12, 2)])
+def test_integrand_with_alpha_matches_oracle(Q, oracle, order, count):
+    from paper_2002_12372_gb300 import workloads as W
+    T, alpha = 10.0, 0.37
+    pr, tabs = _problem(Q, 500 + order, T, alpha)
+    try:
+        u = W.ordered_times(600 + order, count, order, T)
+        gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)
+        mixed = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_MIXED)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    ref, scale = oracle.integrand(order, u, T, tabs, T, return_abs=True, alpha=alpha)
+    assert np.all(np.abs(gpu - ref) <= 1e-12 * scale), np.max(np.abs(gpu - ref) / scale)
+    assert np.all(np.abs(mixed - ref) <= 2.0 ** -20 * scale), np.max(np.abs(mixed - ref) / scale)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("lane", [False, True])
+def test_integration_with_alpha_matches_oracle(Q, oracle, lane):
+    """Both determinant kernels (cooperative warp and one point per lane) at alpha != 0."""
+    from paper_2002_12372_gb300 import autotune
+    from paper_2002_12372_gb300 import workloads as W
+    T, K, alpha = 10.0, 3, -0.6
+    pr, tabs = _problem(Q, 81, T, alpha)
+    try:
+        for n in range(1, 5):
+            Q.qqmc_set_tuning(Q.QQMC_PREC_FP64, n, 2, 1 if lane else 2)
+        for n, N in [(1, 2049), (3, 1000), (4, 777), (7, 200)]:
+            sw = W.shift_words(700 + n, K, n)
+            res, S = Q.qqmc_integrate(pr, n, N, K, Q.QQMC_PREC_FP64, sw)
+            S0, nin = oracle.estimate(n, N, sw, T, 1.0, tabs, T, alpha=alpha)
+            assert res.n_in_domain == int(nin.sum())
+            assert np.all(np.abs(S - S0) <= 1e-10 * np.abs(S0)), (n, S, S0)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+        autotune.reset()
