@@ -267,7 +267,8 @@ def run_ours(args, ws, rank, local, pg):
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d // e2e_steps,
                 "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": _launch_traffic(args, slice_n),
                      "kernel": "detsum_kernel<%s,%d>" % ("double" if args.precision == "fp64" else "float", flat),
                      "peak_source": "derived: 152 SMs x %d %s FMA lanes x 2 flops x 2070 MHz" % (
                          perf.FP64_LANES if args.precision == "fp64" else perf.FP32_LANES, args.precision),
@@ -279,6 +280,18 @@ def run_ours(args, ws, rank, local, pg):
     for pr in problems:
         Q.qqmc_destroy_problem(pr)
     return out
+
+
+# DRAM bytes (read + write) of one detsum launch of the default benchmark step,
+# from a 1-pass ncu capture of this exact command (profiles/detsum_*_plain-dot_n1-10.md).
+# Set to None whenever the determinant kernel changes until it is captured again.
+MEASURED_LAUNCH_TRAFFIC = {"fp64": 1.08e6 + 1.08e6, "mixed": 588.54e3 + 544.51e3}
+
+
+def _launch_traffic(args, slice_n):
+    if args.config != "plain" or slice_n != 2 ** 16:
+        return None
+    return MEASURED_LAUNCH_TRAFFIC.get(args.precision)
 
 
 def _setup(args, local):
