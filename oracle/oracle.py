@@ -1,7 +1,9 @@
 """ORACLE -- test infrastructure only.
 
-Plain, slow CPU restatement of the QQMC estimator for the charge coefficients
-Q_n of the Anderson single-level dot (wide-band leads, T = 0, zero bias).
+Plain, slow CPU restatement of the QQMC estimator for the perturbative
+coefficients of the Anderson single-level dot at T = 0: the charge Q_n
+(wide-band or semicircular leads) and the current I_n (semicircular leads of
+half-bandwidth D under a symmetric bias V).
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  It shares no code with the CUDA path
 and imports nothing from the product package; inputs (shift words, synthetic
@@ -32,9 +34,15 @@ Pieces and the passages they follow:
   Eq. (warper1d) with App. F Eq. (hi_expo); estimator Eq. (warped_int2)).
 * ``integrand`` -- App. E Eq. (integral_gf): naive sum over all 2^n Keldysh
   index vectors of det M_up * det M_down, each by pivoted LU.
-* ``q_from_sums`` / ``shift_statistics`` -- readout Q_n = -2i c_n and the
-  randomised-QMC error bar (App. G, App. H: standard deviation over the K
-  shifted sequences divided by sqrt(K)).
+* ``lead_functions`` / ``lead_tables`` -- finite-bandwidth leads, App. E
+  (semicircular hybridisation Delta(w), bias V, Eq. (lesser_greater_freq) for
+  g_00 and the dot-lead function gamma g_01), Fourier transformed by adaptive
+  quadrature; ``landauer_current`` and ``lead_occupation`` are independent 1-D
+  integrals used by the pins.
+* ``q_from_sums`` / ``i_from_sums`` / ``shift_statistics`` -- readouts
+  Q_n = -2i c_n and I_n = -4 Re c_n (measurement column on lead site 1, App. E
+  "i = 1"), and the randomised-QMC error bar (App. G, App. H: standard
+  deviation over the K shifted sequences divided by sqrt(K)).
 """
 from __future__ import annotations
 
@@ -80,18 +88,20 @@ def lib():
         u32p = ctypes.POINTER(ctypes.c_uint32)
         i64 = ctypes.c_int64
         L.oracle_integrand.argtypes = [ctypes.c_int, i64, dp, ctypes.c_double, dp, dp, ctypes.c_int,
-                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double]
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double,
+                                       dp]
         L.oracle_sobol.argtypes = [ctypes.c_int, i64, i64, u32p, u32p]
         L.oracle_estimate.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
                                       ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64), ctypes.c_double]
+                                      ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64), ctypes.c_double,
+                                      dp]
         L.oracle_warp.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
                                   ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int32)]
         L.oracle_det.argtypes = [ctypes.c_int, dp, dp]
         L.oracle_estimate_proj.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double, ctypes.c_double,
                                            dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64),
-                                           ctypes.c_double]
+                                           ctypes.c_double, dp]
         L.oracle_table_at.argtypes = [dp, ctypes.c_int, ctypes.c_double, i64, dp, dp]
         _lib = L
     return _lib
@@ -182,6 +192,117 @@ def gf_tables(gamma: float, eps_d: float, T: float, L: int = 4096):
 
 
 # --------------------------------------------------------------------------
+# Semicircular leads at finite half-bandwidth D and symmetric bias V (App. E)
+# --------------------------------------------------------------------------
+#
+# Hybridisation of both leads, App. E: inside the band |w| < D,
+#     Delta(w) = (Gamma / D) (w - i sqrt(D^2 - w^2)),  Gamma(w) = -Im Delta(w),
+# g^R = 1 / (w - E_d - Delta); each lead carries Delta / 2.  Lead L has Fermi
+# level +V/2, lead R (the one holding site 1) -V/2; T = 0 Fermi functions
+# f_L = theta(V/2 - w), f_R = theta(-V/2 - w).  Keldysh functions in the
+# textbook normalisation of the charge tables (g^< = i A f; the paper's
+# Eq. (lesser_greater_freq) differs by an overall factor, see the reading in
+# the design notes):
+#     g^<_00 =  i Gamma(w) |g^R|^2 (f_L + f_R)
+#     g^>_00 = -i Gamma(w) |g^R|^2 (2 - f_L - f_R)
+# and, from the Dyson equation G_01 = G_00 gamma g_11 with the Langreth rule
+# (AB)^< = A^R B^< + A^< B^A and gamma^2 g_11 = Delta / 2:
+#     gamma g^<_01 =  i f_R Gamma(w) g^R + (Delta^* / 2) g^<_00
+#     gamma g^>_01 = -i (1 - f_R) Gamma(w) g^R + (Delta^* / 2) g^>_00.
+# Outside the band Gamma(w) = 0 and all four vanish (no bound state exists for
+# |E_d| < D - Gamma).  Time domain: g(tau) = Int dw/2pi e^{-i w tau} g(w).
+# With w = D sin(theta) the square root becomes Gamma cos(theta) and every
+# integrand is smooth in theta between the Fermi steps.
+
+def _lead_spectra(theta, gamma: float, Ed: float, D: float, V: float):
+    """[g^<_00, g^>_00, gamma g^<_01, gamma g^>_01](w(theta)) * (dw/dtheta) / 2pi, and w."""
+    theta = np.asarray(theta, dtype=np.float64)
+    w = D * np.sin(theta)
+    G = gamma * np.cos(theta)
+    delta = gamma * (np.sin(theta) - 1j * np.cos(theta))
+    gR = 1.0 / (w - Ed - delta)
+    fL = (w < 0.5 * V).astype(np.float64)
+    fR = (w < -0.5 * V).astype(np.float64)
+    a2 = np.abs(gR) ** 2
+    gl = 1j * G * a2 * (fL + fR)
+    gg = -1j * G * a2 * (2.0 - fL - fR)
+    cl = 1j * fR * G * gR + 0.5 * np.conj(delta) * gl
+    cg = -1j * (1.0 - fR) * G * gR + 0.5 * np.conj(delta) * gg
+    jac = D * np.cos(theta) / (2.0 * np.pi)
+    return w, np.stack([gl, gg, cl, cg]) * jac
+
+
+def _theta_breaks(D: float, V: float):
+    b = [-0.5 * math.pi]
+    if 0.5 * V < D:
+        b += sorted({math.asin(-0.5 * V / D), math.asin(0.5 * V / D)})
+    return b + [0.5 * math.pi]
+
+
+def lead_functions(tau, gamma: float, Ed: float, D: float, V: float = 0.0, epsabs: float = 1e-13):
+    """[4, len(tau)] complex: g^<_00, g^>_00, gamma g^<_01, gamma g^>_01 at tau, by adaptive
+    vector quadrature (scipy quad_vec) of the Fourier integral in theta, split at the Fermi steps."""
+    from scipy.integrate import quad_vec
+
+    tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
+
+    def f(th):
+        w, S = _lead_spectra(th, gamma, Ed, D, V)
+        z = S[:, None] * np.exp(-1j * w * tau)[None, :]
+        return np.concatenate([z.real.ravel(), z.imag.ravel()])
+
+    br = _theta_breaks(D, V)
+    tot = np.zeros(8 * tau.size)
+    for a, b in zip(br[:-1], br[1:]):
+        if b > a:
+            val, _err = quad_vec(f, a, b, epsabs=epsabs, epsrel=1e-13, norm="max", limit=200000)
+            tot += val
+    m = 4 * tau.size
+    return (tot[:m] + 1j * tot[m:]).reshape(4, tau.size)
+
+
+def lead_tables(gamma: float, Ed: float, D: float, V: float, T: float, L: int):
+    """Tables of the finite-bandwidth dot on ``table_nodes(T, L)``:
+    ((g^<_00, g^>_00, g^<_00(0)), (gamma g^<_01, gamma g^>_01, gamma g^<_01(0)))."""
+    nodes = np.concatenate([table_nodes(T, L), [0.0]])
+    F = lead_functions(nodes, gamma, Ed, D, V)
+    return (F[0, :L], F[1, :L], complex(F[0, L])), (F[2, :L], F[3, :L], complex(F[2, L]))
+
+
+def landauer_current(gamma: float, Ed: float, D: float, V: float) -> float:
+    """Non-interacting current, both spins: (1/pi) Int_{-V/2}^{V/2} Gamma(w)^2 |g^R(w)|^2 dw."""
+    from scipy.integrate import quad
+
+    def T(w):
+        s = math.sqrt(max(D * D - w * w, 0.0))
+        G = gamma / D * s
+        den = complex(w - Ed - gamma / D * w, G)
+        return G * G / abs(den) ** 2
+
+    a = 0.5 * min(V, 2 * D)
+    return quad(T, -a, a, epsabs=1e-15, epsrel=1e-13, limit=500, points=[Ed] if -a < Ed < a else None)[0] / math.pi
+
+
+def lead_occupation(gamma: float, Ed: float, D: float, V: float) -> float:
+    """<n_sigma> = Int dw/2pi Gamma(w) |g^R|^2 (f_L + f_R), by quadrature in w."""
+    from scipy.integrate import quad
+
+    def A(w):
+        s = math.sqrt(max(D * D - w * w, 0.0))
+        G = gamma / D * s
+        den = complex(w - Ed - gamma / D * w, G)
+        return G / abs(den) ** 2 / (2.0 * math.pi)
+
+    tot = 0.0
+    for mu in (0.5 * V, -0.5 * V):
+        hi = min(mu, D)
+        if hi > -D:
+            pts = [Ed] if -D < Ed < hi else None
+            tot += quad(A, -D, hi, epsabs=1e-15, epsrel=1e-13, limit=500, points=pts)[0]
+    return tot
+
+
+# --------------------------------------------------------------------------
 # Sobol' direction numbers (library primitive: scipy's unscrambled generator)
 # --------------------------------------------------------------------------
 
@@ -246,9 +367,27 @@ def _tab(a: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
 
 
-def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: bool = False, alpha: float = 0.0):
+def _col(col, L: int):
+    """Packed dot-lead tables for the current (None for the charge):
+    col = (gamma g^<_01 [L], gamma g^>_01 [L], gamma g^<_01(0))."""
+    if col is None:
+        return None
+    cl, cg, c0 = col
+    cl, cg = _tab(cl), _tab(cg)
+    if cl.size != 2 * L or cg.size != 2 * L:
+        raise ValueError("dot-lead tables must be on the same mesh as the dot tables")
+    return np.ascontiguousarray(np.concatenate([cl, cg, [float(np.real(c0)), float(np.imag(c0))]]))
+
+
+def _cp(a):
+    return None if a is None else _dp(a)
+
+
+def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: bool = False, alpha: float = 0.0,
+              col=None):
     """c(u) of App. E Eq. (integral_gf) at each row of u ([count, n], any time order);
-    alpha: quadratic shift of the vertex diagonals (App. E)."""
+    alpha: quadratic shift of the vertex diagonals (App. E); col: dot-lead tables
+    (gamma g^<_01, gamma g^>_01, gamma g^<_01(0)) for the current, None for the charge."""
     gl, gg, gl0 = tables
     u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)).reshape(-1, n))
     count = u.shape[0]
@@ -256,8 +395,10 @@ def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: boo
     L = gl_t.size // 2
     out = np.zeros(2 * count)
     ab = np.zeros(count)
+    cp = _col(col, L)
     rc = lib().oracle_integrand(n, count, _dp(u), t, _dp(gl_t), _dp(gg_t), L, T,
-                                float(np.real(gl0)), float(np.imag(gl0)), _dp(out), _dp(ab), float(alpha))
+                                float(np.real(gl0)), float(np.imag(gl0)), _dp(out), _dp(ab), float(alpha),
+                                _cp(cp))
     if rc != 0:
         raise ValueError("oracle_integrand rejected its arguments")
     val = out[0::2] + 1j * out[1::2]
@@ -283,12 +424,12 @@ def table_at(table: np.ndarray, T: float, tau: np.ndarray) -> np.ndarray:
 
 
 def _estimate_chunk(args):
-    n, i0, i1, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha = args
+    n, i0, i1, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha, cp = args
     res = np.zeros(4)
     n_in = ctypes.c_int64(0)
     rc = lib().oracle_estimate(n, i0, i1, _u32p(Vc), _u32p(S), t, tau, _dp(gl_t), _dp(gg_t), L, T,
                                float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in),
-                               float(alpha))
+                               float(alpha), _cp(cp))
     if rc != 0:
         raise ValueError("oracle_estimate rejected its arguments")
     return res, n_in.value
@@ -296,7 +437,7 @@ def _estimate_chunk(args):
 
 def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T: float,
              V: np.ndarray | None = None, threads: int | None = None, i0: int = 0,
-             chunk: int = 4096, alpha: float = 0.0):
+             chunk: int = 4096, alpha: float = 0.0, col=None):
     """Per-shift estimates S_k = (1/N) sum_{i=i0}^{i0+N-1} w_i c(u_i), Eq. (warped_int2).
 
     shifts: uint32 [K, >= n] digital-shift words.  Returns (S [K] complex,
@@ -310,6 +451,7 @@ def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T
     gl, gg, gl0 = tables
     gl_t, gg_t = _tab(gl), _tab(gg)
     L = gl_t.size // 2
+    cp = _col(col, L)
     shifts = np.atleast_2d(np.asarray(shifts, dtype=np.uint32))
     K = shifts.shape[0]
     jobs = []
@@ -317,7 +459,7 @@ def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T
         S = np.ascontiguousarray(shifts[k, :n])
         for a in range(i0, i0 + N, chunk):
             b = min(a + chunk, i0 + N)
-            jobs.append((k, (n, a, b, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha)))
+            jobs.append((k, (n, a, b, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha, cp)))
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(max_workers=threads) as ex:
         results = list(ex.map(_estimate_chunk, [j[1] for j in jobs]))
@@ -335,6 +477,15 @@ def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T
 def q_from_sums(S: np.ndarray) -> np.ndarray:
     """Q_n^{(k)} = -2i * S_k (readout of the charge from G^<(t,t) = i<n_up>)."""
     return -2j * np.asarray(S)
+
+
+def i_from_sums(S: np.ndarray) -> np.ndarray:
+    """I_n^{(k)} = -4 Re S_k: current from the dot into lead site 1, both spins.
+
+    Per spin dN_R/dt = i[H, N_R] = -2 gamma Im<c_0^+ c_1>, and with the
+    textbook G^<_{01}(t,t) = i<c_1^+ c_0> this is -2 Re(gamma G^<_{01}(t,t));
+    S carries gamma G^<_{01} because the measurement column holds gamma g_01."""
+    return -4.0 * np.real(np.asarray(S))
 
 
 def shift_statistics(values: np.ndarray):
@@ -446,19 +597,20 @@ def learn_projection(n: int, M: int, seed: int, t: float, tau: float, tables, T:
 
 
 def _estimate_proj_chunk(args):
-    n, i0, i1, Vc, S, t, tau, cdf, cells, gl_t, gg_t, L, T, gl0, alpha = args
+    n, i0, i1, Vc, S, t, tau, cdf, cells, gl_t, gg_t, L, T, gl0, alpha, cp = args
     res = np.zeros(4)
     n_in = ctypes.c_int64(0)
     rc = lib().oracle_estimate_proj(n, i0, i1, _u32p(Vc), _u32p(S), t, tau, _dp(cdf), cells, _dp(gl_t), _dp(gg_t),
                                     L, T, float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in),
-                                    float(alpha))
+                                    float(alpha), _cp(cp))
     if rc != 0:
         raise ValueError("oracle_estimate_proj rejected its arguments")
     return res, n_in.value
 
 
 def estimate_proj(n: int, N: int, shifts: np.ndarray, t: float, tau: float, cdf: np.ndarray, tables, T: float,
-                  V: np.ndarray | None = None, threads: int | None = None, chunk: int = 4096, alpha: float = 0.0):
+                  V: np.ndarray | None = None, threads: int | None = None, chunk: int = 4096, alpha: float = 0.0,
+                  col=None):
     """Per-shift estimates with the learned warp (same contract as ``estimate``)."""
     if V is None:
         V = sobol_direction_numbers(max(n, 1))
@@ -468,13 +620,15 @@ def estimate_proj(n: int, N: int, shifts: np.ndarray, t: float, tau: float, cdf:
     gl, gg, gl0 = tables
     gl_t, gg_t = _tab(gl), _tab(gg)
     L = gl_t.size // 2
+    cp = _col(col, L)
     shifts = np.atleast_2d(np.asarray(shifts, dtype=np.uint32))
     K = shifts.shape[0]
     jobs = []
     for k in range(K):
         S = np.ascontiguousarray(shifts[k, :n])
         for a in range(0, N, chunk):
-            jobs.append((k, (n, a, min(a + chunk, N), Vc, S, t, tau, cdf, cells, gl_t, gg_t, L, T, gl0, alpha)))
+            jobs.append((k, (n, a, min(a + chunk, N), Vc, S, t, tau, cdf, cells, gl_t, gg_t, L, T, gl0, alpha,
+                             cp)))
     with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
         results = list(ex.map(_estimate_proj_chunk, [j[1] for j in jobs]))
     re_parts = [[] for _ in range(K)]

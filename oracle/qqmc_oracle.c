@@ -2,8 +2,9 @@
  * ORACLE -- test infrastructure only.
  *
  * Plain, slow, obviously-correct CPU restatement of the quantum quasi-Monte
- * Carlo (QQMC) estimator for the order-n charge coefficient Q_n of the
- * Anderson single-level dot.  Only tests, the smoke check and the CPU-baseline
+ * Carlo (QQMC) estimator for the order-n coefficient of the equal-time lesser
+ * function G^<_{0i}(t,t) of the Anderson single-level dot: i = 0 gives the
+ * charge Q_n, i = 1 (dot-lead) the current I_n (App. E).  Only tests, the smoke check and the CPU-baseline
  * leg of the benchmark may load this code; the product never does.  It shares
  * no source with the CUDA path.
  *
@@ -59,7 +60,25 @@ typedef struct {
     double T;         /* table covers [-T, T] */
     cplx gl0;         /* g^<(0): the equal-time value of the measurement pair */
     cplx dv;          /* diagonal of a vertex: g^<(0) - i alpha (App. E, quadratic shift alpha) */
+    /* Current (i = 1): the measurement column point sits on lead site 1, so the
+     * entries of column 0 are dot-lead functions.  cl, cg: gamma g^<_{01},
+     * gamma g^>_{01} on the same mesh; c0 = gamma g^<_{01}(0).  cl == NULL for
+     * the charge. */
+    const double *cl, *cg;
+    cplx c0;
 } gf_t;
+
+/* col: NULL (charge) or [gamma g^<_01 (2L doubles) | gamma g^>_01 (2L) | re, im of gamma g^<_01(0)]. */
+static gf_t make_gf(const double *gl, const double *gg, int L, double T, double gl0_re, double gl0_im,
+                    double alpha, const double *col) {
+    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im, gl0_re + I * (gl0_im - alpha), NULL, NULL, 0.0};
+    if (col) {
+        g.cl = col;
+        g.cg = col + 2 * L;
+        g.c0 = col[4 * L] + I * col[4 * L + 1];
+    }
+    return g;
+}
 
 /*
  * Keldysh Green function between two contour points (time u, Keldysh index a)
@@ -69,18 +88,22 @@ typedef struct {
  * `same` marks a point paired with itself: 1 = the measurement pair, whose
  * entry is g^<(0); 2 = a vertex on the diagonal, g^<(0) shifted by -i alpha
  * (App. E: every diagonal except the one of the measurement point).
+ * `lead`: the second point is on lead site 1 (current measurement column):
+ * the dot-lead tables replace the dot-dot ones.
  */
-static cplx keldysh_g(const gf_t *g, double u, int a, double up, int ap, int same) {
-    if (same == 1) return g->gl0;
+static cplx keldysh_g(const gf_t *g, double u, int a, double up, int ap, int same, int lead) {
+    const double *tl = lead ? g->cl : g->gl;
+    const double *tg = lead ? g->cg : g->gg;
+    if (same == 1) return lead ? g->c0 : g->gl0;
     if (same == 2) return g->dv;
     double tau = u - up;
-    if (a == 0 && ap == 1) return table_at(g->gl, g->L, g->T, tau);
-    if (a == 1 && ap == 0) return table_at(g->gg, g->L, g->T, tau);
+    if (a == 0 && ap == 1) return table_at(tl, g->L, g->T, tau);
+    if (a == 1 && ap == 0) return table_at(tg, g->L, g->T, tau);
     int later = (u > up); /* theta(u - u') */
     if (a == 0) /* time ordered */
-        return later ? table_at(g->gg, g->L, g->T, tau) : table_at(g->gl, g->L, g->T, tau);
+        return later ? table_at(tg, g->L, g->T, tau) : table_at(tl, g->L, g->T, tau);
     /* anti-time ordered */
-    return later ? table_at(g->gl, g->L, g->T, tau) : table_at(g->gg, g->L, g->T, tau);
+    return later ? table_at(tl, g->L, g->T, tau) : table_at(tg, g->L, g->T, tau);
 }
 
 /* Determinant by Doolittle LU factorisation with partial pivoting (row swaps
@@ -117,8 +140,8 @@ static cplx det_lu(cplx *A, int m) {
  * Order-n integrand of App. E Eq. (integral_gf) at vertex times u[0..n-1]
  * (any order; the theta functions decide), measurement time t:
  *   c(u) = i^n * sum_{a in {0,1}^n} (-1)^{sum a}
- *          [[(0,t,0), U_1..U_n ; (0,t,1), U_1..U_n]] * [[U_1..U_n ; U_1..U_n]]
- * with U_k = (u_k, a_k).  The left Wick determinant is the spin-up one
+ *          [[(0,t,0), U_1..U_n ; (i,t,1), U_1..U_n]] * [[U_1..U_n ; U_1..U_n]]
+ * with U_k = (0, u_k, a_k); i = 1 (current) when g->cl is set, else 0.  The left Wick determinant is the spin-up one
  * ((n+1)x(n+1), row 0 / column 0 = the measurement points), the right one is
  * spin-down (n x n).  Both are formed from scratch for every a.
  * Also returns sum_a |term| (before the i^n factor) in *abs_sum if non-NULL.
@@ -141,12 +164,13 @@ static cplx integrand(const gf_t *g, int n, const double *u, double t, double *a
             for (int c = 0; c < m; ++c) {
                 double uc = (c == 0) ? t : u[c - 1];
                 int ac = (c == 0) ? 1 : a[c - 1];
-                up[r * m + c] = keldysh_g(g, ur, ar, uc, ac, r == c ? (r == 0 ? 1 : 2) : 0);
+                up[r * m + c] = keldysh_g(g, ur, ar, uc, ac, r == c ? (r == 0 ? 1 : 2) : 0,
+                                          c == 0 && g->cl != NULL);
             }
         }
         for (int r = 0; r < n; ++r)
             for (int c = 0; c < n; ++c)
-                dn[r * n + c] = keldysh_g(g, u[r], a[r], u[c], a[c], r == c ? 2 : 0);
+                dn[r * n + c] = keldysh_g(g, u[r], a[r], u[c], a[c], r == c ? 2 : 0, 0);
         cplx term = det_lu(up, m) * det_lu(dn, n);
         if (parity) term = -term;
         asum += cabs(term);
@@ -168,12 +192,14 @@ static cplx integrand(const gf_t *g, int n, const double *u, double t, double *a
 /* ------------------------------ exported API ------------------------------ */
 
 /* Integrand at `count` points; u is count x n row-major (any time order).
- * out: 2*count doubles (re, im) of c(u); abs_out (optional): sum_a |term|. */
+ * out: 2*count doubles (re, im) of c(u); abs_out (optional): sum_a |term|.
+ * col: NULL for the charge, else the dot-lead tables (see make_gf). */
 int oracle_integrand(int n, int64_t count, const double *u, double t,
                      const double *gl, const double *gg, int L, double T,
-                     double gl0_re, double gl0_im, double *out, double *abs_out, double alpha) {
+                     double gl0_re, double gl0_im, double *out, double *abs_out, double alpha,
+                     const double *col) {
     if (n < 0 || n > ORACLE_MAX_ORDER || L < 2 || count < 0) return -1;
-    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im, gl0_re + I * (gl0_im - alpha)};
+    gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     for (int64_t i = 0; i < count; ++i) {
         double as;
         cplx v = integrand(&g, n, u + i * n, t, &as);
@@ -213,9 +239,10 @@ int oracle_sobol(int n, int64_t i0, int64_t count, const uint32_t *V, uint32_t *
  */
 int oracle_estimate(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint32_t *S,
                     double t, double tau, const double *gl, const double *gg, int L,
-                    double T, double gl0_re, double gl0_im, double *result, int64_t *n_in, double alpha) {
+                    double T, double gl0_re, double gl0_im, double *result, int64_t *n_in, double alpha,
+                    const double *col) {
     if (n < 1 || n > ORACLE_MAX_ORDER || L < 2) return -1;
-    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im, gl0_re + I * (gl0_im - alpha)};
+    gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
     int64_t inside = 0;
     uint32_t X[ORACLE_MAX_ORDER];
@@ -311,9 +338,9 @@ static double learned_w(const double *cdf, int cells, double x, double *jac) {
 int oracle_estimate_proj(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint32_t *S, double t,
                          double tau, const double *cdf, int cells, const double *gl, const double *gg, int L,
                          double T, double gl0_re, double gl0_im, double *result, int64_t *n_in,
-                         double alpha) {
+                         double alpha, const double *col) {
     if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || cells < 1) return -1;
-    gf_t g = {gl, gg, L, T, gl0_re + I * gl0_im, gl0_re + I * (gl0_im - alpha)};
+    gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
     int64_t inside = 0;
     uint32_t X[ORACLE_MAX_ORDER];
