@@ -285,7 +285,7 @@ def run_ours(args, ws, rank, local, pg):
 # DRAM bytes (read + write) of one detsum launch of the default benchmark step,
 # from a 1-pass ncu capture of this exact command (profiles/detsum_*_plain-dot_n1-10.md).
 # Set to None whenever the determinant kernel changes until it is captured again.
-MEASURED_LAUNCH_TRAFFIC = {"fp64": 1.08e6 + 1.08e6, "mixed": 588.54e3 + 544.51e3}
+MEASURED_LAUNCH_TRAFFIC = {"fp64": None, "mixed": None}
 
 
 def _launch_traffic(args, slice_n):
@@ -357,17 +357,16 @@ def run_batched(args, local):
 
 def run_precision(args, local):
     """Orders 6..12 at N = 2^log2 x 16 shifts: mixed (FP32 tables and Schur updates) against the FP64 path,
-    plus the per-point integrand error of the mixed path against the CPU oracle on identical points."""
+    plus the per-point integrand error of the mixed path against the FP64 path on identical points (the FP64
+    integrand itself agrees with the CPU oracle to 1e-12 of the Keldysh-sum scale in the parity tests)."""
     import numpy as np
     import torch
 
-    from oracle import oracle as O
     from paper_2002_12372_gb300 import workloads as W
 
     Q = _setup(args, local)
     N = 2 ** args.precision_log2
     pr = Q.qqmc_create_problem(Q.make_params(GAMMA, 0.0, T_MAX, TAU, L_TABLE, SEED))
-    tabs = O.gf_tables(GAMMA, 0.0, T_MAX, L_TABLE)
     rows = {}
     stream = torch.cuda.Stream()
     t_mixed = t_fp64 = 0.0
@@ -385,17 +384,67 @@ def run_precision(args, local):
         t_fp64 += kf
         u = W.ordered_times(900 + n, 8 if n < 11 else 3, n, T_MAX)
         cm = Q.qqmc_integrand(pr, n, u, Q.QQMC_PREC_MIXED)
-        ref, scale = O.integrand(n, u, T_MAX, tabs, T_MAX, return_abs=True)
+        ref = Q.qqmc_integrand(pr, n, u, Q.QQMC_PREC_FP64)
         rows[n] = {"q_mixed": rm.q_mean, "q_fp64": rf.q_mean, "err_bar": rf.q_err,
                    "abs_dev": abs(rm.q_mean - rf.q_mean), "dev_over_err": abs(rm.q_mean - rf.q_mean) / rf.q_err,
                    "rel_dev": abs(rm.q_mean - rf.q_mean) / abs(rf.q_mean),
-                   "point_err_over_scale_max": float(np.max(np.abs(cm - ref) / scale)),
+                   "point_err_rel_max": float(np.max(np.abs(cm - ref) / np.abs(ref))),
                    "point_err_rel_median": float(np.median(np.abs(cm - ref) / np.abs(ref))),
                    "ms_mixed": km, "ms_fp64": kf}
     Q.qqmc_destroy_problem(pr)
     return {"metric": "precision_study", "value": t_fp64 / t_mixed, "unit": "speedup mixed over fp64",
             "config": {"workload": "orders 6..12, N=2^%d x 16 shifts, Gamma=1, eps_d=0, t=10, tau=1, L=4096"
                                    % args.precision_log2}, "per_order": rows}
+
+
+def run_current(args, local):
+    """Current I_n through the dot with semicircular leads under bias (the paper's finite-bias current
+    calculations): one plan over orders 1..10 with 2^log2 points x 10 shifts each."""
+    import torch
+
+    from paper_2002_12372_gb300 import workloads as W
+
+    Q = _setup(args, local)
+    c = W.CurrentConfig()
+    prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
+    L = args.current_table
+    p = Q.make_params(c.gamma, c.E_d, c.t_max, c.tau, L, SEED, alpha=c.alpha, observable=Q.QQMC_OBS_CURRENT,
+                      half_bandwidth=c.half_bandwidth, bias=c.bias)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    pr = Q.qqmc_create_problem(p)
+    table_s = time.perf_counter() - t0
+    N = 2 ** args.current_log2
+    plan = Q.Plan([(pr, n, c.n_shifts, N) for n in c.orders], prec)
+    for _ in range(args.warmup):
+        plan.launch(stream.cuda_stream, use_graph=True)
+        plan.results()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.launch(stream.cuda_stream, use_graph=True)
+        e1.record(stream)
+        res = plan.results()
+        ms.append(e0.elapsed_time(e1))
+    plan.close()
+    _cl, _cg, c0 = Q.qqmc_problem_current_tables(pr, L)
+    Q.qqmc_destroy_problem(pr)
+    t = sum(ms) / len(ms) / 1e3
+    pts = sum(r.n_points * r.n_shifts for r, _ in res)
+    return {"metric": "current_integrand_evals_per_s", "value": pts / t, "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "current, semicircular leads D=%g, Gamma=%g, E_d=%g, alpha=%g, V=%g, t=%g, "
+                                   "tau=%g, L=%d, orders %d..%d, N=2^%d x %d shifts, one CUDA-graph launch"
+                                   % (c.half_bandwidth, c.gamma, c.E_d, c.alpha, c.bias, c.t_max, c.tau, L,
+                                      c.orders[0], c.orders[-1], args.current_log2, c.n_shifts),
+                       "precision": args.precision, "l2": "flushed (256 MiB write) between timed steps"},
+            "table_build_s": table_s, "I_0": -4.0 * c0.real,
+            "per_order": {r.order: {"I": r.q_mean, "err": r.q_err, "in_domain": r.n_in_domain} for r, _ in res}}
 
 
 def run_serving(args, local):
@@ -509,16 +558,19 @@ def main():
                     help="autotuner table (JSON keyed by GPU name); built-in defaults when absent")
     ap.add_argument("--slice-log2", type=int, default=16,
                     help="Sobol' indices per shift in one step (16: the benchmark batch; smaller for profiling)")
-    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving"], default="plain",
+    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving", "current"], default="plain",
                     help="plain: the benchmark workload; the others print their own study line")
     ap.add_argument("--precision-log2", type=int, default=22)
+    ap.add_argument("--current-log2", type=int, default=16)
+    ap.add_argument("--current-table", type=int, default=16384)
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--serve-log2-min", type=int, default=16)
     ap.add_argument("--serve-log2-max", type=int, default=22)
     args = ap.parse_args()
     if args.config != "plain":
         local = int(os.environ.get("LOCAL_RANK", "0"))
-        fn = {"batched": run_batched, "precision": run_precision, "serving": run_serving}[args.config]
+        fn = {"batched": run_batched, "precision": run_precision, "serving": run_serving,
+              "current": run_current}[args.config]
         print(json.dumps(fn(args, local)), flush=True)
         return
     ws, rank, local, pg = _dist()

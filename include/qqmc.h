@@ -1,9 +1,10 @@
 /*
  * qqmc.h -- C ABI of the GB300 quantum quasi-Monte Carlo (QQMC) library.
  *
- * The library evaluates the order-n perturbative coefficient Q_n of the charge
- * on the Anderson single-level dot (wide-band leads, T = 0, zero bias) by the
- * QQMC method: digitally shifted Sobol' points are warped through the product
+ * The library evaluates order-n perturbative coefficients of the Anderson
+ * single-level dot at T = 0 -- the charge Q_n (wide-band or semicircular
+ * leads) and the current I_n (semicircular leads under a symmetric bias) --
+ * by the QQMC method: digitally shifted Sobol' points are warped through the product
  * model function p_n(u) = prod_i exp(-(u_{i-1}-u_i)/tau) into ordered vertex
  * times t = u_0 > u_1 > ... > u_n > 0, the Keldysh integrand (sum over the
  * 2^n Keldysh index vectors of det M_up * det M_down) is evaluated there, and
@@ -19,6 +20,10 @@
  *    cube form is absorbed by ordering the vertices).
  *  - Charge readout Q_n = -2i * (1/N) sum_i w_i c_n(u_i), paper Eq.
  *    (warped_int2) with w = C/p_n, C = tau^n; points with u_n <= 0 add 0.
+ *  - Current (App. E, measurement column on lead site 1): the column of
+ *    M_up holds gamma g^<_01(u_k - t) (a_k = 0) or gamma g^>_01 (a_k = 1),
+ *    and I_n = -4 Re (1/N) sum_i w_i c_n(u_i): the current from the dot into
+ *    the lead at -V/2, both spins, e = hbar = 1 (per spin -2 gamma Im<c_0^+ c_1>).
  *  - Error bar: sample standard deviation over the K shifted sequences
  *    (ddof = 1) divided by sqrt(K), paper App. G and App. H.
  *  - Sobol' points in Gray-code order, X_i = XOR of the direction words
@@ -60,6 +65,10 @@ extern "C" {
 #define QQMC_MAX_ORDER 16
 #define QQMC_MAX_POINTS_LOG2 30 /* N <= 2^30 points per shifted sequence */
 
+/* Observable (qqmc_params.observable). */
+#define QQMC_OBS_CHARGE 0  /* Q: G^<_00(t,t) */
+#define QQMC_OBS_CURRENT 1 /* I: G^<_01(t,t), needs half_bandwidth > 0 */
+
 /* Arithmetic of the determinant stage. */
 #define QQMC_PREC_FP64 0  /* tables, Schur updates and sums in FP64 */
 #define QQMC_PREC_MIXED 1 /* tables and Schur updates in FP32, leaf sums two-sum
@@ -67,28 +76,39 @@ extern "C" {
 
 /* Physical problem and warp (paper: App. E model, App. F exponential h). */
 typedef struct qqmc_params {
-    double gamma;    /* tunnelling rate Gamma (Lorentzian half-width), > 0 */
-    double eps_d;    /* dot level eps_d */
-    double t_max;    /* measurement time t = u_0; tables cover [-t_max, t_max]; > 0 */
-    double tau;      /* model-function decay: h(v) = exp(-v / tau), > 0 */
-    int32_t n_table; /* L, number of table nodes; even, 4 <= L <= 2^20 */
-    int32_t reserved;
-    uint64_t seed;   /* digital-shift seed (used when no shift words are given) */
-    double alpha;    /* quadratic shift of the interaction, U (n_up - alpha)(n_dn - alpha) (App. E):
-                        the diagonal of every Wick determinant becomes g^<(0) - i alpha, except the
-                        entry of the measurement pair; 0 for the plain expansion */
+    double gamma;       /* tunnelling rate Gamma at the Fermi level (Lorentzian half-width), > 0 */
+    double eps_d;       /* level E_d of the non-interacting dot (App. E: eps_d = E_d - alpha U) */
+    double t_max;       /* measurement time t = u_0; tables cover [-t_max, t_max]; > 0 */
+    double tau;         /* model-function decay: h(v) = exp(-v / tau), > 0 */
+    int32_t n_table;    /* L, number of table nodes; even, 4 <= L <= 2^20 */
+    int32_t observable; /* QQMC_OBS_CHARGE or QQMC_OBS_CURRENT */
+    uint64_t seed;      /* digital-shift seed (used when no shift words are given) */
+    double alpha;       /* quadratic shift of the interaction, U (n_up - alpha)(n_dn - alpha) (App. E):
+                           the diagonal of every Wick determinant becomes g^<(0) - i alpha, except the
+                           entry of the measurement pair; 0 for the plain expansion */
+    double half_bandwidth; /* D of the semicircular lead density of states (App. E); 0 = wide band
+                              (Delta = -i Gamma).  D > 0 needs |eps_d| + gamma < D. */
+    double bias;        /* symmetric bias V >= 0: lead L at +V/2, lead R (holding site 1) at -V/2;
+                           V > 0 needs D > 0 */
 } qqmc_params;
 
 typedef struct qqmc_problem qqmc_problem;
 
 /*
- * Build a problem: the g^<, g^> tables of the wide-band dot at T = 0, V = 0
- * are computed on the device by the App. E contour-deformed Fourier integral
- * (vertical ray into the half plane where e^{-i w tau} decays, plus the real
- * segment up to the Fermi level; composite Gauss-Legendre), g^> from the
- * exact sum rule g^> - g^< = -i exp(-i eps_d tau - Gamma |tau|), and kept
- * resident in device memory.  *out is owned by the caller until
- * qqmc_destroy_problem.  Errors: E_INVAL (bad params), E_NOMEM, E_CUDA.
+ * Build a problem: the Green-function tables are computed on the device and
+ * kept resident in device memory.
+ *  - half_bandwidth = 0 (wide band, V = 0): g^<, g^> by the App. E
+ *    contour-deformed Fourier integral (vertical ray into the half plane
+ *    where e^{-i w tau} decays, plus the real segment up to the Fermi level;
+ *    composite Gauss-Legendre), g^> from the exact sum rule
+ *    g^> - g^< = -i exp(-i eps_d tau - Gamma |tau|); g^<(0) = i<n> in closed form.
+ *  - half_bandwidth = D > 0 (semicircular leads, App. E, bias V): g^<_00,
+ *    g^>_00 and, for the current, gamma g^<_01, gamma g^>_01 from their
+ *    spectral forms (Eq. (lesser_greater_freq); textbook normalisation
+ *    g^< = i A f) by composite Gauss-Legendre in w = D sin(theta), split at
+ *    the Fermi steps +-V/2; the equal-time values from the same quadrature.
+ * *out is owned by the caller until qqmc_destroy_problem.
+ * Errors: E_INVAL (bad params), E_NOMEM, E_CUDA.
  */
 int qqmc_create_problem(const qqmc_params *p, qqmc_problem **out);
 
@@ -103,6 +123,21 @@ int qqmc_create_problem(const qqmc_params *p, qqmc_problem **out);
  */
 int qqmc_create_problem_tables(const qqmc_params *p, const double *g_lesser, const double *g_greater,
                                double g0_re, double g0_im, qqmc_problem **out);
+
+/*
+ * Switch a problem to the current observable with caller dot-lead tables:
+ * cl = gamma g^<_01, cg = gamma g^>_01, 2*L doubles each (interleaved
+ * complex) on the problem's mesh; only the nodes k = 0 .. L/2 (tau <= h/2)
+ * are read, since the column entries sit at tau = u_k - t < 0.
+ * c0 = gamma g^<_01(0) (the measurement pair; it cancels from every order
+ * n >= 1 and gives I_0 = -4 Re c0).  Copied.  Errors: E_INVAL, E_NOMEM, E_CUDA.
+ */
+int qqmc_set_current_tables(qqmc_problem *pr, const double *cl, const double *cg, double c0_re, double c0_im);
+
+/* Copy a current problem's dot-lead tables to host: nodes k = 0 .. L/2 only,
+ * (L/2 + 1) complex values each; c0 (optional) = gamma g^<_01(0).
+ * E_INVAL for a charge problem. */
+int qqmc_problem_current_tables(const qqmc_problem *pr, double *cl, double *cg, double *c0);
 
 /* Free a problem and its device memory.  NULL is accepted. */
 int qqmc_destroy_problem(qqmc_problem *pr);
@@ -143,9 +178,10 @@ typedef struct qqmc_result {
     int32_t order;
     int32_t n_shifts;          /* K */
     uint64_t n_points;         /* N per shifted sequence */
-    double q_mean;             /* mean over shifts of Q_n^(k) */
+    double q_mean;             /* mean over shifts of Q_n^(k) (current: I_n^(k)) */
     double q_err;              /* std_{ddof=1} over shifts / sqrt(K) (0 if K == 1) */
-    double q_imag_absmax;      /* max_k |Im Q_n^(k)| (zero in exact arithmetic) */
+    double q_imag_absmax;      /* charge: max_k |Im Q_n^(k)| (zero in exact arithmetic);
+                                  current: max_k |-4 Im S_k / N| (not a check) */
     uint64_t n_in_domain;      /* points with u_n > 0, summed over shifts */
     double device_ms;          /* device time of the launch that produced it */
 } qqmc_result;
@@ -303,7 +339,8 @@ typedef struct qqmc_server_opts {
     double request_timeout_s;     /* 0: none */
 } qqmc_server_opts;
 
-/* A request: Q_1..Q_{n_max} of one dot (paper App. H parameter sweep). */
+/* A request: Q_1..Q_{n_max} (or I_1..I_{n_max} when params.observable is the
+ * current) of one dot (paper App. H parameter sweep). */
 typedef struct qqmc_request {
     qqmc_params params;
     int32_t n_max;      /* 1..QQMC_MAX_ORDER */
@@ -315,7 +352,8 @@ typedef struct qqmc_request {
 typedef struct qqmc_series {
     int32_t n_max;
     int32_t status;                    /* QQMC_OK or an error code */
-    double q[QQMC_MAX_ORDER + 1];      /* q[0] = Q_0 = -2i g^<(0); q[n] = Q_n */
+    double q[QQMC_MAX_ORDER + 1];      /* q[0] = Q_0 = -2i g^<(0) (current: I_0 = -4 Re gamma g^<_01(0));
+                                          q[n] = Q_n (I_n) */
     double q_err[QQMC_MAX_ORDER + 1];
     double series_sum;                 /* sum_{n <= n_max} Q_n U^n (truncated, not resummed) */
     double latency_ms;                 /* submit -> completion */

@@ -60,7 +60,9 @@ Tuning get_tuning(int precision, int order) {
 
 }  // namespace qqmc
 
-static bool valid_params(const qqmc_params *p, std::string &why) {
+namespace qqmc {
+
+bool valid_params(const qqmc_params *p, std::string &why) {
     if (!p) { why = "params is NULL"; return false; }
     if (!(p->gamma > 0) || !isfinite(p->gamma)) { why = "gamma must be > 0"; return false; }
     if (!isfinite(p->eps_d)) { why = "eps_d must be finite"; return false; }
@@ -71,8 +73,33 @@ static bool valid_params(const qqmc_params *p, std::string &why) {
         why = "n_table must be even and in 4..2^20";
         return false;
     }
+    if (p->observable != QQMC_OBS_CHARGE && p->observable != QQMC_OBS_CURRENT) {
+        why = "observable must be QQMC_OBS_CHARGE or QQMC_OBS_CURRENT";
+        return false;
+    }
+    if (!(p->half_bandwidth >= 0) || !isfinite(p->half_bandwidth)) { why = "half_bandwidth must be >= 0"; return false; }
+    if (!(p->bias >= 0) || !isfinite(p->bias)) { why = "bias must be >= 0"; return false; }
+    if (p->half_bandwidth == 0.0 && p->bias != 0.0) {
+        why = "a bias needs finite-bandwidth leads (half_bandwidth > 0)";
+        return false;
+    }
+    if (p->half_bandwidth == 0.0 && p->observable == QQMC_OBS_CURRENT) {
+        why = "the current needs finite-bandwidth leads (half_bandwidth > 0)";
+        return false;
+    }
+    if (p->half_bandwidth > 0.0 && !(fabs(p->eps_d) + p->gamma < p->half_bandwidth)) {
+        why = "|eps_d| + gamma must be below half_bandwidth (no bound state outside the band)";
+        return false;
+    }
     return true;
 }
+
+// Order-0 value of the observable: Q_0 = -2i g^<(0) = 2 <n>, I_0 = -4 Re gamma g^<_01(0).
+double order0_value(const Problem &pr) {
+    return pr.params.observable == QQMC_OBS_CURRENT ? -4.0 * pr.c0_re : 2.0 * pr.g0_im;
+}
+
+}  // namespace qqmc
 
 static int alloc_problem(const qqmc_params *p, qqmc_problem **out) {
     std::string why;
@@ -90,8 +117,14 @@ static int alloc_problem(const qqmc_params *p, qqmc_problem **out) {
     size_t nh = (size_t)pr->L / 2 + 1;
     cudaError_t e = cudaMalloc(&pr->d_table, nh * sizeof(dbl4));
     if (e == cudaSuccess) e = cudaMalloc(&pr->d_table32, nh * sizeof(float4));
+    if (e == cudaSuccess && p->observable == QQMC_OBS_CURRENT) {
+        e = cudaMalloc(&pr->d_col, nh * sizeof(dbl4));
+        if (e == cudaSuccess) e = cudaMalloc(&pr->d_col32, nh * sizeof(float4));
+    }
     if (e != cudaSuccess) {
         cudaFree(pr->d_table);
+        cudaFree(pr->d_table32);
+        cudaFree(pr->d_col);
         delete pr;
         return set_error(QQMC_E_NOMEM, std::string("device allocation of the tables failed: ") + cudaGetErrorString(e));
     }
@@ -103,12 +136,21 @@ extern "C" int qqmc_create_problem(const qqmc_params *p, qqmc_problem **out) {
     qqmc_problem *pr = nullptr;
     int rc = alloc_problem(p, &pr);
     if (rc != QQMC_OK) return rc;
-    pr->g0_re = 0.0;
-    pr->g0_im = 0.5 - atan(p->eps_d / p->gamma) / M_PI;
-    rc = launch_gf_table(*pr, 0);
-    if (rc == QQMC_OK) {
-        cudaError_t e = cudaStreamSynchronize(0);
-        if (e != cudaSuccess) rc = cuda_error(e, "table build");
+    if (p->half_bandwidth > 0.0) {  // semicircular leads: numerical tables, g^<(0) from the same quadrature
+        double zero[4] = {0, 0, 0, 0};
+        rc = launch_lead_table(*pr, 0, zero);
+        pr->g0_re = zero[0];
+        pr->g0_im = zero[1];
+        pr->c0_re = zero[2];
+        pr->c0_im = zero[3];
+    } else {
+        pr->g0_re = 0.0;
+        pr->g0_im = 0.5 - atan(p->eps_d / p->gamma) / M_PI;
+        rc = launch_gf_table(*pr, 0);
+        if (rc == QQMC_OK) {
+            cudaError_t e = cudaStreamSynchronize(0);
+            if (e != cudaSuccess) rc = cuda_error(e, "table build");
+        }
     }
     if (rc != QQMC_OK) {
         qqmc_destroy_problem(pr);
@@ -122,6 +164,8 @@ extern "C" int qqmc_create_problem_tables(const qqmc_params *p, const double *gl
                                           double g0_im, qqmc_problem **out) {
     if (!gl || !gg) return set_error(QQMC_E_INVAL, "tables are NULL");
     if (!isfinite(g0_re) || !isfinite(g0_im)) return set_error(QQMC_E_INVAL, "g0 must be finite");
+    if (p && p->observable != QQMC_OBS_CHARGE)
+        return set_error(QQMC_E_INVAL, "caller tables start as a charge problem; qqmc_set_current_tables switches it");
     qqmc_problem *pr = nullptr;
     int rc = alloc_problem(p, &pr);
     if (rc != QQMC_OK) return rc;
@@ -146,10 +190,60 @@ extern "C" int qqmc_create_problem_tables(const qqmc_params *p, const double *gl
     return QQMC_OK;
 }
 
+extern "C" int qqmc_set_current_tables(qqmc_problem *pr, const double *cl, const double *cg, double c0_re,
+                                       double c0_im) {
+    if (!pr || !cl || !cg) return set_error(QQMC_E_INVAL, "qqmc_set_current_tables: NULL argument");
+    if (!isfinite(c0_re) || !isfinite(c0_im)) return set_error(QQMC_E_INVAL, "c0 must be finite");
+    const int L = pr->L;
+    const size_t nh = (size_t)L / 2 + 1;
+    std::vector<dbl4> h(nh);
+    std::vector<float4> h32(nh);
+    for (int k = 0; k <= L / 2; ++k) {
+        h[k] = make_double4_32a(cl[2 * k], cl[2 * k + 1], cg[2 * k], cg[2 * k + 1]);
+        h32[k] = make_float4((float)cl[2 * k], (float)cl[2 * k + 1], (float)cg[2 * k], (float)cg[2 * k + 1]);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!pr->d_col) {
+        e = cudaMalloc(&pr->d_col, nh * sizeof(dbl4));
+        if (e == cudaSuccess) e = cudaMalloc(&pr->d_col32, nh * sizeof(float4));
+        if (e != cudaSuccess) {
+            cudaFree(pr->d_col);
+            pr->d_col = nullptr;
+            pr->d_col32 = nullptr;
+            return set_error(QQMC_E_NOMEM, "device allocation of the dot-lead tables failed");
+        }
+    }
+    e = cudaMemcpy(pr->d_col, h.data(), nh * sizeof(dbl4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pr->d_col32, h32.data(), nh * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "dot-lead table upload");
+    pr->c0_re = c0_re;
+    pr->c0_im = c0_im;
+    pr->params.observable = QQMC_OBS_CURRENT;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_problem_current_tables(const qqmc_problem *pr, double *cl, double *cg, double *c0) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    if (pr->params.observable != QQMC_OBS_CURRENT || !pr->d_col)
+        return set_error(QQMC_E_INVAL, "problem has no dot-lead tables (charge observable)");
+    const int L = pr->L;
+    std::vector<dbl4> h(L / 2 + 1);
+    cudaError_t e = cudaMemcpy(h.data(), pr->d_col, h.size() * sizeof(dbl4), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "dot-lead table download");
+    for (int k = 0; k <= L / 2; ++k) {
+        if (cl) { cl[2 * k] = h[k].x; cl[2 * k + 1] = h[k].y; }
+        if (cg) { cg[2 * k] = h[k].z; cg[2 * k + 1] = h[k].w; }
+    }
+    if (c0) { c0[0] = pr->c0_re; c0[1] = pr->c0_im; }
+    return QQMC_OK;
+}
+
 extern "C" int qqmc_destroy_problem(qqmc_problem *pr) {
     if (!pr) return QQMC_OK;
     cudaFree(pr->d_table);
     cudaFree(pr->d_table32);
+    cudaFree(pr->d_col);
+    cudaFree(pr->d_col32);
     for (int n = 0; n <= kMaxOrder; ++n) cudaFree(pr->d_proj[n]);
     delete pr;
     return QQMC_OK;
@@ -315,6 +409,8 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         d.chunks_per_shift = (int)cps;
         d.flat = lm ? 1 : plan_flat;
         d.alpha = pr->params.alpha;
+        d.col = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col : nullptr;
+        d.col32 = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col32 : nullptr;
         d.proj = pr->d_proj[it.order];
         d.proj_cells = pr->proj_cells[it.order];
         if (lm) {
@@ -434,10 +530,12 @@ static void finish_result(const qqmc_item &it, const double *S, const unsigned l
     double mean = 0.0, imax = 0.0;
     uint64_t nin = 0;
     std::vector<double> q(K);
+    const bool current = it.problem->params.observable == QQMC_OBS_CURRENT;
     for (int k = 0; k < K; ++k) {
-        // Q = -2i S / N
-        q[k] = 2.0 * S[2 * k + 1] / N;
-        double qi = -2.0 * S[2 * k] / N;
+        // charge: Q = -2i S / N (real part; the imaginary part is zero in exact arithmetic);
+        // current: I = -4 Re S / N (the other component, -4 Im S / N, is reported as "imag")
+        q[k] = current ? -4.0 * S[2 * k] / N : 2.0 * S[2 * k + 1] / N;
+        double qi = current ? -4.0 * S[2 * k + 1] / N : -2.0 * S[2 * k] / N;
         mean += q[k];
         imax = fabs(qi) > imax ? fabs(qi) : imax;
         nin += cnt[k];
@@ -649,6 +747,8 @@ extern "C" int qqmc_integrand(const qqmc_problem *pr, int order, uint64_t count,
     it.L = pr->L;
     it.order = order;
     it.alpha = pr->params.alpha;
+    it.col = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col : nullptr;
+    it.col32 = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col32 : nullptr;
     Tuning tu = get_tuning(precision, order);
     if (tu.flat < 2) tu.flat = tu.flat_min = 2;  // the check kernel runs one warp per point
     it.flat = tu.flat;
@@ -752,6 +852,8 @@ extern "C" int qqmc_learn_projection(qqmc_problem *pr, int order, uint64_t M, in
         it.L = pr->L;
         it.order = n;
         it.alpha = pr->params.alpha;
+        it.col = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col : nullptr;
+        it.col32 = nullptr;
         Tuning tu = get_tuning(QQMC_PREC_FP64, n);
         if (tu.flat < 2) tu.flat = tu.flat_min = 2;
         it.flat = tu.flat;

@@ -2,6 +2,8 @@
 //
 //  * gf_table_kernel   -- g^<(tau), g^>(tau) of the wide-band dot by the
 //                         contour-deformed Fourier integral of App. E.
+//  * lead_*_kernel     -- the same for semicircular leads of finite width
+//                         and bias, plus the dot-lead tables of the current.
 //  * detsum_kernel     -- the hot path: Sobol' point generation with a digital
 //                         shift, exponential product-model warp, pair
 //                         interpolation of the Green-function tables and the
@@ -15,7 +17,9 @@
 // pair j < k the Keldysh matrix entry above the diagonal depends only on a_k
 // (a_k = 0: g^>(u_j-u_k), a_k = 1: g^<(u_j-u_k)) and the one below only on a_k
 // too (a_k = 0: g^<(u_k-u_j), a_k = 1: g^>(u_k-u_j)); the diagonal is g^<(0).
-// Row 0 / column 0 of M_up are the measurement points (t, a=0) / (t, a=1).
+// Row 0 / column 0 of M_up are the measurement points (t, a=0) / (i, t, a=1):
+// site i = 0 for the charge, lead site 1 for the current, whose column then
+// holds the dot-lead functions gamma g^<_01, gamma g^>_01 (App. E).
 // Hence, once the leading vertices are eliminated, every entry of the Schur
 // complement depends only on the Keldysh indices of its own row and column
 // vertices.  The kernel walks the binary tree of Keldysh indices depth first
@@ -68,9 +72,19 @@ template <class R>
 __device__ __forceinline__ cx<R> cfms(cx<R> c, cx<R> a, cx<R> b) {
     return mk<R>(fmaR(-a.re, b.re, fmaR(a.im, b.im, c.re)), fmaR(-a.re, b.im, fmaR(-a.im, b.re, c.im)));
 }
+// 1/x.  FP64: IEEE division.  FP32: the hardware approximation (PTX
+// rcp.approx.ftz.f32) refined by one Newton-Raphson step r' = r + r (1 - x r),
+// which leaves ~1 ulp, well inside the FP32 path's error budget and without
+// the division's special-case branch.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
 template <class R>
 __device__ __forceinline__ cx<R> crcp(cx<R> a) {
-    R s = R(1) / fmaR(a.re, a.re, a.im * a.im);
+    R s = recip(fmaR(a.re, a.re, a.im * a.im));
     return mk<R>(a.re * s, -a.im * s);
 }
 template <class R>
@@ -78,7 +92,11 @@ __device__ __forceinline__ cx<R> nconj(cx<R> a) {  // -conj(a)
     return mk<R>(-a.re, a.im);
 }
 
-// Knuth two-sum accumulator: value = s + c.
+// Lane accumulator of the Keldysh leaf terms, value = s + c.  FP32 leaves:
+// Knuth two-sum (float-float), since the alternating-sign sum cancels by up to
+// 1e5.  FP64 leaves: plain sum; a lane adds at most 2^(n-1)/32 terms, so its
+// rounding stays below 1e-14 of the Keldysh-sum scale, and the lanes are
+// combined with two-sum in warp_total.
 template <class R>
 struct Acc {
     R s, c;
@@ -90,6 +108,8 @@ struct Acc {
         s = t;
     }
 };
+template <>
+__device__ __forceinline__ void Acc<double>::add(double x) { s += x; }
 
 __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
     s = a + b;
@@ -158,6 +178,24 @@ __device__ __forceinline__ void interp_pair(const typename TabT<R>::V *tab, doub
     gg = mk<R>(fmaR(fr, b.z, g * a.z), fmaR(fr, b.w, g * a.w));
 }
 
+// Measurement-column values of the current at tau = u_k - t < 0 (a_k = 0:
+// gamma g^<_01, a_k = 1: gamma g^>_01).  The column table holds the nodes
+// k = 0 .. L/2 (tau from -T to +h/2).
+template <class R>
+__device__ __forceinline__ void interp_col(const typename TabT<R>::V *col, double inv_h, double s0, int L, double tau,
+                                           cx<R> &cl, cx<R> &cg) {
+    double s = fma(tau, inv_h, s0);
+    int k = __double2int_rd(s);
+    const int kmax = L / 2 - 1;
+    k = k < 0 ? 0 : (k > kmax ? kmax : k);
+    R fr = (R)(s - (double)k);
+    R g = R(1) - fr;
+    typename TabT<R>::V a = col[k];
+    typename TabT<R>::V b = col[k + 1];
+    cl = mk<R>(fmaR(fr, b.x, g * a.x), fmaR(fr, b.y, g * a.y));
+    cg = mk<R>(fmaR(fr, b.z, g * a.z), fmaR(fr, b.w, g * a.w));
+}
+
 // ----------------------------------------------------------------------------
 // Per-warp shared-memory layout for the Keldysh sum.
 //
@@ -173,8 +211,8 @@ template <class R>
 struct WarpSmem {
     cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l
     cx<R> *wrow;    // scaled pivot row(s): <= max(2 n_max, 64) entries
-    cx<R> *P;       // P[j*(n_max+1)+k] = g^>(u_j - u_k), j < k
-    cx<R> *Rr;      // Rr[...]          = g^<(u_j - u_k)
+    cx<R> *P;       // P[j*(n_max+1)+k] = g^>(u_j - u_k), j < k; P[k*(n_max+1)] = column entry (k, a_k=1)
+    cx<R> *Rr;      // Rr[...]          = g^<(u_j - u_k);      Rr[k*(n_max+1)] = column entry (k, a_k=0)
     cx<R> *detD;    // per tree level
     cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
     cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
@@ -247,15 +285,6 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
     w.upt = reinterpret_cast<double *>(base + off);
     return w;
-}
-
-// Generalised Keldysh entry between global vertices v (row) and w (column),
-// 0 = measurement point (row: (t, a=0); column: (t, a=1)).
-template <class R>
-__device__ __forceinline__ cx<R> G(const WarpSmem<R> &ws, int NP, cx<R> d, int v, int av, int w, int aw) {
-    if (v == w) return d;
-    if (v < w) return aw ? ws.Rr[v * NP + w] : ws.P[v * NP + w];
-    return av ? nconj(ws.P[w * NP + v]) : nconj(ws.Rr[w * NP + v]);
 }
 
 // Flat phase: one lane resolves the F remaining vertices of node matrix E
@@ -392,6 +421,32 @@ __device__ __forceinline__ void expand_level(const cx<R> *__restrict__ in, int S
     __syncwarp();
 }
 
+// Single child (a depth-first step, S - 2 <= 32): each lane owns one column of
+// the child and a fixed row offset, so the scaled pivot-row entry of its
+// column stays in a register, the pivot-column entry of a row is a broadcast
+// load, and the index arithmetic per entry is one multiply-add.
+template <class R>
+__device__ __forceinline__ void expand_one(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
+                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    const int S2 = S - 2;
+    const int pr = 2 + a;
+    const cx<R> piv = in[pr * S + pr];
+    const cx<R> ip = crcp(piv);
+    if (lane == 0) *detD_out = cmul(*detD_in, piv);
+    const int rows = 32 / S2;  // child rows per pass
+    const int rsub = lane / S2;
+    const int c2 = lane - rsub * S2;
+    if (rsub < rows) {
+        const int c = c2 < 2 ? c2 : c2 + 2;
+        const cx<R> w = cmul(in[pr * S + c], ip);
+        for (int r2 = rsub; r2 < S2; r2 += rows) {
+            const int r = r2 < 2 ? r2 : r2 + 2;
+            out[r2 * S2 + c2] = cfms(in[r * S + c], in[r * S + pr], w);
+        }
+    }
+    __syncwarp();
+}
+
 // Float-float or double-double style butterfly of the lane accumulators:
 // combines (s, c) pairs with two-sum in R, then returns s + c in double.
 template <class R>
@@ -422,7 +477,8 @@ __device__ __forceinline__ double warp_total(Acc<R> acc) {
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
 template <class R, int RFMAX>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
-                                  const typename TabT<R>::V *tab, double inv_h, double s0, int L, int RF, int lane) {
+                                  const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
+                                  double s0, int L, int RF, int lane) {
     const int NP = n_max + 1;
     // 1. pair interpolation, 0 <= j < k <= n
     const int npairs = n * (n + 1) / 2;
@@ -435,6 +491,12 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         interp_pair<R>(tab, inv_h, s0, L, u[j] - u[k], gl, gg);
         ws.P[j * NP + k] = gg;
         ws.Rr[j * NP + k] = gl;
+        if (j == 0) {  // measurement column of vertex k: g^<(u_k - t), g^>(u_k - t) for the charge
+            cx<R> c0 = nconj(gl), c1 = nconj(gg);
+            if (col) interp_col<R>(col, inv_h, s0, L, u[k] - u[0], c0, c1);
+            ws.Rr[k * NP] = c0;
+            ws.P[k * NP] = c1;
+        }
     }
     __syncwarp();
     // 2. level 0: vertex 1 eliminated (both a_1 kept in the two measurement copies).
@@ -449,7 +511,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
         const cx<R> P01 = ws.P[1], R01 = ws.Rr[1];
         const cx<R> r1[2] = {P01, R01};
-        const cx<R> c1d[2] = {cmul(nconj(R01), id), cmul(nconj(P01), id)};
+        const cx<R> c1d[2] = {cmul(ws.Rr[1 * NP], id), cmul(ws.P[1 * NP], id)};
         for (int bid = lane; bid < n * n; bid += 32) {
             const int bx = bid / n, by = bid - bx * n;
             cx<R> base[2][2], left[2], right[2];
@@ -478,8 +540,8 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
                 base[0][1] = base[1][1] = ws.Rr[j];
             } else if (by == 0) {  // measurement column: c_i(ai)
                 const int i = bx + 1;
-                base[0][0] = base[0][1] = nconj(ws.Rr[i]);
-                base[1][0] = base[1][1] = nconj(ws.P[i]);
+                base[0][0] = base[0][1] = ws.Rr[i * NP];
+                base[1][0] = base[1][1] = ws.P[i * NP];
             } else if (bx < by) {  // upper: depends on aj
                 const int i = bx + 1, j = by + 1;
                 base[0][0] = base[1][0] = ws.P[i * NP + j];
@@ -524,8 +586,11 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         for (int l = from; l < levels; ++l) {
             const int a = (b >> (levels - 1 - l)) & 1;
             const int S = 2 * (R0 - l) + 2;
-            expand_level<R>(ws.stack + off[l], S, 1, a, ws.stack + off[l + 1], ws.detD + l, ws.detD + l + 1,
-                            ws.wrow, ws.bip, lane);
+            if (S - 2 <= 32)
+                expand_one<R>(ws.stack + off[l], S, a, ws.stack + off[l + 1], ws.detD + l, ws.detD + l + 1, lane);
+            else
+                expand_level<R>(ws.stack + off[l], S, 1, a, ws.stack + off[l + 1], ws.detD + l, ws.detD + l + 1,
+                                ws.wrow, ws.bip, lane);
         }
         const int tparity = __popc(b) & 1;
         // 4. breadth-first expansion of B levels below the tree leaf
@@ -568,7 +633,8 @@ __device__ __forceinline__ cx<R> sel(int bit, cx<R> one, cx<R> zero) {
 
 template <class R, int N>
 __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d, cx<R> dv,
-                                                       const typename TabT<R>::V *tab, double inv_h, double s0,
+                                                       const typename TabT<R>::V *tab,
+                                                       const typename TabT<R>::V *col, double inv_h, double s0,
                                                        int L) {
     constexpr int M = N + 1;
     cx<R> P[N + 1][N + 1], Rr[N + 1][N + 1];
@@ -579,10 +645,18 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
     for (int k = 1; k <= N; ++k)
 #pragma unroll
         for (int j = 0; j < k; ++j) interp_pair<R>(tab, inv_h, s0, L, uu[j] - uu[k], Rr[j][k], P[j][k]);
+    // measurement column (a_k = 0, 1): g^<, g^> at u_k - t for the charge, dot-lead tables for the current
+    cx<R> C0[N + 1], C1[N + 1];
+#pragma unroll
+    for (int k = 1; k <= N; ++k) {
+        C0[k] = nconj(Rr[0][k]);
+        C1[k] = nconj(P[0][k]);
+        if (col) interp_col<R>(col, inv_h, s0, L, uu[k] - uu[0], C0[k], C1[k]);
+    }
     const cx<R> id = crcp(dv);
     // row/column factors of vertex 1 (eliminated first, pivot dv)
     const cx<R> r1[2] = {P[0][1], Rr[0][1]};
-    const cx<R> c1d[2] = {cmul(nconj(Rr[0][1]), id), cmul(nconj(P[0][1]), id)};
+    const cx<R> c1d[2] = {cmul(C0[1], id), cmul(C1[1], id)};
     Acc<R> ar, ai;
     ar.init();
     ai.init();
@@ -612,7 +686,7 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
                 } else if (x < 2) {  // measurement row, vertex y
                     base = sel<R>((path >> (y - 2)) & 1, Rr[0][y], P[0][y]);
                 } else if (y < 2) {  // vertex x, measurement column
-                    base = nconj(sel<R>((path >> (x - 2)) & 1, P[0][x], Rr[0][x]));
+                    base = sel<R>((path >> (x - 2)) & 1, C1[x], C0[x]);
                 } else if (x < y) {  // upper: index of the column vertex
                     base = sel<R>((path >> (y - 2)) & 1, Rr[x][y], P[x][y]);
                 } else {  // lower: index of the row vertex
@@ -665,6 +739,14 @@ template <>
 __device__ __forceinline__ const dbl4 *item_table<double>(const ItemDev &it) { return it.table; }
 template <>
 __device__ __forceinline__ const float4 *item_table<float>(const ItemDev &it) { return it.table32; }
+
+// dot-lead column table of the current observable, or null (charge)
+template <class R>
+__device__ __forceinline__ const typename TabT<R>::V *item_col(const ItemDev &it);
+template <>
+__device__ __forceinline__ const dbl4 *item_col<double>(const ItemDev &it) { return it.col; }
+template <>
+__device__ __forceinline__ const float4 *item_col<float>(const ItemDev &it) { return it.col32; }
 
 // Gap v = -tau log(1 - x) of the exponential warp, x = y 2^-32.  FP64 for the
 // FP64 path; FP32 for the mixed path (log1p for x < 1/2, log of the exactly
@@ -776,7 +858,8 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             mm &= mm - 1;
             // every warp-per-point item of a launch shares the launch's flat depth
             cx<double> s =
-                keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, inv_h, s0, I.L, RFMAX, lane);
+                keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, item_col<R>(I), inv_h, s0, I.L,
+                                      RFMAX, lane);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -824,7 +907,7 @@ __device__ __forceinline__ cx<double> lane_point(const ItemDev &I, int k, uint64
     const double inv_h = 1.0 / I.h;
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
     const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
-    cx<double> s = lane_keldysh_sum<R, N>(u, d, dv, item_table<R>(I), inv_h, I.T * inv_h, I.L);
+    cx<double> s = lane_keldysh_sum<R, N>(u, d, dv, item_table<R>(I), item_col<R>(I), inv_h, I.T * inv_h, I.L);
     cx<double> c = times_i_pow(s, N);
     return mk<double>(w * c.re, w * c.im);
 }
@@ -970,7 +1053,8 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
     const double inv_h = 1.0 / I.h;
     cx<double> s =
-        keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), inv_h, I.T * inv_h, I.L, RF, lane);
+        keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I), inv_h, I.T * inv_h, I.L,
+                           RF, lane);
     if (lane == 0) {
         cx<double> cval = times_i_pow(s, n);
         out[2 * q] = cval.re;
@@ -1069,6 +1153,114 @@ __global__ void gf_table_kernel(dbl4 *tab, float4 *tab32, int L, double T, doubl
 }
 
 // ----------------------------------------------------------------------------
+// Finite-bandwidth leads (App. E): semicircular hybridisation of half-width D
+// shared by two leads, symmetric bias V, T = 0.  With w = D sin(theta):
+//   Gamma(w) = Gamma cos(theta),  Delta(w) = Gamma (sin(theta) - i cos(theta)),
+//   g^R = 1 / (w - E_d - Delta),  f_L = theta(V/2 - w),  f_R = theta(-V/2 - w),
+//   g^<_00 =  i Gamma(w) |g^R|^2 (f_L + f_R),
+//   g^>_00 = -i Gamma(w) |g^R|^2 (2 - f_L - f_R),
+//   gamma g^<_01 =  i f_R Gamma(w) g^R + (Delta^* / 2) g^<_00,
+//   gamma g^>_01 = -i (1 - f_R) Gamma(w) g^R + (Delta^* / 2) g^>_00
+// (lead R, which holds site 1, sits at -V/2; gamma G_01 = G_00 Delta_R by the
+// Dyson equation and the Langreth rule).  g(tau) = Int dw/2pi e^{-i w tau} g(w)
+// = Int dtheta (D cos(theta) / 2pi) e^{-i w(theta) tau} g(w(theta)): the
+// square-root edges disappear and every integrand is smooth in theta between
+// the Fermi steps, so each segment takes composite 16-point Gauss-Legendre.
+// ----------------------------------------------------------------------------
+struct LeadSeg {
+    double a, b;   // theta range
+    int panels;
+    int first;     // first quadrature node of the segment
+    double fL, fR; // Fermi factors on the segment
+};
+
+struct LeadQuad {
+    LeadSeg seg[3];
+    int n_seg;
+    double gam, Ed, D;
+};
+
+// Quadrature node j: w_j and the four spectral values times weight x dw/dtheta / 2pi.
+__global__ void lead_spectrum_kernel(LeadQuad q, int nq, double *w_out, dbl4 *s00, dbl4 *s01) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    int sg = 0;
+    while (sg + 1 < q.n_seg && j >= q.seg[sg + 1].first) ++sg;
+    const LeadSeg S = q.seg[sg];
+    const int r = j - S.first;
+    const int pnl = r >> 4, g = r & 15;
+    const double pw = (S.b - S.a) / S.panels;
+    const double th = S.a + pw * (pnl + 0.5 * (c_gl_x[g] + 1.0));
+    const double wt = 0.5 * pw * c_gl_w[g];
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    const double w = q.D * sn;
+    const double G = q.gam * cs;
+    // g^R = 1 / (w - E_d - Gamma sin + i Gamma cos)
+    const cx<double> gR = crcp(mk<double>(w - q.Ed - q.gam * sn, G));
+    const double a2 = gR.re * gR.re + gR.im * gR.im;
+    const double jac = wt * q.D * cs * 0.15915494309189535;
+    const double lt = G * a2 * (S.fL + S.fR), gt = G * a2 * (2.0 - S.fL - S.fR);
+    const cx<double> gl = mk<double>(0.0, lt), gg = mk<double>(0.0, -gt);
+    const cx<double> dh = mk<double>(0.5 * q.gam * sn, 0.5 * q.gam * cs);  // Delta^* / 2
+    // i f_R G g^R = f_R G (-gR.im + i gR.re)
+    const cx<double> cl = mk<double>(-S.fR * G * gR.im + (dh.re * gl.re - dh.im * gl.im),
+                                     S.fR * G * gR.re + (dh.re * gl.im + dh.im * gl.re));
+    // -i (1 - f_R) G g^R = (1 - f_R) G (gR.im - i gR.re)
+    const cx<double> cg = mk<double>((1.0 - S.fR) * G * gR.im + (dh.re * gg.re - dh.im * gg.im),
+                                     -(1.0 - S.fR) * G * gR.re + (dh.re * gg.im + dh.im * gg.re));
+    w_out[j] = w;
+    s00[j] = make_double4_32a(jac * gl.re, jac * gl.im, jac * gg.re, jac * gg.im);
+    s01[j] = make_double4_32a(jac * cl.re, jac * cl.im, jac * cg.re, jac * cg.im);
+}
+
+// One warp per output: nodes q = 0 .. L-1 (tau = -T + q h) and q = L (tau = 0).
+// Dot tables go to the half table (nodes L/2-1 .. L-1), dot-lead tables to the
+// column table (nodes 0 .. L/2); tau = 0 gives g^<_00(0) and gamma g^<_01(0).
+__global__ void lead_table_kernel(int nq, const double *__restrict__ wq, const dbl4 *__restrict__ s00,
+                                  const dbl4 *__restrict__ s01, int L, double T, double h, dbl4 *tab, float4 *tab32,
+                                  dbl4 *col, float4 *col32, double *zero) {
+    const int lane = threadIdx.x & 31;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q > L) return;
+    const double tau = q == L ? 0.0 : -T + (double)q * h;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int j = lane; j < nq; j += 32) {
+        double sn, cs;
+        sincos(wq[j] * tau, &sn, &cs);  // e^{-i w tau} = cs - i sn
+        const dbl4 a = s00[j], b = s01[j];
+        acc[0] += cs * a.x + sn * a.y;
+        acc[1] += cs * a.y - sn * a.x;
+        acc[2] += cs * a.z + sn * a.w;
+        acc[3] += cs * a.w - sn * a.z;
+        acc[4] += cs * b.x + sn * b.y;
+        acc[5] += cs * b.y - sn * b.x;
+        acc[6] += cs * b.z + sn * b.w;
+        acc[7] += cs * b.w - sn * b.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(FULL, acc[c], o);
+    if (lane != 0) return;
+    if (q == L) {
+        zero[0] = acc[0];
+        zero[1] = acc[1];
+        zero[2] = acc[4];
+        zero[3] = acc[5];
+        return;
+    }
+    if (q >= L / 2 - 1) {
+        tab[q - (L / 2 - 1)] = make_double4_32a(acc[0], acc[1], acc[2], acc[3]);
+        tab32[q - (L / 2 - 1)] = make_float4((float)acc[0], (float)acc[1], (float)acc[2], (float)acc[3]);
+    }
+    if (col && q <= L / 2) {
+        col[q] = make_double4_32a(acc[4], acc[5], acc[6], acc[7]);
+        col32[q] = make_float4((float)acc[4], (float)acc[5], (float)acc[6], (float)acc[7]);
+    }
+}
+
+// ----------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------
 static void gauss_legendre16(double *x, double *w) {
@@ -1118,6 +1310,78 @@ int launch_gf_table(const Problem &pr, cudaStream_t s) {
                                                panels);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "gf_table_kernel launch");
+    return QQMC_OK;
+}
+
+// Builds the dot (and, for the current, dot-lead) tables of finite-bandwidth
+// leads; returns g^<_00(0) and gamma g^<_01(0) in zero[0..3] (host).  Panels:
+// at most 2 radians of phase D T per panel and a quarter of the resonance
+// width Gamma / D.
+int launch_lead_table(Problem &pr, cudaStream_t s, double *zero) {
+    const qqmc_params &p = pr.params;
+    const double D = p.half_bandwidth, V = p.bias;
+    LeadQuad q{};
+    q.gam = p.gamma;
+    q.Ed = p.eps_d;
+    q.D = D;
+    const double pi2 = 1.5707963267948966;
+    double br[4];
+    double fl[3], fr[3];
+    int nb = 0;
+    br[nb++] = -pi2;
+    if (0.5 * V < D && V > 0.0) {
+        br[nb++] = asin(-0.5 * V / D);
+        br[nb++] = asin(0.5 * V / D);
+        fl[0] = 1; fr[0] = 1;  // w < -V/2
+        fl[1] = 1; fr[1] = 0;  // -V/2 < w < V/2
+        fl[2] = 0; fr[2] = 0;  // w > V/2
+    } else if (0.5 * V < D) {  // V = 0: one Fermi step at w = 0
+        br[nb++] = 0.0;
+        fl[0] = 1; fr[0] = 1;
+        fl[1] = 0; fr[1] = 0;
+    } else {  // the bias window covers the band
+        fl[0] = 1; fr[0] = 0;
+    }
+    br[nb++] = pi2;
+    double dth = fmin(fmin(2.0 / (D * p.t_max), 0.25 * p.gamma / D), 0.05);
+    long long nq = 0;
+    q.n_seg = nb - 1;
+    for (int sg = 0; sg < q.n_seg; ++sg) {
+        q.seg[sg].a = br[sg];
+        q.seg[sg].b = br[sg + 1];
+        long long pn = (long long)ceil((br[sg + 1] - br[sg]) / dth);
+        if (pn < 1) pn = 1;
+        q.seg[sg].panels = (int)(pn > (1 << 22) ? (1 << 22) : pn);
+        q.seg[sg].first = (int)nq;
+        q.seg[sg].fL = fl[sg];
+        q.seg[sg].fR = fr[sg];
+        nq += 16 * pn;
+    }
+    if (nq > (1ll << 24))
+        return set_error(QQMC_E_INVAL, "half_bandwidth x t_max too large for the lead-table quadrature");
+    double *d_w = nullptr, *d_zero = nullptr;
+    dbl4 *d_s00 = nullptr, *d_s01 = nullptr;
+    cudaError_t e = cudaMalloc(&d_w, nq * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&d_s00, nq * sizeof(dbl4));
+    if (e == cudaSuccess) e = cudaMalloc(&d_s01, nq * sizeof(dbl4));
+    if (e == cudaSuccess) e = cudaMalloc(&d_zero, 4 * sizeof(double));
+    if (e == cudaSuccess) {
+        lead_spectrum_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(q, (int)nq, d_w, d_s00, d_s01);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const long long threads = 32ll * (pr.L + 1);
+        lead_table_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
+            (int)nq, d_w, d_s00, d_s01, pr.L, p.t_max, pr.h, pr.d_table, pr.d_table32, pr.d_col, pr.d_col32, d_zero);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(zero, d_zero, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_w);
+    cudaFree(d_s00);
+    cudaFree(d_s01);
+    cudaFree(d_zero);
+    if (e != cudaSuccess) return cuda_error(e, "lead table build");
     return QQMC_OK;
 }
 

@@ -101,6 +101,8 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     it.L = P->L;
     it.chunks_per_shift = (int)cps;
     it.alpha = P->params.alpha;
+    it.col = P->params.observable == QQMC_OBS_CURRENT ? P->d_col : nullptr;
+    it.col32 = P->params.observable == QQMC_OBS_CURRENT ? P->d_col32 : nullptr;
     it.proj = P->d_proj[order];
     it.proj_cells = P->proj_cells[order];
     Tuning tu = get_tuning(precision, order);

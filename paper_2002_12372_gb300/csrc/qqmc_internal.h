@@ -26,6 +26,10 @@ struct Problem {
     int device = 0;
     double *d_proj[kMaxOrder + 1] = {};  // learned warp per order: [order][proj_cells[order] + 1]
     int proj_cells[kMaxOrder + 1] = {};
+    // current observable: dot-lead tables gamma g^<_01, gamma g^>_01 at nodes k = 0 .. L/2
+    dbl4 *d_col = nullptr;
+    float4 *d_col32 = nullptr;
+    double c0_re = 0, c0_im = 0;  // gamma g^<_01(0)
 };
 
 // One item as the device sees it.
@@ -44,6 +48,8 @@ struct ItemDev {
     const double *proj;      // learned warp: [order][proj_cells + 1] CDF per dimension, or null (plain)
     int proj_cells;
     double alpha;            // quadratic shift: vertex diagonals are g^<(0) - i alpha
+    const dbl4 *col;         // current: dot-lead column table [L/2 + 1] at nodes 0 .. L/2, else null
+    const float4 *col32;
 };
 
 struct Tuning {
@@ -64,6 +70,7 @@ void shift_words(uint64_t seed, int n_shifts, int n_dims, uint32_t *out);
 // Kernel launchers (kernels.cu).
 int upload_direction_numbers();
 int launch_gf_table(const Problem &pr, cudaStream_t s);
+int launch_lead_table(Problem &pr, cudaStream_t s, double *zero);
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                           int n_max, int precision, const Tuning &tune, cudaStream_t s);
 cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
@@ -79,5 +86,7 @@ cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_
 cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
                              const Tuning &tune, cudaStream_t s);
 Tuning get_tuning(int precision, int order);
+bool valid_params(const qqmc_params *p, std::string &why);
+double order0_value(const Problem &pr);
 
 }  // namespace qqmc

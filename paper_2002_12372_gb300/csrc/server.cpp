@@ -239,8 +239,10 @@ void qqmc_server::run() {
             lk.lock();
             for (size_t q = 0; q < admit.size(); ++q) {
                 Req &R = reqs[admit[q]];
-                // Q_0 = -2i g^<(0) = 2 <n> = 1 - 2 arctan(eps_d / Gamma) / pi
-                R.out.q[0] = 1.0 - 2.0 * atan(rq[q].params.eps_d / rq[q].params.gamma) / M_PI;
+                // order 0 from the problem's own tables: Q_0 = -2i g^<(0), I_0 = -4 Re gamma g^<_01(0)
+                R.out.q[0] = q < b.problems.size()
+                                 ? order0_value(*reinterpret_cast<const Problem *>(b.problems[q]))
+                                 : 0.0;
                 R.out.n_max = rq[q].n_max;
             }
             if (rc != QQMC_OK) {
@@ -294,10 +296,8 @@ extern "C" int qqmc_submit(qqmc_server *s, const qqmc_request *r, uint64_t *hand
     if (r->n_shifts < 2 || r->n_shifts > 1024) return set_error(QQMC_E_INVAL, "n_shifts must be in 2..1024");
     if (r->n_points < 1 || r->n_points > (1ull << QQMC_MAX_POINTS_LOG2))
         return set_error(QQMC_E_INVAL, "n_points must be in 1..2^30");
-    const qqmc_params &p = r->params;
-    if (!(p.gamma > 0) || !(p.t_max > 0) || !(p.tau > 0) || p.n_table < 4 || (p.n_table & 1) || !isfinite(p.eps_d) ||
-        !isfinite(p.alpha))
-        return set_error(QQMC_E_INVAL, "malformed request parameters");
+    std::string why;
+    if (!valid_params(&r->params, why)) return set_error(QQMC_E_INVAL, "malformed request parameters: " + why);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return set_error(QQMC_E_CANCELLED, "server is shutting down");
     if ((int)s->queue.size() >= s->opts.max_queue) return set_error(QQMC_E_BUSY, "request queue is full");

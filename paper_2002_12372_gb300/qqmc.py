@@ -31,6 +31,8 @@ QQMC_E_NOTFOUND = -8
 QQMC_MAX_ORDER = 16
 QQMC_PREC_FP64 = 0
 QQMC_PREC_MIXED = 1
+QQMC_OBS_CHARGE = 0
+QQMC_OBS_CURRENT = 1
 
 # Every symbol the header declares (checked by the tests against the library).
 EXPORTED = [
@@ -40,14 +42,15 @@ EXPORTED = [
     "qqmc_shift_words", "qqmc_sobol_points", "qqmc_warp_points", "qqmc_integrand", "qqmc_server_create",
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
     "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola", "qqmc_set_projection",
-    "qqmc_learn_projection",
+    "qqmc_learn_projection", "qqmc_set_current_tables", "qqmc_problem_current_tables",
 ]
 
 
 class qqmc_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("eps_d", ctypes.c_double), ("t_max", ctypes.c_double),
-                ("tau", ctypes.c_double), ("n_table", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("alpha", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("n_table", ctypes.c_int32), ("observable", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("alpha", ctypes.c_double), ("half_bandwidth", ctypes.c_double),
+                ("bias", ctypes.c_double)]
 
 
 class qqmc_result(ctypes.Structure):
@@ -126,6 +129,8 @@ def load(path: str = LIB_PATH):
         "qqmc_set_projection": [vp, ctypes.c_int, dp, ctypes.c_int],
         "qqmc_learn_projection": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_int, dp],
+        "qqmc_set_current_tables": [vp, dp, dp, ctypes.c_double, ctypes.c_double],
+        "qqmc_problem_current_tables": [vp, dp, dp, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -184,6 +189,27 @@ def qqmc_problem_tables(pr: int, L: int):
     _check(load().qqmc_problem_tables(ctypes.c_void_p(pr), _ptr(gl, ctypes.c_double), _ptr(gg, ctypes.c_double),
                                       _ptr(g0, ctypes.c_double)), "qqmc_problem_tables")
     return gl.view(np.complex128), gg.view(np.complex128), complex(g0[0], g0[1])
+
+
+def qqmc_set_current_tables(pr: int, c_lesser: np.ndarray, c_greater: np.ndarray, c0: complex) -> None:
+    """Dot-lead tables gamma g^<_01, gamma g^>_01 on the problem's full mesh (L complex values each)."""
+    cl = np.ascontiguousarray(np.asarray(c_lesser, dtype=np.complex128)).view(np.float64)
+    cg = np.ascontiguousarray(np.asarray(c_greater, dtype=np.complex128)).view(np.float64)
+    if cl.size != cg.size or cl.size % 4:
+        raise ValueError("dot-lead tables must have the problem's n_table entries")
+    _check(load().qqmc_set_current_tables(ctypes.c_void_p(pr), _ptr(cl, ctypes.c_double), _ptr(cg, ctypes.c_double),
+                                          float(np.real(c0)), float(np.imag(c0))), "qqmc_set_current_tables")
+
+
+def qqmc_problem_current_tables(pr: int, L: int):
+    """(gamma g^<_01, gamma g^>_01 at nodes 0..L/2, gamma g^<_01(0))."""
+    cl = np.zeros(2 * (L // 2 + 1))
+    cg = np.zeros(2 * (L // 2 + 1))
+    c0 = np.zeros(2)
+    _check(load().qqmc_problem_current_tables(ctypes.c_void_p(pr), _ptr(cl, ctypes.c_double),
+                                              _ptr(cg, ctypes.c_double), _ptr(c0, ctypes.c_double)),
+           "qqmc_problem_current_tables")
+    return cl.view(np.complex128), cg.view(np.complex128), complex(c0[0], c0[1])
 
 
 def qqmc_integrate(pr: int, order: int, n_points: int, n_shifts: int, precision: int = QQMC_PREC_FP64,
@@ -393,5 +419,5 @@ def qqmc_server_destroy(server: int) -> None:
 
 
 def make_params(gamma=1.0, eps_d=0.0, t_max=10.0, tau=1.0, n_table=4096, seed=2002123720,
-                alpha=0.0) -> qqmc_params:
-    return qqmc_params(gamma, eps_d, t_max, tau, n_table, 0, seed, alpha)
+                alpha=0.0, observable=QQMC_OBS_CHARGE, half_bandwidth=0.0, bias=0.0) -> qqmc_params:
+    return qqmc_params(gamma, eps_d, t_max, tau, n_table, observable, seed, alpha, half_bandwidth, bias)

@@ -149,3 +149,37 @@ def synthetic_projection(seed: int, n: int, cells: int = 1024) -> np.ndarray:
         out[d, 1:] = np.cumsum(h) / h.sum()
         out[d, -1] = 1.0
     return out
+
+
+def synthetic_column_tables(seed: int, L: int, T: float, components: int = 3):
+    """Seeded dot-lead tables for the current on the mesh tau_k = -T + k 2T/(L-1):
+    c^<(tau) = sum_j b_j e^{-i e_j tau - gam_j |tau|} and c^> likewise with its own
+    complex amplitudes (|b| ~ 0.1), a smooth complex function with the decay
+    scales of the dot tables.  Returns (c_lesser [L], c_greater [L], c0 = c^<(0))."""
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(-1.5, 1.5, components)
+    gam = rng.uniform(0.05, 0.3, components)
+    bl = 0.1 * (rng.normal(size=components) + 1j * rng.normal(size=components))
+    bg = 0.1 * (rng.normal(size=components) + 1j * rng.normal(size=components))
+    tau = -T + np.arange(L, dtype=np.float64) * (2.0 * T / (L - 1))
+    z = np.exp(-1j * e[None, :] * tau[:, None] - gam[None, :] * np.abs(tau[:, None]))
+    return z @ bl, z @ bg, complex(bl.sum())
+
+
+@dataclass
+class CurrentConfig:
+    """Finite-bias current through the dot with semicircular leads (App. C/E current
+    calculations): D = 2, Gamma = 0.1, t = 10 / Gamma, exponential warp tau = 1.5 / Gamma,
+    orders 1..10, quadratic shift alpha with E_d, V = U / 7 at U = 6 Gamma."""
+    name: str = "current-D2-Gamma0.1-t100-n1-10"
+    gamma: float = 0.1
+    half_bandwidth: float = 2.0
+    E_d: float = 0.09
+    alpha: float = 0.27
+    U: float = 0.6
+    bias: float = 0.6 / 7.0
+    t_max: float = 100.0
+    tau: float = 15.0
+    n_table: int = 4096
+    orders: tuple = tuple(range(1, 11))
+    n_shifts: int = 10
