@@ -62,7 +62,7 @@ extern "C" {
 #define QQMC_E_CANCELLED (-7) /* request cancelled before completion */
 #define QQMC_E_NOTFOUND (-8)  /* unknown handle */
 
-#define QQMC_MAX_ORDER 16
+#define QQMC_MAX_ORDER 22
 #define QQMC_MAX_POINTS_LOG2 30 /* N <= 2^30 points per shifted sequence */
 
 /* Observable (qqmc_params.observable). */

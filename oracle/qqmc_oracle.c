@@ -37,7 +37,7 @@
 
 typedef double complex cplx;
 
-#define ORACLE_MAX_ORDER 16
+#define ORACLE_MAX_ORDER 22
 
 /* ---- table interpolation (plain definition of linear interpolation) ---- */
 static cplx table_at(const double *tab, int L, double T, double tau) {

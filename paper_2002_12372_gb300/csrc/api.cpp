@@ -289,6 +289,9 @@ struct qqmc_plan {
     unsigned long long *d_counter = nullptr;
     double *d_out = nullptr;
     unsigned long long *d_counts = nullptr;
+    void *d_gstack = nullptr;       // FP64 tree stack in device memory (orders whose stack exceeds shared memory)
+    long long gstack_warps = 0;
+    int nmax_warp = 0;
     Tuning tune{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ek0 = nullptr, ek1 = nullptr;
     bool kernel_timed = false;
@@ -308,6 +311,7 @@ static void free_plan(qqmc_plan *pl) {
     cudaFree(pl->d_counter);
     cudaFree(pl->d_out);
     cudaFree(pl->d_counts);
+    cudaFree(pl->d_gstack);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     if (pl->ek0) cudaEventDestroy(pl->ek0);
@@ -428,6 +432,19 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     pl->chunks_lane = cl;
     pl->tune.flat = plan_flat;
     pl->tune.flat_min = plan_flat;
+    for (int q = 0; q < pl->n_warp; ++q)
+        pl->nmax_warp = pl->hitems[q].order > pl->nmax_warp ? pl->hitems[q].order : pl->nmax_warp;
+    if (pl->n_warp > 0) {
+        size_t bpw = 0;
+        pl->gstack_warps = detsum_gstack_warps(pl->nmax_warp, precision, pl->tune, &bpw);
+        if (pl->gstack_warps > 0) {
+            e = cudaMalloc(&pl->d_gstack, (size_t)pl->gstack_warps * bpw);
+            if (e != cudaSuccess) {
+                free_plan(pl);
+                return set_error(QQMC_E_NOMEM, "device allocation of the tree stack failed");
+            }
+        }
+    }
     e = cudaMemcpy(pl->d_shifts, hs.data(), sizeof(uint32_t) * shift_words_total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(pl->d_items, pl->hitems.data(), sizeof(ItemDev) * n_items, cudaMemcpyHostToDevice);
@@ -448,9 +465,8 @@ static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
     if (e != cudaSuccess) return e;
     if (timed && (e = cudaEventRecord(pl->ek0, s)) != cudaSuccess) return e;
     if (pl->n_warp > 0) {
-        int nmax_warp = 0;
-        for (int q = 0; q < pl->n_warp; ++q) nmax_warp = pl->hitems[q].order > nmax_warp ? pl->hitems[q].order : nmax_warp;
-        e = launch_detsum(pl->d_items, pl->n_warp, pl->chunks_warp, pl->d_counter, nmax_warp, pl->precision, pl->tune, s);
+        e = launch_detsum(pl->d_items, pl->n_warp, pl->chunks_warp, pl->d_counter, pl->nmax_warp, pl->precision,
+                          pl->tune, pl->d_gstack, pl->gstack_warps, s);
         if (e != cudaSuccess) return e;
     }
     const int n_lane = (int)pl->items.size() - pl->n_warp;

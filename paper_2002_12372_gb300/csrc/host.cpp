@@ -46,6 +46,12 @@ static const JoeKuo kJoeKuo[] = {
     {6, 1, {1, 3, 3, 9, 7, 49}},
     {6, 13, {1, 1, 1, 15, 21, 21}},
     {6, 16, {1, 3, 1, 13, 27, 49}},
+    {6, 19, {1, 1, 1, 15, 7, 5}},
+    {6, 22, {1, 3, 1, 15, 13, 25}},
+    {6, 25, {1, 1, 5, 5, 19, 61}},
+    {7, 1, {1, 3, 7, 11, 23, 15, 103}},
+    {7, 4, {1, 3, 7, 13, 13, 15, 69}},
+    {7, 7, {1, 1, 3, 13, 7, 35, 63}},
 };
 
 // V[d][j] = m_{j+1} * 2^{31-j}: the j-th direction word of dimension d.

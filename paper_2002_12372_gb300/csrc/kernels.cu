@@ -44,6 +44,7 @@ __constant__ double c_gl_x[16];
 __constant__ double c_gl_w[16];
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory one block can address
 
 // ----------------------------------------------------------------------------
 // complex helpers
@@ -220,6 +221,14 @@ struct WarpSmem {
     double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t)
 };
 
+// wrow, bdet and bip serve the general cooperative expansion: breadth-first
+// levels (flat depth below the tree leaf) and depth-first steps wider than a
+// warp (children of more than 32 rows, orders >= 18).
+__host__ __device__ inline bool needs_wide_buffers(int n_max, int RF) {
+    const int rl = n_max - 1 < kTreeLeaf ? n_max - 1 : kTreeLeaf;
+    return RF < rl || 2 * (n_max - 1) > 32;
+}
+
 __host__ __device__ inline size_t stack_entries(int n_max) {
     size_t tot = 0;
     int R0 = n_max - 1;
@@ -251,25 +260,29 @@ __host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
     return m;
 }
 
+// Shared memory of one warp; with a global stack (gs) the Schur-tree levels
+// live in a per-warp slice of device memory instead (FP64 orders >= 21, whose
+// stack alone exceeds the 227 KB a block can address).
 template <class R>
-__host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF) {
-    size_t wr = 2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64;
-    size_t c = stack_entries(n_max) + wr + 2 * (size_t)(n_max + 1) * (n_max + 1) + n_max + 1 +
-               bfs_max_entries(n_max, RF) + 64 + 32;
-    size_t bytes = c * sizeof(cx<R>);
-    bytes = (bytes + 15) & ~(size_t)15;
+__host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF, bool gs = false) {
+    size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
+    size_t c = (gs ? 0 : stack_entries(n_max)) + 2 * (size_t)(n_max + 1) * (n_max + 1) + n_max + 1 +
+               bfs_max_entries(n_max, RF) + wide;
+    size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
     bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
     return (bytes + 127) & ~(size_t)127;
 }
 
 template <class R>
-__device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int RF) {
+__device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack = nullptr) {
     WarpSmem<R> w;
     cx<R> *p = reinterpret_cast<cx<R> *>(base);
-    w.stack = p;
-    p += stack_entries(n_max);
-    w.wrow = p;
-    p += 2 * n_max > 64 ? 2 * n_max : 64;
+    if (gstack) {
+        w.stack = gstack;
+    } else {
+        w.stack = p;
+        p += stack_entries(n_max);
+    }
     w.P = p;
     p += (n_max + 1) * (n_max + 1);
     w.Rr = p;
@@ -278,10 +291,15 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     p += n_max + 1;
     w.bfs = p;
     p += bfs_max_entries(n_max, RF);
-    w.bdet = p;
-    p += 64;
-    w.bip = p;
-    p += 32;
+    w.wrow = w.bdet = w.bip = nullptr;
+    if (needs_wide_buffers(n_max, RF)) {
+        w.wrow = p;
+        p += 2 * n_max > 64 ? 2 * n_max : 64;
+        w.bdet = p;
+        p += 64;
+        w.bip = p;
+        p += 32;
+    }
     size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
     w.upt = reinterpret_cast<double *>(base + off);
     return w;
@@ -800,13 +818,15 @@ __device__ __forceinline__ void point_gap(const ItemDev &I, int m, uint32_t y, d
 // ----------------------------------------------------------------------------
 // Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
 // ----------------------------------------------------------------------------
-template <class R, int RFMAX>
+template <class R, int RFMAX, bool GS>
 __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
-                              unsigned long long *counter, int n_max, int rf_min) {
+                              unsigned long long *counter, int n_max, int rf_min, cx<R> *gstack) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, rf_min), n_max, rf_min);
+    cx<R> *gst = nullptr;
+    if (GS) gst = gstack + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * stack_entries(n_max);
+    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, rf_min, GS), n_max, rf_min, gst);
     const int NU = n_max + 1;
     while (true) {
         unsigned long long c = 0;
@@ -857,9 +877,8 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
             // every warp-per-point item of a launch shares the launch's flat depth
-            cx<double> s =
-                keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, item_col<R>(I), inv_h, s0, I.L,
-                                      RFMAX, lane);
+            cx<double> s = keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, item_col<R>(I), inv_h,
+                                                 s0, I.L, RFMAX, lane);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -1035,30 +1054,31 @@ __global__ void warp_kernel(int order, uint64_t first, uint64_t count, const uin
 }
 
 // One warp per caller point.
-template <class R, int RF>
-__global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, double *out, int n_max) {
+// One warp per caller point, grid-stride over the points.
+template <class R, int RF, bool GS>
+__global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, double *out, int n_max, cx<R> *gstack) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF), n_max, RF);
+    const uint64_t wid = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
+    cx<R> *gst = nullptr;
+    if (GS) gst = gstack + wid * stack_entries(n_max);
+    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF, GS), n_max, RF, gst);
     const int n = I.order;
-    uint64_t q = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
-    if (q >= count) return;
-    if (lane == 0) {
-        ws.upt[0] = I.t;
-        for (int m = 0; m < n; ++m) ws.upt[1 + m] = u[q * n + m];
-    }
-    __syncwarp();
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
     const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
     const double inv_h = 1.0 / I.h;
-    cx<double> s =
-        keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I), inv_h, I.T * inv_h, I.L,
-                           RF, lane);
-    if (lane == 0) {
-        cx<double> cval = times_i_pow(s, n);
-        out[2 * q] = cval.re;
-        out[2 * q + 1] = cval.im;
+    for (uint64_t q = wid; q < count; q += (uint64_t)gridDim.x * (blockDim.x >> 5)) {
+        if (lane <= n) ws.upt[lane] = lane == 0 ? I.t : u[q * n + lane - 1];
+        __syncwarp();
+        cx<double> s = keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I), inv_h,
+                                          I.T * inv_h, I.L, RF, lane);
+        if (lane == 0) {
+            cx<double> cval = times_i_pow(s, n);
+            out[2 * q] = cval.re;
+            out[2 * q + 1] = cval.im;
+        }
+        __syncwarp();
     }
 }
 
@@ -1391,49 +1411,94 @@ size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
     return per * tune.warps_per_block;
 }
 
-template <class R, int F>
+// The FP64 tree stack moves to device memory when it does not fit in shared memory.
+template <class R>
+static bool stack_in_global(int n_max, int rf_min) {
+    return sizeof(R) == 8 && warp_smem_bytes<R>(n_max, rf_min) > kSmemMax;
+}
+
+template <class R, int F, bool GS>
 static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
-                                   unsigned long long *d_counter, int n_max, int wpb, int rf_min, cudaStream_t s) {
+                                   unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
+                                   long long gstack_warps, cudaStream_t s) {
     // fewer warps per block when the shared memory of the requested shape does not fit
-    const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min);
-    if (per_warp > 227 * 1024) return cudaErrorInvalidConfiguration;
-    while (wpb > 1 && per_warp * wpb > 227 * 1024) --wpb;
+    const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min, GS);
+    if (per_warp > kSmemMax) return cudaErrorInvalidConfiguration;
+    while (wpb > 1 && per_warp * wpb > kSmemMax) --wpb;
     size_t smem = per_warp * wpb;
-    cudaError_t e = cudaFuncSetAttribute(detsum_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(detsum_kernel<R, F, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, detsum_kernel<R, F>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, detsum_kernel<R, F, GS>, wpb * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long want = (total_chunks + wpb - 1) / wpb;
     long long grid = (long long)sms * per_sm;
     if (grid > want) grid = want;
-    if (grid < 1) grid = 1;
-    detsum_kernel<R, F><<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max,
-                                                                rf_min);
+    if (GS) {
+        if (!gstack) return cudaErrorInvalidValue;
+        if (grid > gstack_warps / wpb) grid = gstack_warps / wpb;
+    }
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    detsum_kernel<R, F, GS><<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max,
+                                                                    rf_min, static_cast<cx<R> *>(gstack));
     return cudaGetLastError();
 }
 
+template <class R, int F>
+static cudaError_t launch_detsum_f(const ItemDev *d_items, int n_items, long long total_chunks,
+                                   unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
+                                   long long gstack_warps, cudaStream_t s) {
+    if constexpr (sizeof(R) == 8) {
+        if (stack_in_global<R>(n_max, rf_min))
+            return launch_detsum_t<R, F, true>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack,
+                                               gstack_warps, s);
+    }
+    return launch_detsum_t<R, F, false>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, nullptr, 0, s);
+}
+
+static int clamp_rf_min(const Tuning &tune) {
+    return tune.flat_min < 2 ? 2 : (tune.flat_min > tune.flat ? tune.flat : tune.flat_min);
+}
+
+long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp) {
+    const int rf_min = clamp_rf_min(tune);
+    *bytes_per_warp = 0;
+    if (precision != QQMC_PREC_FP64 || !stack_in_global<double>(n_max, rf_min)) return 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t per_warp = warp_smem_bytes<double>(n_max, rf_min, true);
+    const long long per_sm = (long long)(kSmemMax / per_warp);  // resident warps, bound by shared memory
+    *bytes_per_warp = stack_entries(n_max) * sizeof(cx<double>);
+    return (long long)sms * (per_sm < 1 ? 1 : per_sm);
+}
+
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
-                          int n_max, int precision, const Tuning &tune, cudaStream_t s) {
+                          int n_max, int precision, const Tuning &tune, void *gstack, long long gstack_warps,
+                          cudaStream_t s) {
     const int wpb = tune.warps_per_block;
-    const int rf_min = tune.flat_min < 2 ? 2 : (tune.flat_min > tune.flat ? tune.flat : tune.flat_min);
+    const int rf_min = clamp_rf_min(tune);
+#define QQMC_DETSUM(RT, F)                                                                                        \
+    launch_detsum_f<RT, F>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack, gstack_warps, s)
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
-            case 2: return launch_detsum_t<double, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
-            case 3: return launch_detsum_t<double, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
-            case 4: return launch_detsum_t<double, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
-            default: return launch_detsum_t<double, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+            case 2: return QQMC_DETSUM(double, 2);
+            case 3: return QQMC_DETSUM(double, 3);
+            case 4: return QQMC_DETSUM(double, 4);
+            default: return QQMC_DETSUM(double, 5);
         }
     }
     switch (tune.flat) {
-        case 2: return launch_detsum_t<float, 2>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
-        case 3: return launch_detsum_t<float, 3>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
-        case 4: return launch_detsum_t<float, 4>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
-        default: return launch_detsum_t<float, 5>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, s);
+        case 2: return QQMC_DETSUM(float, 2);
+        case 3: return QQMC_DETSUM(float, 3);
+        case 4: return QQMC_DETSUM(float, 4);
+        default: return QQMC_DETSUM(float, 5);
     }
+#undef QQMC_DETSUM
 }
 
 template <class R>
@@ -1482,19 +1547,40 @@ cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_
     return cudaGetLastError();
 }
 
-template <class R, int F>
+template <class R, int F, bool GS>
 static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
                                       cudaStream_t s) {
-    const size_t per_warp = warp_smem_bytes<R>(item.order, F);
-    if (per_warp > 227 * 1024) return cudaErrorInvalidConfiguration;
-    const int wpb = per_warp * 2 <= 227 * 1024 ? 2 : 1;
+    const size_t per_warp = warp_smem_bytes<R>(item.order, F, GS);
+    if (per_warp > kSmemMax) return cudaErrorInvalidConfiguration;
+    const int wpb = per_warp * 2 <= kSmemMax ? 2 : 1;
     size_t smem = per_warp * wpb;
     cudaError_t e =
-        cudaFuncSetAttribute(integrand_kernel<R, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(integrand_kernel<R, F, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    unsigned blocks = (unsigned)((count + wpb - 1) / wpb);
-    integrand_kernel<R, F><<<blocks, wpb * 32, smem, s>>>(item, count, d_u, d_out, item.order);
-    return cudaGetLastError();
+    uint64_t blocks = (count + wpb - 1) / wpb;
+    cx<R> *gstack = nullptr;
+    if (GS) {  // check path: a bounded number of warps, each with its own slice of device memory
+        if (blocks > 304) blocks = 304;
+        e = cudaMalloc(&gstack, blocks * wpb * stack_entries(item.order) * sizeof(cx<R>));
+        if (e != cudaSuccess) return e;
+    }
+    integrand_kernel<R, F, GS><<<(unsigned)blocks, wpb * 32, smem, s>>>(item, count, d_u, d_out, item.order, gstack);
+    e = cudaGetLastError();
+    if (GS) {
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(gstack);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e;
+}
+
+template <class R, int F>
+static cudaError_t launch_integrand_f(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
+                                      cudaStream_t s) {
+    if constexpr (sizeof(R) == 8) {
+        if (stack_in_global<R>(item.order, F)) return launch_integrand_t<R, F, true>(item, count, d_u, d_out, s);
+    }
+    return launch_integrand_t<R, F, false>(item, count, d_u, d_out, s);
 }
 
 cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
@@ -1502,17 +1588,17 @@ cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *
     if (count == 0) return cudaSuccess;
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
-            case 2: return launch_integrand_t<double, 2>(item, count, d_u, d_out, s);
-            case 3: return launch_integrand_t<double, 3>(item, count, d_u, d_out, s);
-            case 4: return launch_integrand_t<double, 4>(item, count, d_u, d_out, s);
-            default: return launch_integrand_t<double, 5>(item, count, d_u, d_out, s);
+            case 2: return launch_integrand_f<double, 2>(item, count, d_u, d_out, s);
+            case 3: return launch_integrand_f<double, 3>(item, count, d_u, d_out, s);
+            case 4: return launch_integrand_f<double, 4>(item, count, d_u, d_out, s);
+            default: return launch_integrand_f<double, 5>(item, count, d_u, d_out, s);
         }
     }
     switch (tune.flat) {
-        case 2: return launch_integrand_t<float, 2>(item, count, d_u, d_out, s);
-        case 3: return launch_integrand_t<float, 3>(item, count, d_u, d_out, s);
-        case 4: return launch_integrand_t<float, 4>(item, count, d_u, d_out, s);
-        default: return launch_integrand_t<float, 5>(item, count, d_u, d_out, s);
+        case 2: return launch_integrand_f<float, 2>(item, count, d_u, d_out, s);
+        case 3: return launch_integrand_f<float, 3>(item, count, d_u, d_out, s);
+        case 4: return launch_integrand_f<float, 4>(item, count, d_u, d_out, s);
+        default: return launch_integrand_f<float, 5>(item, count, d_u, d_out, s);
     }
 }
 

@@ -109,6 +109,11 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     it.flat = tu.flat;
     if (it.flat < 2 && order > 4) it.flat = 2;
     if (tu.flat < 2) tu.flat = tu.flat_min = 2;
+    size_t gs_bytes = 0;
+    if (!(it.flat == 1 && order <= kLaneMaxOrder) && detsum_gstack_warps(order, precision, tu, &gs_bytes) > 0)
+        return set_error(QQMC_E_INVAL,
+                         "qqmc_integrate_noalloc: this order's FP64 tree stack needs device memory; use the mixed "
+                         "precision or qqmc_integrate");
 
     ItemDev *d_item = reinterpret_cast<ItemDev *>(base + kItemOff);
     unsigned long long *d_counter = reinterpret_cast<unsigned long long *>(base + kCounterOff);
@@ -120,7 +125,7 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
         if (it.flat == 1 && order <= kLaneMaxOrder)
             e = launch_lane(d_item, 1, (long long)(cps * n_shifts), d_counter, precision, s);
         else
-            e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, s);
+            e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, nullptr, 0, s);
     }
     if (e == cudaSuccess) e = launch_reduce(d_item, 1, n_shifts, d_sums, counts, s);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrate_noalloc");

@@ -72,7 +72,11 @@ int upload_direction_numbers();
 int launch_gf_table(const Problem &pr, cudaStream_t s);
 int launch_lead_table(Problem &pr, cudaStream_t s, double *zero);
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
-                          int n_max, int precision, const Tuning &tune, cudaStream_t s);
+                          int n_max, int precision, const Tuning &tune, void *gstack, long long gstack_warps,
+                          cudaStream_t s);
+// Warps (and bytes per warp) of device memory the determinant launch needs for
+// its tree stack; 0 when the stack fits in shared memory.
+long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp);
 cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                         int precision, cudaStream_t s);
 constexpr int kLaneMaxOrder = 4;  // orders that may run one point per lane

@@ -28,7 +28,7 @@ QQMC_E_BUSY = -5
 QQMC_E_TIMEOUT = -6
 QQMC_E_CANCELLED = -7
 QQMC_E_NOTFOUND = -8
-QQMC_MAX_ORDER = 16
+QQMC_MAX_ORDER = 22
 QQMC_PREC_FP64 = 0
 QQMC_PREC_MIXED = 1
 QQMC_OBS_CHARGE = 0

@@ -36,15 +36,16 @@ def test_every_declared_symbol_is_exported(Q):
 
 def test_direction_numbers_match_scipy_sobol(Q):
     from scipy.stats import qmc
-    V = Q.qqmc_direction_numbers(16)
+    D = Q.QQMC_MAX_ORDER
+    V = Q.qqmc_direction_numbers(D)
     # natural-order point 2^j is V[:, j]; scipy emits Gray order: out[2^j-1] ^ out[2^j] = V[:, j]
-    pts = np.rint(qmc.Sobol(16, scramble=False, bits=32).random(2 ** 14) * 2.0 ** 32).astype(np.uint64)
+    pts = np.rint(qmc.Sobol(D, scramble=False, bits=32).random(2 ** 14) * 2.0 ** 32).astype(np.uint64)
     for j in range(14):
         assert np.array_equal((pts[(1 << j) - 1] ^ pts[1 << j]).astype(np.uint32), V[:, j]), j
     # Gray-code points from V reproduce scipy exactly
     i = np.arange(2 ** 14, dtype=np.uint64)
     g = i ^ (i >> np.uint64(1))
-    X = np.zeros((2 ** 14, 16), dtype=np.uint32)
+    X = np.zeros((2 ** 14, D), dtype=np.uint32)
     for j in range(14):
         bit = ((g >> np.uint64(j)) & np.uint64(1)).astype(bool)
         X[bit] ^= V[:, j]
@@ -58,7 +59,7 @@ def test_shift_words_match_oracle_splitmix(Q):
 
 def test_argument_errors_without_device(Q):
     with pytest.raises(Q.QQMCError) as e:
-        Q.qqmc_sobol_points(17, 0, 4)
+        Q.qqmc_sobol_points(Q.QQMC_MAX_ORDER + 1, 0, 4)
     assert e.value.code == Q.QQMC_E_RANGE
     with pytest.raises(Q.QQMCError) as e:
         Q.qqmc_direction_numbers(0)

@@ -9,6 +9,8 @@ Keldysh tables, shift words, vertex times.  Bars:
   * FP64 coefficients per shift: relative 1e-10 (the stated target);
   * mixed precision: the bound stated in each test.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -323,7 +325,7 @@ def test_checkpoint_resume_by_index_cursor(Q, W, oracle):
         Q.qqmc_destroy_problem(pr)
 
 
-@pytest.mark.parametrize("order", [13, 14, 16])
+@pytest.mark.parametrize("order", [13, 14, 16, 17, 18])
 def test_high_orders_match_oracle(Q, W, oracle, order):
     """Orders beyond the benchmark table (the paper reaches 22): integrand parity at a few points
     and, at order 13, a small integration against the oracle."""
@@ -342,3 +344,54 @@ def test_high_orders_match_oracle(Q, W, oracle, order):
             assert np.all(np.abs(S - S0) <= 1e-10 * np.abs(S0))
     finally:
         Q.qqmc_destroy_problem(pr)
+
+
+def _golden_high_orders():
+    rows = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "high_order_integrand.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, re, im, sc = line.split()
+                rows[int(n)] = (complex(float(re), float(im)), float(sc))
+    return rows
+
+
+@pytest.mark.parametrize("order", [19, 20, 21, 22])
+def test_orders_19_to_22_match_stored_oracle_values(Q, W, order):
+    """Orders 19..22 against oracle values stored by tests/golden/make_high_order_integrand.py
+    (the oracle needs 10 s to 2 min per point there).  From order 21 the FP64 tree stack lives in
+    device memory; the mixed path keeps it in shared memory."""
+    c_ref, scale = _golden_high_orders()[order]
+    T = 10.0
+    pr, _ = _problem(Q, W, seed=200 + order, T=T)
+    try:
+        u = W.ordered_times(300 + order, 1, order, T)
+        gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)[0]
+        mixed = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_MIXED)[0]
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    assert abs(gpu - c_ref) <= 1e-12 * scale, abs(gpu - c_ref) / scale
+    assert abs(mixed - c_ref) <= 2.0 ** -20 * scale, abs(mixed - c_ref) / scale
+
+
+def test_order_22_plan_equals_its_points(Q, W):
+    """A batched FP64 plan at order 22 (tree stack in device memory) returns the weighted sum of
+    the integrand at its own warped points."""
+    T, n, N = 10.0, 22, 40
+    pr, _ = _problem(Q, W, seed=222, T=T, tau=0.35)
+    try:
+        sw = W.shift_words(2222, 1, n)
+        plan = Q.Plan([(pr, n, 1, N, sw)], Q.QQMC_PREC_FP64)
+        plan.launch()
+        (res, S), = plan.results()
+        plan.close()
+        u, w, ins = Q.qqmc_warp_points(pr, n, 0, N, sw[0])
+        c = Q.qqmc_integrand(pr, n, u[ins], Q.QQMC_PREC_FP64)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    assert res.n_in_domain == int(ins.sum()) > 0
+    ref = np.sum(w[ins] * c) / N
+    # The two kernels round differently (separately compiled), and at order 22 the Keldysh sum
+    # cancels to |c| ~ 1e-11 of its terms, so an FP64 c is good to ~1e-4 relative; a bookkeeping
+    # error (wrong point, weight or stack slice) would be O(1).
+    assert abs(S[0] - ref) <= 1e-3 * np.sum(np.abs(w[ins] * c)) / N

@@ -103,7 +103,7 @@ def test_failure_paths_report_codes(Q):
     srv = Q.qqmc_server_create(Q.qqmc_server_opts(device_memory_limit=1, precision=0, max_queue=2,
                                                   request_timeout_s=0.05))
     try:
-        bad = _req(Q, 0.0, 10.0, 17, 1024)
+        bad = _req(Q, 0.0, 10.0, Q.QQMC_MAX_ORDER + 1, 1024)
         with pytest.raises(Q.QQMCError) as e:
             Q.qqmc_submit(srv, bad)
         assert e.value.code == Q.QQMC_E_RANGE
