@@ -94,14 +94,15 @@ def lib():
         L.oracle_estimate.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
                                       ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64), ctypes.c_double,
-                                      dp]
+                                      dp, ctypes.c_int]
         L.oracle_warp.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
-                                  ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int32)]
+                                  ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+        L.oracle_points.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_int, u32p]
         L.oracle_det.argtypes = [ctypes.c_int, dp, dp]
         L.oracle_estimate_proj.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double, ctypes.c_double,
                                            dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(i64),
-                                           ctypes.c_double, dp]
+                                           ctypes.c_double, dp, ctypes.c_int]
         L.oracle_table_at.argtypes = [dp, ctypes.c_int, ctypes.c_double, i64, dp, dp]
         _lib = L
     return _lib
@@ -347,16 +348,70 @@ def sobol_points(n: int, i0: int, count: int, V: np.ndarray) -> np.ndarray:
     return out
 
 
-def warp(n: int, i0: int, count: int, V: np.ndarray, shift: np.ndarray, t: float, tau: float):
+def _family(n: int, V, lattice):
+    """(generator words, log2 N): Sobol' direction numbers V [n, 32] with m = 0, or a rank-1
+    lattice given as (z [>= n], m) for N = 2^m points."""
+    if lattice is None:
+        return np.ascontiguousarray(V[:n], dtype=np.uint32), 0
+    z, m = lattice
+    return np.ascontiguousarray(np.asarray(z, dtype=np.uint32)[:n]), int(m)
+
+
+def warp(n: int, i0: int, count: int, V: np.ndarray, shift: np.ndarray, t: float, tau: float, lattice=None):
     """Warped points: (u [count, n], weight C/p_n [count], in-domain flag [count])."""
-    Vc = np.ascontiguousarray(V[:n], dtype=np.uint32)
+    Vc, lm = _family(n, V, lattice)
     S = np.ascontiguousarray(shift[:n], dtype=np.uint32)
     u = np.zeros((count, n))
     w = np.zeros(count)
     ins = np.zeros(count, dtype=np.int32)
     lib().oracle_warp(n, i0, count, _u32p(Vc), _u32p(S), t, tau, _dp(u), _dp(w),
-                      ins.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+                      ins.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), lm)
     return u, w, ins.astype(bool)
+
+
+def lattice_points(n: int, i0: int, count: int, z: np.ndarray, m: int, shift: np.ndarray) -> np.ndarray:
+    """Shifted rank-1 lattice words uint32 [count, n]: ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32."""
+    Vc, lm = _family(n, None, (z, m))
+    S = np.ascontiguousarray(np.asarray(shift, dtype=np.uint32)[:n])
+    out = np.zeros((count, n), dtype=np.uint32)
+    if lib().oracle_points(n, i0, count, _u32p(Vc), _u32p(S), lm, _u32p(out)) != 0:
+        raise ValueError("oracle_points rejected its arguments")
+    return out
+
+
+def lattice_cbc_criterion(z: np.ndarray, m: int, gamma: np.ndarray) -> float:
+    """Shift-averaged worst-case error squared of the rank-1 lattice (N = 2^m, generating vector z)
+    in the Korobov-type space with smoothness 2 and product weights gamma:
+        e^2(z) = -1 + (1/N) sum_{k=0}^{N-1} prod_d (1 + gamma_d 2 pi^2 B_2({k z_d / N})),
+    B_2(x) = x^2 - x + 1/6 (the criterion minimised by component-by-component constructions)."""
+    N = 1 << m
+    k = np.arange(N, dtype=np.int64)
+    prod = np.ones(N)
+    for d, zd in enumerate(np.asarray(z, dtype=np.int64)):
+        x = ((k * zd) % N) / N
+        prod *= 1.0 + gamma[d] * 2.0 * math.pi ** 2 * (x * x - x + 1.0 / 6.0)
+    return float(prod.mean() - 1.0)
+
+
+def lattice_cbc(m: int, dims: int, gamma: np.ndarray) -> np.ndarray:
+    """Component-by-component construction: z_1 = 1, then each z_d the odd number in [1, N/2]
+    (z and N - z give the same points up to reflection) minimising e^2 given z_1..z_{d-1};
+    ties (equal up to rounding: e.g. z and its inverse mod N give the same point set) go to the
+    smallest z.  Plain O(dims N^2) evaluation (small N only)."""
+    N = 1 << m
+    k = np.arange(N, dtype=np.int64)
+    cand = np.arange(1, N // 2 + 1, 2, dtype=np.int64) if N > 2 else np.array([1], dtype=np.int64)
+    z = [1]
+    prod = 1.0 + gamma[0] * 2.0 * math.pi ** 2 * ((k / N) ** 2 - k / N + 1.0 / 6.0)
+    for d in range(1, dims):
+        x = ((k[None, :] * cand[:, None]) % N) / N
+        vals = (prod[None, :] * (1.0 + gamma[d] * 2.0 * math.pi ** 2 * (x * x - x + 1.0 / 6.0))).mean(axis=1)
+        lo = float(np.min(vals))
+        best = int(cand[np.nonzero(vals <= lo + 1e-12 * abs(lo))[0][0]])
+        z.append(best)
+        xb = ((k * best) % N) / N
+        prod = prod * (1.0 + gamma[d] * 2.0 * math.pi ** 2 * (xb * xb - xb + 1.0 / 6.0))
+    return np.array(z, dtype=np.uint32)
 
 
 # --------------------------------------------------------------------------
@@ -424,12 +479,12 @@ def table_at(table: np.ndarray, T: float, tau: np.ndarray) -> np.ndarray:
 
 
 def _estimate_chunk(args):
-    n, i0, i1, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha, cp = args
+    n, i0, i1, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha, cp, lm = args
     res = np.zeros(4)
     n_in = ctypes.c_int64(0)
     rc = lib().oracle_estimate(n, i0, i1, _u32p(Vc), _u32p(S), t, tau, _dp(gl_t), _dp(gg_t), L, T,
                                float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in),
-                               float(alpha), _cp(cp))
+                               float(alpha), _cp(cp), lm)
     if rc != 0:
         raise ValueError("oracle_estimate rejected its arguments")
     return res, n_in.value
@@ -437,17 +492,18 @@ def _estimate_chunk(args):
 
 def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T: float,
              V: np.ndarray | None = None, threads: int | None = None, i0: int = 0,
-             chunk: int = 4096, alpha: float = 0.0, col=None):
+             chunk: int = 4096, alpha: float = 0.0, col=None, lattice=None):
     """Per-shift estimates S_k = (1/N) sum_{i=i0}^{i0+N-1} w_i c(u_i), Eq. (warped_int2).
+    lattice = (z, m): a rank-1 lattice of 2^m points instead of Sobol' (shifts added mod 2^32).
 
     shifts: uint32 [K, >= n] digital-shift words.  Returns (S [K] complex,
     n_in [K] int).  Point ranges are split into chunks run on a thread pool
     (the C call releases the GIL); each chunk is a Neumaier sum and the
     chunk totals are combined with math.fsum (exact rounding).
     """
-    if V is None:
+    if V is None and lattice is None:
         V = sobol_direction_numbers(max(n, 1))
-    Vc = np.ascontiguousarray(V[:n], dtype=np.uint32)
+    Vc, lm = _family(n, V, lattice)
     gl, gg, gl0 = tables
     gl_t, gg_t = _tab(gl), _tab(gg)
     L = gl_t.size // 2
@@ -459,7 +515,7 @@ def estimate(n: int, N: int, shifts: np.ndarray, t: float, tau: float, tables, T
         S = np.ascontiguousarray(shifts[k, :n])
         for a in range(i0, i0 + N, chunk):
             b = min(a + chunk, i0 + N)
-            jobs.append((k, (n, a, b, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha, cp)))
+            jobs.append((k, (n, a, b, Vc, S, t, tau, gl_t, gg_t, L, T, gl0, alpha, cp, lm)))
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(max_workers=threads) as ex:
         results = list(ex.map(_estimate_chunk, [j[1] for j in jobs]))
@@ -602,7 +658,7 @@ def _estimate_proj_chunk(args):
     n_in = ctypes.c_int64(0)
     rc = lib().oracle_estimate_proj(n, i0, i1, _u32p(Vc), _u32p(S), t, tau, _dp(cdf), cells, _dp(gl_t), _dp(gg_t),
                                     L, T, float(np.real(gl0)), float(np.imag(gl0)), _dp(res), ctypes.byref(n_in),
-                                    float(alpha), _cp(cp))
+                                    float(alpha), _cp(cp), 0)
     if rc != 0:
         raise ValueError("oracle_estimate_proj rejected its arguments")
     return res, n_in.value

@@ -20,6 +20,10 @@
  *     App. B (main computing loop), with C = int p_n = tau^n.
  *   - Sobol' points (Gray-code order) with a digital shift: main text below
  *     Eq. (warped_int2) and App. H (digitally shifted generators).
+ *   - Or a rank-1 lattice with N = 2^m points and a random shift (the lattice
+ *     rules the paper cites as the alternative low-discrepancy family):
+ *     x_i = frac(i z / N + Delta), held as 32-bit fixed point, so the point
+ *     word is ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32.
  *
  * The determinant of every Keldysh configuration is formed independently by
  * LU factorisation with partial pivoting; there is no reuse between
@@ -227,11 +231,28 @@ int oracle_sobol(int n, int64_t i0, int64_t count, const uint32_t *V, uint32_t *
     return 0;
 }
 
+/* Shifted point words of index i: Sobol' (digital shift, XOR) when lattice_m
+ * == 0, else the rank-1 lattice with generating vector V[0..n-1] and N = 2^m
+ * (shift added modulo 2^32). */
+static void point_words(int n, int64_t i, const uint32_t *V, const uint32_t *S, int lattice_m, uint32_t *X) {
+    if (lattice_m == 0) {
+        oracle_sobol(n, i, 1, V, X);
+        for (int d = 0; d < n; ++d) X[d] ^= S[d];
+        return;
+    }
+    uint64_t mask = (lattice_m >= 64) ? ~0ull : ((1ull << lattice_m) - 1ull);
+    for (int d = 0; d < n; ++d) {
+        uint64_t r = ((uint64_t)i * (uint64_t)V[d]) & mask;
+        X[d] = (uint32_t)((r << (32 - lattice_m)) + (uint64_t)S[d]);
+    }
+}
+
 /*
  * Partial QQMC estimate over point indices [i0, i1) of one digitally shifted
- * Sobol' sequence: returns sum_i w_i c(u_i) (Neumaier-compensated, re/im) and
- * the number of points inside the domain.
- *   x_m = (X_{i,m-1} XOR S_{m-1}) * 2^-32,
+ * Sobol' sequence (or one randomly shifted lattice, see point_words): returns
+ * sum_i w_i c(u_i) (Neumaier-compensated, re/im) and the number of points
+ * inside the domain.
+ *   x_m = (shifted point word of dimension m-1) * 2^-32,
  *   v_m = -tau * log1p(-x_m)          (inverse CDF of h(v) = exp(-v/tau)),
  *   u_0 = t, u_m = u_{m-1} - v_m,     in domain iff u_n > 0,
  *   w   = C / p_n(u) with C = tau^n and p_n = prod_m exp(-v_m / tau).
@@ -240,18 +261,18 @@ int oracle_sobol(int n, int64_t i0, int64_t count, const uint32_t *V, uint32_t *
 int oracle_estimate(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint32_t *S,
                     double t, double tau, const double *gl, const double *gg, int L,
                     double T, double gl0_re, double gl0_im, double *result, int64_t *n_in, double alpha,
-                    const double *col) {
-    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2) return -1;
+                    const double *col, int lattice_m) {
+    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || lattice_m < 0 || lattice_m > 32) return -1;
     gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
     int64_t inside = 0;
     uint32_t X[ORACLE_MAX_ORDER];
     double u[ORACLE_MAX_ORDER];
     for (int64_t i = i0; i < i1; ++i) {
-        oracle_sobol(n, i, 1, V, X);
+        point_words(n, i, V, S, lattice_m, X);
         double uprev = t, vsum = 0.0;
         for (int m = 0; m < n; ++m) {
-            double x = (double)(X[m] ^ S[m]) * 0x1p-32;
+            double x = (double)X[m] * 0x1p-32;
             double v = -tau * log1p(-x);
             vsum += v;
             u[m] = uprev - v;
@@ -280,13 +301,14 @@ int oracle_estimate(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint
 
 /* Warped points only (for the domain / weight checks): u (count x n), w, flag. */
 int oracle_warp(int n, int64_t i0, int64_t count, const uint32_t *V, const uint32_t *S,
-                double t, double tau, double *u_out, double *w_out, int32_t *inside) {
+                double t, double tau, double *u_out, double *w_out, int32_t *inside, int lattice_m) {
     uint32_t X[ORACLE_MAX_ORDER];
+    if (lattice_m < 0 || lattice_m > 32) return -1;
     for (int64_t q = 0; q < count; ++q) {
-        oracle_sobol(n, i0 + q, 1, V, X);
+        point_words(n, i0 + q, V, S, lattice_m, X);
         double uprev = t, vsum = 0.0;
         for (int m = 0; m < n; ++m) {
-            double x = (double)(X[m] ^ S[m]) * 0x1p-32;
+            double x = (double)X[m] * 0x1p-32;
             double v = -tau * log1p(-x);
             vsum += v;
             u_out[q * n + m] = uprev - v;
@@ -295,6 +317,14 @@ int oracle_warp(int n, int64_t i0, int64_t count, const uint32_t *V, const uint3
         w_out[q] = pow(tau, (double)n) / exp(-vsum / tau);
         inside[q] = (u_out[q * n + n - 1] > 0.0);
     }
+    return 0;
+}
+
+/* Shifted point words (count x n) of either point family; for the pins. */
+int oracle_points(int n, int64_t i0, int64_t count, const uint32_t *V, const uint32_t *S, int lattice_m,
+                  uint32_t *out) {
+    if (n < 1 || n > ORACLE_MAX_ORDER || lattice_m < 0 || lattice_m > 32) return -1;
+    for (int64_t q = 0; q < count; ++q) point_words(n, i0 + q, V, S, lattice_m, out + q * n);
     return 0;
 }
 
@@ -338,18 +368,18 @@ static double learned_w(const double *cdf, int cells, double x, double *jac) {
 int oracle_estimate_proj(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint32_t *S, double t,
                          double tau, const double *cdf, int cells, const double *gl, const double *gg, int L,
                          double T, double gl0_re, double gl0_im, double *result, int64_t *n_in,
-                         double alpha, const double *col) {
-    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || cells < 1) return -1;
+                         double alpha, const double *col, int lattice_m) {
+    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || cells < 1 || lattice_m < 0 || lattice_m > 32) return -1;
     gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
     int64_t inside = 0;
     uint32_t X[ORACLE_MAX_ORDER];
     double u[ORACLE_MAX_ORDER];
     for (int64_t i = i0; i < i1; ++i) {
-        oracle_sobol(n, i, 1, V, X);
+        point_words(n, i, V, S, lattice_m, X);
         double uprev = t, vsum = 0.0, jt = 1.0;
         for (int m = 0; m < n; ++m) {
-            double x = (double)(X[m] ^ S[m]) * 0x1p-32;
+            double x = (double)X[m] * 0x1p-32;
             double jac;
             double w = learned_w(cdf + (size_t)m * (cells + 1), cells, x, &jac);
             double v = -tau * log1p(-w);
