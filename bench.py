@@ -179,6 +179,9 @@ def run_ours(args, ws, rank, local, pg):
     plans = [Q.Plan(workload_items(Q, problems, s, slice_n), prec) for s in range(n_plans)]
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
     wpb, flat = Q.qqmc_get_tuning(prec, max(ORDERS))
+    # every item runs with its own order's tuned flat depth (one launch per shape group);
+    # one-point-per-lane orders (flat 1) resolve all their vertices per lane
+    flat_of = {n: (lambda f: f if f >= 2 else n - 1)(Q.qqmc_get_tuning(prec, n)[1]) for n in ORDERS}
 
     def step(s):
         p = plans[s % n_plans]
@@ -211,7 +214,7 @@ def run_ours(args, ws, rank, local, pg):
             pts += r.n_points * r.n_shifts
             pts_in += r.n_in_domain
             dets += r.n_in_domain * 2.0 ** r.order
-            flops += r.n_in_domain * perf.flops_per_point(r.order, flat)
+            flops += r.n_in_domain * perf.flops_per_point(r.order, flat_of[r.order])
             naive += r.n_in_domain * perf.w_naive(r.order)
     torch.cuda.synchronize()
     _barrier(pg)
@@ -258,6 +261,7 @@ def run_ours(args, ws, rank, local, pg):
                    "precision": args.precision, "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "tuning": {"warps_per_block": wpb, "flat_vertices": flat,
+                              "flat_per_order": flat_of,
                               "source": "autotuner table" if tuned else "built-in defaults"}},
         "in_domain_evals_per_s": _sum_over_ranks(pg, pts_in) / dev_s_max,
         "keldysh_det_evals_per_s": _sum_over_ranks(pg, dets) / dev_s_max,
@@ -269,7 +273,8 @@ def run_ours(args, ws, rank, local, pg):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": _launch_traffic(args, slice_n),
-                     "kernel": "detsum_kernel<%s,%d>" % ("double" if args.precision == "fp64" else "float", flat),
+                     "kernel": "detsum_kernel<%s,flat> (one launch per tuned flat depth)" % (
+                         "double" if args.precision == "fp64" else "float"),
                      "peak_source": "derived: 152 SMs x %d %s FMA lanes x 2 flops x 2070 MHz" % (
                          perf.FP64_LANES if args.precision == "fp64" else perf.FP32_LANES, args.precision),
                      "kernel_ms_per_step": k_s * 1e3 / args.steps},
@@ -282,10 +287,11 @@ def run_ours(args, ws, rank, local, pg):
     return out
 
 
-# DRAM bytes (read + write) of one detsum launch of the default benchmark step,
-# from a 1-pass ncu capture of this exact command (profiles/detsum_*_plain-dot_n1-10.md).
+# DRAM bytes (read + write) of the detsum launches of one default benchmark step (one launch per
+# tuned flat depth: two here), from a 1-pass ncu capture of this exact command
+# (profiles/detsum_*_plain-dot_n1-10.md); per step, like the achieved rate.
 # Set to None whenever the determinant kernel changes until it is captured again.
-MEASURED_LAUNCH_TRAFFIC = {"fp64": None, "mixed": None}
+MEASURED_LAUNCH_TRAFFIC = {"fp64": 649.98e3 + 1.59e6 + 35.33e3, "mixed": 365.06e3 + 85.25e3 + 495.62e3}
 
 
 def _launch_traffic(args, slice_n):
@@ -447,6 +453,42 @@ def run_current(args, local):
             "per_order": {r.order: {"I": r.q_mean, "err": r.q_err, "in_domain": r.n_in_domain} for r, _ in res}}
 
 
+def run_lattice(args, local):
+    """Sobol' against a rank-1 lattice (component-by-component vector, product weights 0.9^d) on the
+    plain dot at equal point counts: per order the estimate, its shift error bar, and the time."""
+    import numpy as np
+    import torch
+
+    Q = _setup(args, local)
+    prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
+    m, K = args.lattice_log2, 16
+    orders = (2, 4, 6, 8, 10)
+    gamma = np.array([0.9 ** d for d in range(max(orders))])
+    z = Q.qqmc_lattice_cbc(m, max(orders), gamma)
+    stream = torch.cuda.Stream()
+    rows = {}
+    for family in ("sobol", "lattice"):
+        pr = Q.qqmc_create_problem(Q.make_params(GAMMA, 0.0, T_MAX, TAU, L_TABLE, SEED))
+        if family == "lattice":
+            Q.qqmc_set_lattice(pr, m, z)
+        plan = Q.Plan([(pr, n, K, 1 << m) for n in orders], prec)
+        plan.launch(stream.cuda_stream)
+        res = plan.results()
+        ms = plan.timing()[0]
+        plan.close()
+        Q.qqmc_destroy_problem(pr)
+        for r, _ in res:
+            rows.setdefault(r.order, {})[family] = {"q": r.q_mean, "err": r.q_err}
+        rows.setdefault("kernel_ms", {})[family] = ms
+    ratios = [rows[n]["sobol"]["err"] / rows[n]["lattice"]["err"] for n in orders]
+    return {"metric": "lattice_vs_sobol_error_ratio", "value": float(np.exp(np.mean(np.log(ratios)))),
+            "unit": "geometric mean of err(Sobol')/err(lattice)", "n_gpus": 1,
+            "config": {"workload": "plain dot Gamma=1, eps_d=0, t=10, tau=1, L=4096, orders %s, N=2^%d x %d shifts"
+                                   % (list(orders), m, K), "precision": args.precision,
+                       "lattice": "CBC, product weights 0.9^d, z=%s" % list(map(int, z))},
+            "per_order": rows}
+
+
 def run_serving(args, local):
     """Request sweep with Poisson arrivals through qqmc_submit / qqmc_poll (continuous batching)."""
     import torch
@@ -455,7 +497,7 @@ def run_serving(args, local):
 
     Q = _setup(args, local)
     prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
-    reqs = W.serving_sweep(SEED, args.requests, 50.0, args.serve_log2_min, args.serve_log2_max, 16)
+    reqs = W.serving_sweep(SEED, args.requests, args.rate, args.serve_log2_min, args.serve_log2_max, 16)
     opts = Q.qqmc_server_opts(device_memory_limit=8 << 30, max_queue=4096, max_batch_items=256, precision=prec,
                               use_graph=0, request_timeout_s=0.0)
     srv = Q.qqmc_server_create(opts)
@@ -487,8 +529,8 @@ def run_serving(args, local):
     return {"metric": "serving", "value": evals / makespan, "unit": "evals/s", "n_gpus": 1,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": "%d requests, eps_d~U[-3,3], U in {1,2,4}, t_max in {5,10,20}, n_max~U{4..10}, "
-                                   "N=2^floor(U[%d,%d]), 16 shifts, Poisson arrivals at 50/s"
-                                   % (len(reqs), args.serve_log2_min, args.serve_log2_max),
+                                   "N=2^floor(U[%d,%d]), 16 shifts, Poisson arrivals at %g/s"
+                                   % (len(reqs), args.serve_log2_min, args.serve_log2_max, args.rate),
                        "precision": args.precision},
             "p50_latency_ms": pct(50), "p99_latency_ms": pct(99), "makespan_s": makespan,
             "completed": len(lat), "failed": len(reqs) - len(lat),
@@ -558,19 +600,22 @@ def main():
                     help="autotuner table (JSON keyed by GPU name); built-in defaults when absent")
     ap.add_argument("--slice-log2", type=int, default=16,
                     help="Sobol' indices per shift in one step (16: the benchmark batch; smaller for profiling)")
-    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving", "current"], default="plain",
+    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving", "current", "lattice"],
+                    default="plain",
                     help="plain: the benchmark workload; the others print their own study line")
     ap.add_argument("--precision-log2", type=int, default=22)
     ap.add_argument("--current-log2", type=int, default=16)
     ap.add_argument("--current-table", type=int, default=16384)
+    ap.add_argument("--lattice-log2", type=int, default=16)
     ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-log2-min", type=int, default=16)
     ap.add_argument("--serve-log2-max", type=int, default=22)
     args = ap.parse_args()
     if args.config != "plain":
         local = int(os.environ.get("LOCAL_RANK", "0"))
         fn = {"batched": run_batched, "precision": run_precision, "serving": run_serving,
-              "current": run_current}[args.config]
+              "current": run_current, "lattice": run_lattice}[args.config]
         print(json.dumps(fn(args, local)), flush=True)
         return
     ws, rank, local, pg = _dist()

@@ -147,6 +147,29 @@ int qqmc_destroy_problem(qqmc_problem *pr);
 int qqmc_problem_tables(const qqmc_problem *pr, double *g_lesser, double *g_greater, double *g0);
 
 /*
+ * Rank-1 lattice point set (the lattice rules the paper cites as the other
+ * randomised low-discrepancy family) instead of Sobol': N = 2^log2_n points
+ * x_i = frac(i z / N + Delta), z = generating vector (dims odd components),
+ * Delta the random shift.  Points are 32-bit fixed point like the Sobol'
+ * words: word_d = ((i z_d mod N) << (32 - log2_n)) + S_d mod 2^32, with the
+ * shift words S (caller or seed, as for Sobol') added instead of XORed.
+ * Every later integration on the problem uses the lattice; items must stay
+ * inside it (order <= dims, first_index + n_points <= N; E_INVAL otherwise).
+ * z = NULL restores Sobol'.  Errors: E_INVAL, E_NOMEM, E_CUDA.
+ */
+int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims);
+
+/*
+ * Component-by-component construction of a generating vector for N = 2^log2_n
+ * (3 <= log2_n <= 24): z_1 = 1, then each z_d the odd number <= N/2 minimising
+ * the shift-averaged worst-case error e^2 = -1 + (1/N) sum_k prod_d
+ * (1 + gamma_d 2 pi^2 B_2({k z_d / N})) (weighted Korobov space of smoothness 2,
+ * product weights gamma[0..dims-1] > 0), ties to the smallest z.  Host only,
+ * O(N log N) per component (FFT over the group of odd residues mod 2^m).
+ */
+int qqmc_lattice_cbc(int log2_n, int dims, const double *gamma, uint32_t *z);
+
+/*
  * Learned warp (paper App. F, "learning h from the integrand"): a second
  * change of variables w -> x on top of the exponential one, with
  * w_m = 1 - exp(-v_m / tau) in [0, 1).  Per dimension m the density of w_m is

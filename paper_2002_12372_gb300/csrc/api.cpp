@@ -222,6 +222,32 @@ extern "C" int qqmc_set_current_tables(qqmc_problem *pr, const double *cl, const
     return QQMC_OK;
 }
 
+extern "C" int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims) {
+    if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
+    if (!z) {  // back to Sobol'
+        cudaFree(pr->d_lat_z);
+        pr->d_lat_z = nullptr;
+        pr->lat_m = pr->lat_dims = 0;
+        return QQMC_OK;
+    }
+    if (log2_n < 1 || log2_n > 32 || dims < 1 || dims > kMaxOrder)
+        return set_error(QQMC_E_INVAL, "qqmc_set_lattice: need 1 <= log2_n <= 32 and 1 <= dims <= QQMC_MAX_ORDER");
+    for (int d = 0; d < dims; ++d)
+        if (!(z[d] & 1u)) return set_error(QQMC_E_INVAL, "qqmc_set_lattice: components must be odd (units mod 2^m)");
+    if (!pr->d_lat_z) {
+        cudaError_t e = cudaMalloc(&pr->d_lat_z, sizeof(uint32_t) * kMaxOrder);
+        if (e != cudaSuccess) {
+            pr->d_lat_z = nullptr;
+            return set_error(QQMC_E_NOMEM, "device allocation of the lattice failed");
+        }
+    }
+    cudaError_t e = cudaMemcpy(pr->d_lat_z, z, sizeof(uint32_t) * dims, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "lattice upload");
+    pr->lat_m = log2_n;
+    pr->lat_dims = dims;
+    return QQMC_OK;
+}
+
 extern "C" int qqmc_problem_current_tables(const qqmc_problem *pr, double *cl, double *cg, double *c0) {
     if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
     if (pr->params.observable != QQMC_OBS_CURRENT || !pr->d_col)
@@ -244,6 +270,7 @@ extern "C" int qqmc_destroy_problem(qqmc_problem *pr) {
     cudaFree(pr->d_table32);
     cudaFree(pr->d_col);
     cudaFree(pr->d_col32);
+    cudaFree(pr->d_lat_z);
     for (int n = 0; n <= kMaxOrder; ++n) cudaFree(pr->d_proj[n]);
     delete pr;
     return QQMC_OK;
@@ -277,7 +304,16 @@ struct qqmc_plan {
     std::vector<ItemDev> hitems;    // device order: highest order first (longest work first)
     std::vector<int> perm;          // device position -> caller index
     int n_warp = 0;                 // items [0, n_warp) run one warp per point, the rest one lane per point
-    long long chunks_warp = 0, chunks_lane = 0;
+    long long chunks_lane = 0;
+    // Warp-per-point items in groups of equal tuned shape (flat depth), one
+    // persistent launch per group with shared memory sized for its own
+    // highest order; every item runs with its own order's flat depth.
+    struct Group {
+        int first = 0, count = 0, n_max = 0;
+        long long chunks = 0;
+        Tuning tune{};
+    };
+    std::vector<Group> groups;
     int precision = 0;
     int n_max = 0;
     long long total_chunks = 0;
@@ -291,8 +327,6 @@ struct qqmc_plan {
     unsigned long long *d_counts = nullptr;
     void *d_gstack = nullptr;       // FP64 tree stack in device memory (orders whose stack exceeds shared memory)
     long long gstack_warps = 0;
-    int nmax_warp = 0;
-    Tuning tune{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ek0 = nullptr, ek1 = nullptr;
     bool kernel_timed = false;
     cudaGraphExec_t gexec = nullptr;
@@ -333,6 +367,9 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
             return set_error(QQMC_E_INVAL, "n_points must be in 1..2^30");
         if (it.n_shifts < 1 || it.n_shifts > 1024) return set_error(QQMC_E_INVAL, "n_shifts must be in 1..1024");
         if (it.first_index > (1ull << 40)) return set_error(QQMC_E_INVAL, "first_index too large");
+        const Problem *P = it.problem;
+        if (P->d_lat_z && (it.order > P->lat_dims || it.first_index + it.n_points > (1ull << P->lat_m)))
+            return set_error(QQMC_E_INVAL, "item outside its problem's lattice (order > its dimension or index >= N)");
     }
     int rc = ensure_device();
     if (rc != QQMC_OK) return rc;
@@ -351,34 +388,44 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         pl->total_shifts += it.n_shifts;
     }
     pl->total_chunks = (long long)chunk_total;
-    pl->tune = get_tuning(precision, pl->n_max);  // warps per block of the highest order
     cudaError_t e = cudaMalloc(&pl->d_items, sizeof(ItemDev) * n_items);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_shifts, sizeof(uint32_t) * shift_words_total);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_partials, sizeof(double) * 4 * chunk_total);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_inside, sizeof(unsigned int) * chunk_total);
-    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counter, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counter, (kMaxOrder + 2) * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_out, sizeof(double) * 2 * pl->total_shifts);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_counts, sizeof(unsigned long long) * pl->total_shifts);
     if (e != cudaSuccess) {
         free_plan(pl);
         return set_error(QQMC_E_NOMEM, std::string("device allocation of the plan failed: ") + cudaGetErrorString(e));
     }
-    // Device order: the warp-per-point items, then the one-point-per-lane items
-    // (orders <= 4 whose tuning asks for it); within each group highest order
+    // Device order: the warp-per-point items grouped by their order's tuned flat
+    // depth (groups holding higher orders first), then the one-point-per-lane
+    // items (orders <= 4 whose tuning asks for it); within a group highest order
     // first, then more points first, so the longest items start early and the
-    // persistent grid drains evenly.  Each group has its own chunk numbering.
+    // persistent grid drains evenly.  Each launch has its own chunk numbering.
     auto lane_mode = [&](int i) {
         return items[i].order <= kLaneMaxOrder && get_tuning(precision, items[i].order).flat == 1;
     };
+    auto flat_of = [&](int i) {
+        const int f = get_tuning(precision, items[i].order).flat;
+        return f < 2 ? 2 : f;
+    };
+    int group_top[6] = {0, 0, 0, 0, 0, 0};  // highest order per flat depth 2..5
+    for (int i = 0; i < n_items; ++i)
+        if (!lane_mode(i) && items[i].order > group_top[flat_of(i)]) group_top[flat_of(i)] = items[i].order;
     pl->perm.resize(n_items);
     for (int i = 0; i < n_items; ++i) pl->perm[i] = i;
     std::stable_sort(pl->perm.begin(), pl->perm.end(), [&](int a, int b) {
         if (lane_mode(a) != lane_mode(b)) return !lane_mode(a);
+        if (!lane_mode(a)) {
+            const int fa = flat_of(a), fb = flat_of(b);
+            if (group_top[fa] != group_top[fb]) return group_top[fa] > group_top[fb];
+            if (fa != fb) return fa > fb;
+        }
         if (items[a].order != items[b].order) return items[a].order > items[b].order;
         return items[a].n_points > items[b].n_points;
     });
-    // plan-wide flat depth of the warp-per-point items: the highest order's tuning
-    const int plan_flat = pl->tune.flat >= 2 ? pl->tune.flat : 2;
     std::vector<uint32_t> hs(shift_words_total);
     size_t so = 0, co = 0;
     long long cw = 0, cl = 0;
@@ -411,38 +458,49 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         d.n_shifts = it.n_shifts;
         d.L = pr->L;
         d.chunks_per_shift = (int)cps;
-        d.flat = lm ? 1 : plan_flat;
+        d.flat = lm ? 1 : flat_of(ci);
         d.alpha = pr->params.alpha;
         d.col = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col : nullptr;
         d.col32 = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col32 : nullptr;
+        d.lat_z = pr->d_lat_z;
+        d.lat_m = pr->lat_m;
         d.proj = pr->d_proj[it.order];
         d.proj_cells = pr->proj_cells[it.order];
         if (lm) {
             d.chunk_begin = cl;
             cl += (long long)cps * it.n_shifts;
         } else {
-            d.chunk_begin = cw;
-            cw += (long long)cps * it.n_shifts;
+            if (pl->groups.empty() || pl->groups.back().tune.flat != d.flat) {
+                qqmc_plan::Group g;
+                g.first = q;
+                g.n_max = it.order;  // highest order first within a group
+                g.tune = get_tuning(precision, it.order);
+                g.tune.flat = g.tune.flat_min = d.flat;
+                pl->groups.push_back(g);
+            }
+            qqmc_plan::Group &g = pl->groups.back();
+            d.chunk_begin = g.chunks;
+            g.chunks += (long long)cps * it.n_shifts;
+            ++g.count;
             ++pl->n_warp;
         }
         so += (size_t)it.n_shifts * it.order;
         co += cps * it.n_shifts;
     }
-    pl->chunks_warp = cw;
     pl->chunks_lane = cl;
-    pl->tune.flat = plan_flat;
-    pl->tune.flat_min = plan_flat;
-    for (int q = 0; q < pl->n_warp; ++q)
-        pl->nmax_warp = pl->hitems[q].order > pl->nmax_warp ? pl->hitems[q].order : pl->nmax_warp;
-    if (pl->n_warp > 0) {
+    // the groups launch one after another on the plan's stream and share one tree-stack buffer
+    size_t gs_bytes = 0;
+    for (const auto &g : pl->groups) {
         size_t bpw = 0;
-        pl->gstack_warps = detsum_gstack_warps(pl->nmax_warp, precision, pl->tune, &bpw);
-        if (pl->gstack_warps > 0) {
-            e = cudaMalloc(&pl->d_gstack, (size_t)pl->gstack_warps * bpw);
-            if (e != cudaSuccess) {
-                free_plan(pl);
-                return set_error(QQMC_E_NOMEM, "device allocation of the tree stack failed");
-            }
+        const long long w = detsum_gstack_warps(g.n_max, precision, g.tune, &bpw);
+        if ((size_t)w * bpw > gs_bytes) gs_bytes = (size_t)w * bpw;
+        if (w > pl->gstack_warps) pl->gstack_warps = w;
+    }
+    if (gs_bytes > 0) {
+        e = cudaMalloc(&pl->d_gstack, gs_bytes);
+        if (e != cudaSuccess) {
+            free_plan(pl);
+            return set_error(QQMC_E_NOMEM, "device allocation of the tree stack failed");
         }
     }
     e = cudaMemcpy(pl->d_shifts, hs.data(), sizeof(uint32_t) * shift_words_total, cudaMemcpyHostToDevice);
@@ -461,17 +519,22 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
 }
 
 static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
-    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, 2 * sizeof(unsigned long long), s);
+    const int ng = (int)pl->groups.size();
+    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, (ng + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (timed && (e = cudaEventRecord(pl->ek0, s)) != cudaSuccess) return e;
-    if (pl->n_warp > 0) {
-        e = launch_detsum(pl->d_items, pl->n_warp, pl->chunks_warp, pl->d_counter, pl->nmax_warp, pl->precision,
-                          pl->tune, pl->d_gstack, pl->gstack_warps, s);
+    for (int gi = 0; gi < ng; ++gi) {
+        const auto &g = pl->groups[gi];
+        // a group's share of the device-memory stack: the buffer holds the largest group's need
+        size_t bpw = 0;
+        const long long w = detsum_gstack_warps(g.n_max, pl->precision, g.tune, &bpw);
+        e = launch_detsum(pl->d_items + g.first, g.count, g.chunks, pl->d_counter + gi, g.n_max, pl->precision, g.tune,
+                          pl->d_gstack, w, s);
         if (e != cudaSuccess) return e;
     }
     const int n_lane = (int)pl->items.size() - pl->n_warp;
     if (n_lane > 0) {
-        e = launch_lane(pl->d_items + pl->n_warp, n_lane, pl->chunks_lane, pl->d_counter + 1, pl->precision, s);
+        e = launch_lane(pl->d_items + pl->n_warp, n_lane, pl->chunks_lane, pl->d_counter + ng, pl->precision, s);
         if (e != cudaSuccess) return e;
     }
     if (timed && (e = cudaEventRecord(pl->ek1, s)) != cudaSuccess) return e;
@@ -524,7 +587,7 @@ extern "C" int qqmc_plan_launch(qqmc_plan *pl, void *stream, int use_graph) {
 
 extern "C" int qqmc_plan_kernel_count(const qqmc_plan *pl) {
     if (!pl) return 0;
-    return 1 + (pl->n_warp > 0 ? 1 : 0) + ((int)pl->items.size() > pl->n_warp ? 1 : 0);
+    return 1 + (int)pl->groups.size() + ((int)pl->items.size() > pl->n_warp ? 1 : 0);
 }
 
 extern "C" int qqmc_plan_timing(const qqmc_plan *pl, double *kernel_ms, double *total_ms) {
@@ -694,7 +757,7 @@ extern "C" int qqmc_sobol_points(int order, uint64_t first, uint64_t count, cons
         e = d_shift.alloc(order);
         if (e == cudaSuccess) e = cudaMemcpy(d_shift.p, shift, sizeof(uint32_t) * order, cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = launch_sobol(order, first, count, shift ? d_shift.p : nullptr, d_out.p, 0);
+    if (e == cudaSuccess) e = launch_sobol(order, first, count, shift ? d_shift.p : nullptr, d_out.p, nullptr, 0, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out, d_out.p, sizeof(uint32_t) * count * order, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_sobol_points");
     return QQMC_OK;
@@ -718,9 +781,11 @@ extern "C" int qqmc_warp_points(const qqmc_problem *pr, int order, uint64_t firs
         e = d_shift.alloc(order);
         if (e == cudaSuccess) e = cudaMemcpy(d_shift.p, shift, sizeof(uint32_t) * order, cudaMemcpyHostToDevice);
     }
+    if (pr->d_lat_z && (order > pr->lat_dims || first + count > (1ull << pr->lat_m)))
+        return set_error(QQMC_E_INVAL, "points outside the problem's lattice (order > its dimension or index >= N)");
     if (e == cudaSuccess)
         e = launch_warp(order, first, count, shift ? d_shift.p : nullptr, pr->params.t_max, pr->params.tau, d_u.p,
-                        d_w.p, d_in.p, 0);
+                        d_w.p, d_in.p, pr->d_lat_z, pr->lat_m, 0);
     if (e == cudaSuccess) e = cudaMemcpy(u, d_u.p, sizeof(double) * count * order, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(w, d_w.p, sizeof(double) * count, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(inside, d_in.p, sizeof(int32_t) * count, cudaMemcpyDeviceToHost);

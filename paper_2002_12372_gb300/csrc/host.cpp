@@ -4,7 +4,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "qqmc_internal.h"
 
@@ -176,6 +178,118 @@ extern "C" int qqmc_resum_parabola(const double *a, const double *a_err, int n, 
             }
         }
         *err = sqrt(e2);
+    }
+    return QQMC_OK;
+}
+
+namespace qqmc {
+
+// In-place radix-2 complex DFT, X[f] = sum_n x[n] exp(-2 pi i f n / L) (inv: +i, no 1/L).
+static void fft(std::vector<double> &re, std::vector<double> &im, bool inv) {
+    const size_t L = re.size();
+    for (size_t i = 1, j = 0; i < L; ++i) {
+        size_t bit = L >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            std::swap(re[i], re[j]);
+            std::swap(im[i], im[j]);
+        }
+    }
+    for (size_t len = 2; len <= L; len <<= 1) {
+        const double ang = (inv ? 2.0 : -2.0) * M_PI / (double)len;
+        for (size_t i = 0; i < L; i += len) {
+            for (size_t k = 0; k < len / 2; ++k) {
+                const double wr = cos(ang * (double)k), wi = sin(ang * (double)k);
+                const size_t a = i + k, b = a + len / 2;
+                const double tr = re[b] * wr - im[b] * wi, ti = re[b] * wi + im[b] * wr;
+                re[b] = re[a] - tr;
+                im[b] = im[a] - ti;
+                re[a] += tr;
+                im[a] += ti;
+            }
+        }
+    }
+}
+
+// omega(x) = 2 pi^2 B_2(x), B_2(x) = x^2 - x + 1/6: the kernel of the shift-averaged worst-case
+// error of a rank-1 lattice in the weighted Korobov space of smoothness 2.
+static inline double omega(double x) { return 2.0 * M_PI * M_PI * (x * x - x + 1.0 / 6.0); }
+
+}  // namespace qqmc
+
+// Component-by-component construction for N = 2^m (see qqmc.h).  For each new
+// component the criterion of every candidate z is T(z) = sum_k p_k omega({k z / N}),
+// p the running product over the earlier components.  Grouping k = 2^j k' (k' odd)
+// turns the sum into one sum per modulus M = 2^(m-j) over the odd residues, a group
+// {+-5^a}; omega is symmetric, so each sum is a cyclic correlation of length M/4 in
+// the exponent a, done by FFT: O(N log N) per component.
+extern "C" int qqmc_lattice_cbc(int log2_n, int dims, const double *gamma, uint32_t *z) {
+    if (!z || !gamma || log2_n < 3 || log2_n > 24 || dims < 1 || dims > qqmc::kMaxOrder)
+        return qqmc::set_error(QQMC_E_INVAL, "qqmc_lattice_cbc: need 3 <= log2_n <= 24, 1 <= dims <= QQMC_MAX_ORDER");
+    for (int d = 0; d < dims; ++d)
+        if (!(gamma[d] > 0.0) || !isfinite(gamma[d])) return qqmc::set_error(QQMC_E_INVAL, "weights must be > 0");
+    const int m = log2_n;
+    const uint64_t N = 1ull << m;
+    // a_N(r): exponent of odd r = +-5^a mod N
+    std::vector<uint32_t> expo(N, 0);
+    {
+        uint64_t r = 1;
+        for (uint64_t a = 0; a < N / 4; ++a) {
+            expo[r] = (uint32_t)a;
+            expo[N - r] = (uint32_t)a;
+            r = (r * 5) & (N - 1);
+        }
+    }
+    std::vector<double> p(N);
+    for (uint64_t k = 0; k < N; ++k) p[k] = 1.0 + gamma[0] * qqmc::omega((double)k / (double)N);
+    z[0] = 1;
+    std::vector<double> T(N / 4);  // T indexed by a_N(z) (z and -z share it)
+    for (int d = 1; d < dims; ++d) {
+        std::fill(T.begin(), T.end(), p[0] * qqmc::omega(0.0));
+        for (int j = 0; j < m; ++j) {
+            const uint64_t M = N >> j;  // modulus; odd k' < M, k = 2^j k'
+            if (M == 2) {  // k' = 1: omega(1/2) for every z
+                const double v = p[(uint64_t)1 << j] * qqmc::omega(0.5);
+                for (auto &t : T) t += v;
+                continue;
+            }
+            if (M == 4) {  // k' z = 1 or 3 mod 4: omega(1/4) = omega(3/4)
+                const double v = (p[(uint64_t)1 << j] + p[(uint64_t)3 << j]) * qqmc::omega(0.25);
+                for (auto &t : T) t += v;
+                continue;
+            }
+            const uint64_t Lj = M / 4;
+            std::vector<double> qr(Lj), qi(Lj, 0.0), wr(Lj), wi(Lj, 0.0);
+            uint64_t r = 1;
+            for (uint64_t b = 0; b < Lj; ++b) {  // Q(b) = q(5^b) + q(-5^b), W(b) = omega(5^b / M)
+                qr[b] = p[r << j] + p[(M - r) << j];
+                wr[b] = qqmc::omega((double)r / (double)M);
+                r = (r * 5) & (M - 1);
+            }
+            qqmc::fft(qr, qi, false);
+            qqmc::fft(wr, wi, false);
+            for (uint64_t f = 0; f < Lj; ++f) {  // A^ = W^ conj(Q^)
+                const double ar = wr[f] * qr[f] + wi[f] * qi[f], ai = wi[f] * qr[f] - wr[f] * qi[f];
+                wr[f] = ar;
+                wi[f] = ai;
+            }
+            qqmc::fft(wr, wi, true);
+            for (uint64_t a = 0; a < N / 4; ++a) T[a] += wr[a % Lj] / (double)Lj;
+        }
+        // smallest odd z <= N/2 whose criterion is within rounding of the minimum
+        double lo = T[expo[1]];
+        for (uint64_t c = 3; c <= N / 2; c += 2) lo = T[expo[c]] < lo ? T[expo[c]] : lo;
+        const double tol = 1e-12 * fabs(lo) + 1e-300;
+        uint64_t best = 1;
+        for (uint64_t c = 1; c <= N / 2; c += 2)
+            if (T[expo[c]] <= lo + tol) {
+                best = c;
+                break;
+            }
+        z[d] = (uint32_t)best;
+        for (uint64_t k = 0; k < N; ++k)
+            p[k] *= 1.0 + gamma[d] * qqmc::omega((double)((k * best) & (N - 1)) / (double)N);
     }
     return QQMC_OK;
 }

@@ -147,6 +147,17 @@ __device__ __forceinline__ uint32_t sobol_word(int d, uint64_t i) {
     return x;
 }
 
+// Shifted point word of dimension d for index i: Sobol' with a digital shift
+// (XOR), or a rank-1 lattice of 2^lat_m points, x = frac(i z / N + Delta) in
+// 32-bit fixed point: ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32.
+__device__ __forceinline__ uint32_t point_word(const uint32_t *lat_z, int lat_m, int d, uint64_t i, uint32_t s) {
+    if (lat_z) {
+        const uint64_t r = (i * (uint64_t)lat_z[d]) & ((lat_m >= 64 ? 0ull : (1ull << lat_m)) - 1ull);
+        return (uint32_t)(r << (32 - lat_m)) + s;
+    }
+    return sobol_word(d, i) ^ s;
+}
+
 // ----------------------------------------------------------------------------
 // Table interpolation: half table starting at node L/2 - 1 (tau = -h/2).
 // ----------------------------------------------------------------------------
@@ -851,7 +862,7 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             ws.upt[lane * NU] = I.t;
             double jt = 1.0;
             for (int m = 0; m < n; ++m) {
-                uint32_t y = sobol_word(m, i) ^ I.shifts[k * n + m];
+                uint32_t y = point_word(I.lat_z, I.lat_m, m, i, I.shifts[k * n + m]);
                 double v, omx, jac;
                 point_gap<R>(I, m, y, v, omx, jac);
                 uprev = uprev - v;
@@ -911,7 +922,7 @@ __device__ __forceinline__ cx<double> lane_point(const ItemDev &I, int k, uint64
     u[0] = I.t;
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-        uint32_t y = sobol_word(m, i) ^ I.shifts[k * N + m];
+        uint32_t y = point_word(I.lat_z, I.lat_m, m, i, I.shifts[k * N + m]);
         double v, omx, jac;
         point_gap<R>(I, m, y, v, omx, jac);
         uprev = uprev - v;
@@ -1031,19 +1042,21 @@ __global__ void reduce_kernel(const ItemDev *__restrict__ items, int n_items, do
 // ----------------------------------------------------------------------------
 // Check kernels
 // ----------------------------------------------------------------------------
-__global__ void sobol_kernel(int order, uint64_t first, uint64_t count, const uint32_t *shift, uint32_t *out) {
+__global__ void sobol_kernel(int order, uint64_t first, uint64_t count, const uint32_t *shift, uint32_t *out,
+                             const uint32_t *lat_z, int lat_m) {
     uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (q >= count) return;
-    for (int m = 0; m < order; ++m) out[q * order + m] = sobol_word(m, first + q) ^ (shift ? shift[m] : 0u);
+    for (int m = 0; m < order; ++m)
+        out[q * order + m] = point_word(lat_z, lat_m, m, first + q, shift ? shift[m] : 0u);
 }
 
 __global__ void warp_kernel(int order, uint64_t first, uint64_t count, const uint32_t *shift, double t, double tau,
-                            double *u, double *w, int32_t *inside) {
+                            double *u, double *w, int32_t *inside, const uint32_t *lat_z, int lat_m) {
     uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (q >= count) return;
     double uprev = t, prod = 1.0;
     for (int m = 0; m < order; ++m) {
-        uint32_t y = sobol_word(m, first + q) ^ (shift ? shift[m] : 0u);
+        uint32_t y = point_word(lat_z, lat_m, m, first + q, shift ? shift[m] : 0u);
         double x = (double)y * 0x1p-32;
         uprev = uprev - (-tau * log1p(-x));
         u[q * order + m] = uprev;
@@ -1532,18 +1545,19 @@ cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts,
 }
 
 cudaError_t launch_sobol(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, uint32_t *d_out,
-                         cudaStream_t s) {
+                         const uint32_t *d_lat_z, int lat_m, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((count + 255) / 256);
-    sobol_kernel<<<blocks, 256, 0, s>>>(order, first, count, d_shift, d_out);
+    sobol_kernel<<<blocks, 256, 0, s>>>(order, first, count, d_shift, d_out, d_lat_z, lat_m);
     return cudaGetLastError();
 }
 
 cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, double t, double tau,
-                        double *d_u, double *d_w, int32_t *d_inside, cudaStream_t s) {
+                        double *d_u, double *d_w, int32_t *d_inside, const uint32_t *d_lat_z, int lat_m,
+                        cudaStream_t s) {
     if (count == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((count + 255) / 256);
-    warp_kernel<<<blocks, 256, 0, s>>>(order, first, count, d_shift, t, tau, d_u, d_w, d_inside);
+    warp_kernel<<<blocks, 256, 0, s>>>(order, first, count, d_shift, t, tau, d_u, d_w, d_inside, d_lat_z, lat_m);
     return cudaGetLastError();
 }
 

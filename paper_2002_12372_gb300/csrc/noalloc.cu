@@ -103,6 +103,10 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     it.alpha = P->params.alpha;
     it.col = P->params.observable == QQMC_OBS_CURRENT ? P->d_col : nullptr;
     it.col32 = P->params.observable == QQMC_OBS_CURRENT ? P->d_col32 : nullptr;
+    it.lat_z = P->d_lat_z;
+    it.lat_m = P->lat_m;
+    if (P->d_lat_z && (order > P->lat_dims || n_points > (1ull << P->lat_m)))
+        return set_error(QQMC_E_INVAL, "points outside the problem's lattice (order > its dimension or index >= N)");
     it.proj = P->d_proj[order];
     it.proj_cells = P->proj_cells[order];
     Tuning tu = get_tuning(precision, order);

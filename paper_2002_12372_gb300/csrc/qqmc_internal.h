@@ -30,6 +30,10 @@ struct Problem {
     dbl4 *d_col = nullptr;
     float4 *d_col32 = nullptr;
     double c0_re = 0, c0_im = 0;  // gamma g^<_01(0)
+    // rank-1 lattice point set (instead of Sobol'): generating vector and log2 of its size
+    uint32_t *d_lat_z = nullptr;
+    int lat_m = 0;
+    int lat_dims = 0;
 };
 
 // One item as the device sees it.
@@ -50,6 +54,8 @@ struct ItemDev {
     double alpha;            // quadratic shift: vertex diagonals are g^<(0) - i alpha
     const dbl4 *col;         // current: dot-lead column table [L/2 + 1] at nodes 0 .. L/2, else null
     const float4 *col32;
+    const uint32_t *lat_z;   // rank-1 lattice generating vector, or null (Sobol')
+    int lat_m;               // lattice size 2^lat_m
 };
 
 struct Tuning {
@@ -84,9 +90,10 @@ cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts,
                           cudaStream_t s);
 size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune);
 cudaError_t launch_sobol(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, uint32_t *d_out,
-                         cudaStream_t s);
+                         const uint32_t *d_lat_z, int lat_m, cudaStream_t s);
 cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, double t, double tau,
-                        double *d_u, double *d_w, int32_t *d_inside, cudaStream_t s);
+                        double *d_u, double *d_w, int32_t *d_inside, const uint32_t *d_lat_z, int lat_m,
+                        cudaStream_t s);
 cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
                              const Tuning &tune, cudaStream_t s);
 Tuning get_tuning(int precision, int order);

@@ -42,7 +42,8 @@ EXPORTED = [
     "qqmc_shift_words", "qqmc_sobol_points", "qqmc_warp_points", "qqmc_integrand", "qqmc_server_create",
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
     "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola", "qqmc_set_projection",
-    "qqmc_learn_projection", "qqmc_set_current_tables", "qqmc_problem_current_tables",
+    "qqmc_learn_projection", "qqmc_set_current_tables", "qqmc_problem_current_tables", "qqmc_set_lattice",
+    "qqmc_lattice_cbc",
 ]
 
 
@@ -130,6 +131,8 @@ def load(path: str = LIB_PATH):
         "qqmc_learn_projection": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_int, dp],
         "qqmc_set_current_tables": [vp, dp, dp, ctypes.c_double, ctypes.c_double],
+        "qqmc_set_lattice": [vp, ctypes.c_int, u32p, ctypes.c_int],
+        "qqmc_lattice_cbc": [ctypes.c_int, ctypes.c_int, dp, u32p],
         "qqmc_problem_current_tables": [vp, dp, dp, dp],
     }
     for name, args in sig.items():
@@ -199,6 +202,24 @@ def qqmc_set_current_tables(pr: int, c_lesser: np.ndarray, c_greater: np.ndarray
         raise ValueError("dot-lead tables must have the problem's n_table entries")
     _check(load().qqmc_set_current_tables(ctypes.c_void_p(pr), _ptr(cl, ctypes.c_double), _ptr(cg, ctypes.c_double),
                                           float(np.real(c0)), float(np.imag(c0))), "qqmc_set_current_tables")
+
+
+def qqmc_set_lattice(pr: int, log2_n: int, z: np.ndarray | None) -> None:
+    """Rank-1 lattice of 2^log2_n points with generating vector z (None: back to Sobol')."""
+    if z is None:
+        _check(load().qqmc_set_lattice(ctypes.c_void_p(pr), 0, None, 0), "qqmc_set_lattice")
+        return
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.uint32))
+    _check(load().qqmc_set_lattice(ctypes.c_void_p(pr), log2_n, _ptr(zz, ctypes.c_uint32), zz.size),
+           "qqmc_set_lattice")
+
+
+def qqmc_lattice_cbc(log2_n: int, dims: int, gamma) -> np.ndarray:
+    g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64)[:dims])
+    z = np.zeros(dims, dtype=np.uint32)
+    _check(load().qqmc_lattice_cbc(log2_n, dims, _ptr(g, ctypes.c_double), _ptr(z, ctypes.c_uint32)),
+           "qqmc_lattice_cbc")
+    return z
 
 
 def qqmc_problem_current_tables(pr: int, L: int):
