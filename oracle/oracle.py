@@ -349,12 +349,14 @@ def sobol_points(n: int, i0: int, count: int, V: np.ndarray) -> np.ndarray:
 
 
 def _family(n: int, V, lattice):
-    """(generator words, log2 N): Sobol' direction numbers V [n, 32] with m = 0, or a rank-1
-    lattice given as (z [>= n], m) for N = 2^m points."""
+    """(generator words, family code): Sobol' direction numbers V [n, 32] with code 0, or a rank-1
+    lattice given as (z [>= n], m) or (z, m, tent) for N = 2^m points: code m, or 64 + m when the
+    baker's transform follows the shift."""
     if lattice is None:
         return np.ascontiguousarray(V[:n], dtype=np.uint32), 0
-    z, m = lattice
-    return np.ascontiguousarray(np.asarray(z, dtype=np.uint32)[:n]), int(m)
+    z, m = lattice[0], int(lattice[1])
+    tent = len(lattice) > 2 and bool(lattice[2])
+    return np.ascontiguousarray(np.asarray(z, dtype=np.uint32)[:n]), m + (64 if tent else 0)
 
 
 def warp(n: int, i0: int, count: int, V: np.ndarray, shift: np.ndarray, t: float, tau: float, lattice=None):
@@ -369,9 +371,11 @@ def warp(n: int, i0: int, count: int, V: np.ndarray, shift: np.ndarray, t: float
     return u, w, ins.astype(bool)
 
 
-def lattice_points(n: int, i0: int, count: int, z: np.ndarray, m: int, shift: np.ndarray) -> np.ndarray:
-    """Shifted rank-1 lattice words uint32 [count, n]: ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32."""
-    Vc, lm = _family(n, None, (z, m))
+def lattice_points(n: int, i0: int, count: int, z: np.ndarray, m: int, shift: np.ndarray,
+                   tent: bool = False) -> np.ndarray:
+    """Shifted rank-1 lattice words uint32 [count, n]: ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32,
+    then the baker's transform if tent."""
+    Vc, lm = _family(n, None, (z, m, tent))
     S = np.ascontiguousarray(np.asarray(shift, dtype=np.uint32)[:n])
     out = np.zeros((count, n), dtype=np.uint32)
     if lib().oracle_points(n, i0, count, _u32p(Vc), _u32p(S), lm, _u32p(out)) != 0:

@@ -23,7 +23,10 @@
  *   - Or a rank-1 lattice with N = 2^m points and a random shift (the lattice
  *     rules the paper cites as the alternative low-discrepancy family):
  *     x_i = frac(i z / N + Delta), held as 32-bit fixed point, so the point
- *     word is ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32.
+ *     word is ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32; optionally followed
+ *     by the baker's (tent) transform x -> 1 - |2x - 1| (Hickernell 2002), which
+ *     keeps the uniform measure and lets lattice rules integrate non-periodic
+ *     functions at their higher rate.
  *
  * The determinant of every Keldysh configuration is formed independently by
  * LU factorisation with partial pivoting; there is no reuse between
@@ -231,19 +234,37 @@ int oracle_sobol(int n, int64_t i0, int64_t count, const uint32_t *V, uint32_t *
     return 0;
 }
 
+/* Point-family code: 0 = Sobol', m = lattice of 2^m points, 64 + m = the same followed by the tent map. */
+static int bad_family(int code) { return code < 0 || (code > 32 && (code < 65 || code > 96)); }
+
+/* Baker's transform on a 32-bit fixed-point word: x' = 2x below 1/2, 2 - 2x
+ * above (the single word 2^31, which would give exactly 1, is kept at 1 - 2^-32). */
+static uint32_t tent_word(uint32_t w) {
+    if (w < 0x80000000u) return w << 1;
+    uint64_t v = (1ull << 33) - 2ull * (uint64_t)w;
+    return v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;
+}
+
 /* Shifted point words of index i: Sobol' (digital shift, XOR) when lattice_m
  * == 0, else the rank-1 lattice with generating vector V[0..n-1] and N = 2^m
- * (shift added modulo 2^32). */
+ * (shift added modulo 2^32); lattice_m + 64 selects the lattice followed by
+ * the baker's transform. */
 static void point_words(int n, int64_t i, const uint32_t *V, const uint32_t *S, int lattice_m, uint32_t *X) {
+    int tent = 0;
+    if (lattice_m >= 64) {
+        tent = 1;
+        lattice_m -= 64;
+    }
     if (lattice_m == 0) {
         oracle_sobol(n, i, 1, V, X);
         for (int d = 0; d < n; ++d) X[d] ^= S[d];
         return;
     }
-    uint64_t mask = (lattice_m >= 64) ? ~0ull : ((1ull << lattice_m) - 1ull);
+    uint64_t mask = (1ull << lattice_m) - 1ull;
     for (int d = 0; d < n; ++d) {
         uint64_t r = ((uint64_t)i * (uint64_t)V[d]) & mask;
         X[d] = (uint32_t)((r << (32 - lattice_m)) + (uint64_t)S[d]);
+        if (tent) X[d] = tent_word(X[d]);
     }
 }
 
@@ -262,7 +283,7 @@ int oracle_estimate(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint
                     double t, double tau, const double *gl, const double *gg, int L,
                     double T, double gl0_re, double gl0_im, double *result, int64_t *n_in, double alpha,
                     const double *col, int lattice_m) {
-    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || lattice_m < 0 || lattice_m > 32) return -1;
+    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || bad_family(lattice_m)) return -1;
     gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
     int64_t inside = 0;
@@ -303,7 +324,7 @@ int oracle_estimate(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint
 int oracle_warp(int n, int64_t i0, int64_t count, const uint32_t *V, const uint32_t *S,
                 double t, double tau, double *u_out, double *w_out, int32_t *inside, int lattice_m) {
     uint32_t X[ORACLE_MAX_ORDER];
-    if (lattice_m < 0 || lattice_m > 32) return -1;
+    if (bad_family(lattice_m)) return -1;
     for (int64_t q = 0; q < count; ++q) {
         point_words(n, i0 + q, V, S, lattice_m, X);
         double uprev = t, vsum = 0.0;
@@ -323,7 +344,7 @@ int oracle_warp(int n, int64_t i0, int64_t count, const uint32_t *V, const uint3
 /* Shifted point words (count x n) of either point family; for the pins. */
 int oracle_points(int n, int64_t i0, int64_t count, const uint32_t *V, const uint32_t *S, int lattice_m,
                   uint32_t *out) {
-    if (n < 1 || n > ORACLE_MAX_ORDER || lattice_m < 0 || lattice_m > 32) return -1;
+    if (n < 1 || n > ORACLE_MAX_ORDER || bad_family(lattice_m)) return -1;
     for (int64_t q = 0; q < count; ++q) point_words(n, i0 + q, V, S, lattice_m, out + q * n);
     return 0;
 }
@@ -369,7 +390,7 @@ int oracle_estimate_proj(int n, int64_t i0, int64_t i1, const uint32_t *V, const
                          double tau, const double *cdf, int cells, const double *gl, const double *gg, int L,
                          double T, double gl0_re, double gl0_im, double *result, int64_t *n_in,
                          double alpha, const double *col, int lattice_m) {
-    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || cells < 1 || lattice_m < 0 || lattice_m > 32) return -1;
+    if (n < 1 || n > ORACLE_MAX_ORDER || L < 2 || cells < 1 || bad_family(lattice_m)) return -1;
     gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0;
     int64_t inside = 0;
