@@ -291,7 +291,7 @@ def run_ours(args, ws, rank, local, pg):
 # tuned flat depth: two here), from a 1-pass ncu capture of this exact command
 # (profiles/detsum_*_plain-dot_n1-10.md); per step, like the achieved rate.
 # Set to None whenever the determinant kernel changes until it is captured again.
-MEASURED_LAUNCH_TRAFFIC = {"fp64": 649.98e3 + 1.59e6 + 35.33e3, "mixed": 365.06e3 + 85.25e3 + 495.62e3}
+MEASURED_LAUNCH_TRAFFIC = {"fp64": None, "mixed": None}
 
 
 def _launch_traffic(args, slice_n):
@@ -453,6 +453,49 @@ def run_current(args, local):
             "per_order": {r.order: {"I": r.q_mean, "err": r.q_err, "in_domain": r.n_in_domain} for r, _ in res}}
 
 
+def run_orders(args, local):
+    """Integrand evals/s and Keldysh-det evals/s at each order n (the benchmark's per-order metric):
+    one single-order plan per n on the paper's long-time dot (Gamma=1, eps_d=0, t=30, tau=0.95, L=4096:
+    nearly every point in the domain up to n ~ 20), K = 16 shifts, N a power of two budgeted from the
+    algorithmic cost to ~0.3 s, the kernel time of the second launch."""
+    import torch
+
+    from paper_2002_12372_gb300 import perf
+
+    Q = _setup(args, local)
+    prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
+    if args.stack_min_order:
+        Q.qqmc_set_stack_policy(prec, args.stack_min_order)
+    pr = Q.qqmc_create_problem(Q.make_params(GAMMA, 0.0, 30.0, 0.95, L_TABLE, SEED))
+    stream = torch.cuda.Stream()
+    rows = {}
+    rate = 0.7e12 if prec == Q.QQMC_PREC_FP64 else 15e12
+    for n in range(1, args.orders_max + 1):
+        f = Q.qqmc_get_tuning(prec, n)[1]
+        f = f if f >= 2 else n - 1
+        want = 0.3 * rate / perf.flops_per_point(n, f) / 16
+        N = int(2 ** max(6, min(22, math.floor(math.log2(max(want, 1.0))))))
+        plan = Q.Plan([(pr, n, 16, N)], prec)
+        plan.launch(stream.cuda_stream)
+        plan.results()
+        plan.launch(stream.cuda_stream)
+        (r, _S), = plan.results()
+        km = plan.timing()[0]
+        plan.close()
+        secs = km / 1e3
+        rows[n] = {"N": N, "shifts": 16, "kernel_ms": km, "evals_per_s": N * 16 / secs,
+                   "in_domain_evals_per_s": r.n_in_domain / secs,
+                   "keldysh_det_evals_per_s": r.n_in_domain * 2.0 ** n / secs,
+                   "tflops": r.n_in_domain * perf.flops_per_point(n, f) / secs / 1e12, "flat": f}
+    Q.qqmc_destroy_problem(pr)
+    return {"metric": "per_order_integrand_evals_per_s", "value": rows[min(10, args.orders_max)]["evals_per_s"],
+            "unit": "evals/s at order 10", "n_gpus": 1, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "plain dot Gamma=1, eps_d=0, t=30, tau=0.95, L=4096, one plan per order, 16 shifts",
+                       "precision": args.precision, "stack_min_order": args.stack_min_order or "default"},
+            "per_order": rows}
+
+
 def run_lattice(args, local):
     """Sobol' against a rank-1 lattice (component-by-component vector, product weights 0.9^d) on the
     plain dot at equal point counts: per order the estimate, its shift error bar, and the time."""
@@ -467,10 +510,10 @@ def run_lattice(args, local):
     z = Q.qqmc_lattice_cbc(m, max(orders), gamma)
     stream = torch.cuda.Stream()
     rows = {}
-    for family in ("sobol", "lattice"):
+    for family in ("sobol", "lattice", "lattice_bakers"):
         pr = Q.qqmc_create_problem(Q.make_params(GAMMA, 0.0, T_MAX, TAU, L_TABLE, SEED))
-        if family == "lattice":
-            Q.qqmc_set_lattice(pr, m, z)
+        if family != "sobol":
+            Q.qqmc_set_lattice(pr, m, z, family == "lattice_bakers")
         plan = Q.Plan([(pr, n, K, 1 << m) for n in orders], prec)
         plan.launch(stream.cuda_stream)
         res = plan.results()
@@ -480,9 +523,9 @@ def run_lattice(args, local):
         for r, _ in res:
             rows.setdefault(r.order, {})[family] = {"q": r.q_mean, "err": r.q_err}
         rows.setdefault("kernel_ms", {})[family] = ms
-    ratios = [rows[n]["sobol"]["err"] / rows[n]["lattice"]["err"] for n in orders]
+    ratios = [rows[n]["sobol"]["err"] / rows[n]["lattice_bakers"]["err"] for n in orders]
     return {"metric": "lattice_vs_sobol_error_ratio", "value": float(np.exp(np.mean(np.log(ratios)))),
-            "unit": "geometric mean of err(Sobol')/err(lattice)", "n_gpus": 1,
+            "unit": "geometric mean of err(Sobol')/err(lattice with baker's transform)", "n_gpus": 1,
             "config": {"workload": "plain dot Gamma=1, eps_d=0, t=10, tau=1, L=4096, orders %s, N=2^%d x %d shifts"
                                    % (list(orders), m, K), "precision": args.precision,
                        "lattice": "CBC, product weights 0.9^d, z=%s" % list(map(int, z))},
@@ -600,13 +643,16 @@ def main():
                     help="autotuner table (JSON keyed by GPU name); built-in defaults when absent")
     ap.add_argument("--slice-log2", type=int, default=16,
                     help="Sobol' indices per shift in one step (16: the benchmark batch; smaller for profiling)")
-    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving", "current", "lattice"],
+    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving", "current", "lattice", "orders"],
                     default="plain",
                     help="plain: the benchmark workload; the others print their own study line")
     ap.add_argument("--precision-log2", type=int, default=22)
     ap.add_argument("--current-log2", type=int, default=16)
     ap.add_argument("--current-table", type=int, default=16384)
     ap.add_argument("--lattice-log2", type=int, default=16)
+    ap.add_argument("--orders-max", type=int, default=22)
+    ap.add_argument("--stack-min-order", type=int, default=0,
+                    help="orders: split tree stack from this order on (0: library default)")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-log2-min", type=int, default=16)
@@ -615,7 +661,7 @@ def main():
     if args.config != "plain":
         local = int(os.environ.get("LOCAL_RANK", "0"))
         fn = {"batched": run_batched, "precision": run_precision, "serving": run_serving,
-              "current": run_current, "lattice": run_lattice}[args.config]
+              "current": run_current, "lattice": run_lattice, "orders": run_orders}[args.config]
         print(json.dumps(fn(args, local)), flush=True)
         return
     ws, rank, local, pg = _dist()

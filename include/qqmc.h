@@ -155,9 +155,24 @@ int qqmc_problem_tables(const qqmc_problem *pr, double *g_lesser, double *g_grea
  * shift words S (caller or seed, as for Sobol') added instead of XORed.
  * Every later integration on the problem uses the lattice; items must stay
  * inside it (order <= dims, first_index + n_points <= N; E_INVAL otherwise).
+ * bakers != 0 applies the baker's (tent) transform x -> 1 - |2x - 1| after the
+ * shift (measure preserving; lets the lattice integrate non-periodic
+ * integrands at its higher rate; the word 2^31 maps to 1 - 2^-32).
  * z = NULL restores Sobol'.  Errors: E_INVAL, E_NOMEM, E_CUDA.
  */
-int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims);
+int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims, int bakers);
+
+/*
+ * Where the Schur-tree stack of the determinant kernel lives: from order
+ * min_order on (per precision) its wide top levels (matrices of more than 20
+ * rows) move from shared memory to a per-warp slice of device memory
+ * allocated with each plan, so that high orders keep more warps per SM.
+ * Orders whose stack does not fit in shared memory at all (FP64 from 21)
+ * always split it.  min_order > QQMC_MAX_ORDER: only those; min_order <= 0:
+ * the built-in default (13 in both precisions).  Process-wide; set before
+ * creating plans.  Errors: E_INVAL.
+ */
+int qqmc_set_stack_policy(int precision, int min_order);
 
 /*
  * Component-by-component construction of a generating vector for N = 2^log2_n

@@ -222,7 +222,14 @@ extern "C" int qqmc_set_current_tables(qqmc_problem *pr, const double *cl, const
     return QQMC_OK;
 }
 
-extern "C" int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims) {
+extern "C" int qqmc_set_stack_policy(int precision, int min_order) {
+    if (precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED)
+        return set_error(QQMC_E_INVAL, "precision must be QQMC_PREC_FP64 or QQMC_PREC_MIXED");
+    set_stack_policy(precision, min_order);
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims, int bakers) {
     if (!pr) return set_error(QQMC_E_INVAL, "problem is NULL");
     if (!z) {  // back to Sobol'
         cudaFree(pr->d_lat_z);
@@ -243,7 +250,7 @@ extern "C" int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z,
     }
     cudaError_t e = cudaMemcpy(pr->d_lat_z, z, sizeof(uint32_t) * dims, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_error(e, "lattice upload");
-    pr->lat_m = log2_n;
+    pr->lat_m = log2_n + (bakers ? 64 : 0);
     pr->lat_dims = dims;
     return QQMC_OK;
 }
@@ -368,7 +375,7 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         if (it.n_shifts < 1 || it.n_shifts > 1024) return set_error(QQMC_E_INVAL, "n_shifts must be in 1..1024");
         if (it.first_index > (1ull << 40)) return set_error(QQMC_E_INVAL, "first_index too large");
         const Problem *P = it.problem;
-        if (P->d_lat_z && (it.order > P->lat_dims || it.first_index + it.n_points > (1ull << P->lat_m)))
+        if (P->d_lat_z && (it.order > P->lat_dims || it.first_index + it.n_points > (1ull << (P->lat_m & 63))))
             return set_error(QQMC_E_INVAL, "item outside its problem's lattice (order > its dimension or index >= N)");
     }
     int rc = ensure_device();
@@ -379,11 +386,22 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     pl->items.assign(items, items + n_items);
     pl->precision = precision;
     size_t shift_words_total = 0, chunk_total = 0;
+    // High orders with few points: each point's Keldysh tree is cut into 2^split subtrees, each a
+    // separate work unit, until the item has about kTargetUnits units (the grid needs work for every
+    // warp; the points alone would leave most of it idle).  The split depends on the item alone.
+    constexpr long long kTargetUnits = 1 << 14;
+    auto split_of = [&](const qqmc_item &it) {
+        const int levels = it.order - 1 > 5 ? it.order - 1 - 5 : 0;  // depth-first levels above the tree leaf
+        const long long units = (long long)((it.n_points + kChunk - 1) / kChunk) * it.n_shifts;
+        int sp = 0;
+        while (sp < levels && (units << sp) < kTargetUnits) ++sp;
+        return sp;
+    };
     for (int i = 0; i < n_items; ++i) {
         const qqmc_item &it = items[i];
         pl->n_max = it.order > pl->n_max ? it.order : pl->n_max;
         shift_words_total += (size_t)it.n_shifts * it.order;
-        size_t cps = (it.n_points + kChunk - 1) / kChunk;
+        size_t cps = ((it.n_points + kChunk - 1) / kChunk) << split_of(it);
         chunk_total += cps * it.n_shifts;
         pl->total_shifts += it.n_shifts;
     }
@@ -443,7 +461,9 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         d.table = pr->d_table;
         d.table32 = pr->d_table32;
         d.shifts = pl->d_shifts + so;
-        size_t cps = (it.n_points + kChunk - 1) / kChunk;
+        const int split = lm ? 0 : split_of(it);
+        size_t cps = ((it.n_points + kChunk - 1) / kChunk) << split;  // work units per shift
+        d.split = split;
         d.partials = pl->d_partials + 4 * co;
         d.inside = pl->d_inside + co;
         d.g0_re = pr->g0_re;
@@ -675,12 +695,19 @@ extern "C" int qqmc_plan_chunk_sums(const qqmc_plan *pl, int item, int shift, co
     if (shift < 0 || shift >= d.n_shifts) return set_error(QQMC_E_INVAL, "qqmc_plan_chunk_sums: bad shift");
     cudaError_t e = cudaEventSynchronize(pl->ev1);
     if (e != cudaSuccess) return cuda_error(e, "plan execution");
+    const int nsub = 1 << d.split;  // a chunk's sum is split over its subtrees' work units
+    std::vector<double> buf(4 * (size_t)nsub);
     for (int i = 0; i < count; ++i) {
-        if (chunk[i] < 0 || chunk[i] >= d.chunks_per_shift)
+        if (chunk[i] < 0 || chunk[i] >= (int64_t)(d.chunks_per_shift >> d.split))
             return set_error(QQMC_E_INVAL, "qqmc_plan_chunk_sums: chunk index out of range");
-        const double *src = d.partials + 4 * ((size_t)shift * d.chunks_per_shift + (size_t)chunk[i]);
-        e = cudaMemcpy(out + 4 * i, src, 4 * sizeof(double), cudaMemcpyDeviceToHost);
+        const double *src = d.partials + 4 * ((size_t)shift * d.chunks_per_shift + (size_t)chunk[i] * nsub);
+        e = cudaMemcpy(buf.data(), src, 4 * sizeof(double) * nsub, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_error(e, "chunk download");
+        for (int c = 0; c < 4; ++c) {
+            double acc = 0.0;
+            for (int j = 0; j < nsub; ++j) acc += buf[4 * j + c];
+            out[4 * i + c] = acc;
+        }
     }
     return QQMC_OK;
 }
@@ -781,7 +808,7 @@ extern "C" int qqmc_warp_points(const qqmc_problem *pr, int order, uint64_t firs
         e = d_shift.alloc(order);
         if (e == cudaSuccess) e = cudaMemcpy(d_shift.p, shift, sizeof(uint32_t) * order, cudaMemcpyHostToDevice);
     }
-    if (pr->d_lat_z && (order > pr->lat_dims || first + count > (1ull << pr->lat_m)))
+    if (pr->d_lat_z && (order > pr->lat_dims || first + count > (1ull << (pr->lat_m & 63))))
         return set_error(QQMC_E_INVAL, "points outside the problem's lattice (order > its dimension or index >= N)");
     if (e == cudaSuccess)
         e = launch_warp(order, first, count, shift ? d_shift.p : nullptr, pr->params.t_max, pr->params.tau, d_u.p,

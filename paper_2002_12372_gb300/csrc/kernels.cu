@@ -148,12 +148,20 @@ __device__ __forceinline__ uint32_t sobol_word(int d, uint64_t i) {
 }
 
 // Shifted point word of dimension d for index i: Sobol' with a digital shift
-// (XOR), or a rank-1 lattice of 2^lat_m points, x = frac(i z / N + Delta) in
-// 32-bit fixed point: ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32.
+// (XOR), or a rank-1 lattice of 2^m points, x = frac(i z / N + Delta) in 32-bit
+// fixed point: ((i z_d mod 2^m) << (32 - m)) + S_d mod 2^32, optionally
+// followed by the baker's transform x -> 1 - |2x - 1| (the word 2^31, which
+// would map to exactly 1, stays at 1 - 2^-32).  lat_m: m, or 64 + m with the
+// transform.
 __device__ __forceinline__ uint32_t point_word(const uint32_t *lat_z, int lat_m, int d, uint64_t i, uint32_t s) {
     if (lat_z) {
-        const uint64_t r = (i * (uint64_t)lat_z[d]) & ((lat_m >= 64 ? 0ull : (1ull << lat_m)) - 1ull);
-        return (uint32_t)(r << (32 - lat_m)) + s;
+        const int m = lat_m & 63;
+        const uint64_t r = (i * (uint64_t)lat_z[d]) & ((1ull << m) - 1ull);
+        const uint32_t w = (uint32_t)(r << (32 - m)) + s;
+        if (lat_m < 64) return w;
+        if (w < 0x80000000u) return w << 1;
+        const uint64_t v = (1ull << 33) - 2ull * (uint64_t)w;
+        return v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;
     }
     return sobol_word(d, i) ^ s;
 }
@@ -221,7 +229,8 @@ constexpr int kTreeLeaf = 5;
 
 template <class R>
 struct WarpSmem {
-    cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l
+    cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l (shared memory)
+    cx<R> *gstack;  // split stack: the levels wider than kSmemLevel in device memory, or null
     cx<R> *wrow;    // scaled pivot row(s): <= max(2 n_max, 64) entries
     cx<R> *P;       // P[j*(n_max+1)+k] = g^>(u_j - u_k), j < k; P[k*(n_max+1)] = column entry (k, a_k=1)
     cx<R> *Rr;      // Rr[...]          = g^<(u_j - u_k);      Rr[k*(n_max+1)] = column entry (k, a_k=0)
@@ -251,6 +260,21 @@ __host__ __device__ inline size_t stack_entries(int n_max) {
     return tot;
 }
 
+// With the split stack the tree levels wider than kSmemLevel (the few top
+// levels, built 2, 4, 8 ... times per point) live in device memory and the
+// narrow, hot bottom levels stay in shared memory.
+constexpr int kSmemLevel = 20;
+__host__ __device__ inline size_t stack_entries_split(int n_max, bool global_part) {
+    size_t tot = 0;
+    int R0 = n_max - 1;
+    int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
+    for (int l = 0; l <= levels; ++l) {
+        size_t S = 2 * (size_t)(R0 - l) + 2;
+        if ((S > kSmemLevel) == global_part) tot += S * S;
+    }
+    return tot;
+}
+
 // entries of the breadth-first levels below a tree leaf of Rleaf vertices
 __host__ __device__ inline size_t bfs_entries(int Rleaf, int RF) {
     size_t tot = 0;
@@ -271,13 +295,15 @@ __host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
     return m;
 }
 
-// Shared memory of one warp; with a global stack (gs) the Schur-tree levels
-// live in a per-warp slice of device memory instead (FP64 orders >= 21, whose
-// stack alone exceeds the 227 KB a block can address).
+// Shared memory of one warp; with the split stack (gs) the wide top levels of
+// the Schur tree live in a per-warp slice of device memory (FP64 orders >= 21,
+// whose whole stack exceeds the 227 KB a block can address, and the orders the
+// stack policy names).
 template <class R>
 __host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF, bool gs = false) {
     size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
-    size_t c = (gs ? 0 : stack_entries(n_max)) + 2 * (size_t)(n_max + 1) * (n_max + 1) + n_max + 1 +
+    size_t c = (gs ? stack_entries_split(n_max, false) : stack_entries(n_max)) + 2 * (size_t)(n_max + 1) * (n_max + 1) +
+               n_max + 1 +
                bfs_max_entries(n_max, RF) + wide;
     size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
     bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
@@ -288,12 +314,9 @@ template <class R>
 __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack = nullptr) {
     WarpSmem<R> w;
     cx<R> *p = reinterpret_cast<cx<R> *>(base);
-    if (gstack) {
-        w.stack = gstack;
-    } else {
-        w.stack = p;
-        p += stack_entries(n_max);
-    }
+    w.gstack = gstack;
+    w.stack = p;
+    p += gstack ? stack_entries_split(n_max, false) : stack_entries(n_max);
     w.P = p;
     p += (n_max + 1) * (n_max + 1);
     w.Rr = p;
@@ -314,6 +337,18 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
     w.upt = reinterpret_cast<double *>(base + off);
     return w;
+}
+
+// Leaf term after the last vertex p: with pivot pv and the copies' entries,
+//   det' = det pv,   S_aa = m_aa - m_ap m_pa / pv   (a = copy 0, 1),
+//   det'^2 (S_00 - S_11) = det^2 pv (pv (m_00 - m_11) - (m_0p m_p0 - m_1p m_p1)):
+// the last elimination needs no reciprocal.
+template <class R>
+__device__ __forceinline__ cx<R> leaf_term(cx<R> m00, cx<R> m11, cx<R> m0p, cx<R> mp0, cx<R> m1p, cx<R> mp1, cx<R> pv,
+                                           cx<R> det) {
+    const cx<R> q = cfms(cmul(m0p, mp0), m1p, mp1);                        // m0p mp0 - m1p mp1
+    const cx<R> r = cfms(q, pv, mk<R>(m00.re - m11.re, m00.im - m11.im));  // q - pv (m00 - m11)
+    return cmul(cmul(det, det), cmul(pv, mk<R>(-r.re, -r.im)));
 }
 
 // Flat phase: one lane resolves the F remaining vertices of node matrix E
@@ -358,7 +393,7 @@ __device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parit
         }
     }
 #pragma unroll
-    for (int q = 1; q < F; ++q) {
+    for (int q = 1; q < F - 1; ++q) {
         const int p = q + 1;
         cx<R> pv = m[p][p];
         detD = cmul(detD, pv);
@@ -377,9 +412,12 @@ __device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parit
             }
         }
     }
-    cx<R> dd = cmul(detD, detD);
-    cx<R> diff = mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im);
-    cx<R> term = cmul(dd, diff);
+    cx<R> term;
+    if constexpr (F >= 2) {  // the last vertex is eliminated inside the leaf term
+        term = leaf_term(m[0][0], m[1][1], m[0][M - 1], m[M - 1][0], m[1][M - 1], m[M - 1][1], m[M - 1][M - 1], detD);
+    } else {  // F = 1: the gather step eliminated the only vertex
+        term = cmul(cmul(detD, detD), mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im));
+    }
     parity ^= __popc(path) & 1;
     if (parity) term = mk<R>(-term.re, -term.im);
     acc_re.add(term.re);
@@ -504,10 +542,12 @@ __device__ __forceinline__ double warp_total(Acc<R> acc) {
 // Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
 // Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
-template <class R, int RFMAX>
+// The depth-first walk covers the subtree `sub` of 2^split: the first `split`
+// tree levels follow the bits of sub (split <= levels); split = 0: whole tree.
+template <class R, int RFMAX, bool GS>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
-                                  double s0, int L, int RF, int lane) {
+                                  double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
     const int NP = n_max + 1;
     // 1. pair interpolation, 0 <= j < k <= n
     const int npairs = n * (n + 1) / 2;
@@ -535,6 +575,25 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     // right = M(vertex 1, .) / d.
     const int R0 = n - 1;
     const int S0 = 2 * R0 + 2;
+    // tree levels: offsets in shared memory, or (split stack) in device memory for the wide ones
+    const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
+    int off[kMaxOrder];
+    int lg = 0;  // levels [0, lg) in device memory
+    {
+        int o = 0, og = 0;
+        for (int l = 0; l <= levels; ++l) {
+            const int S = 2 * (R0 - l) + 2;
+            if (GS && S > kSmemLevel) {
+                off[l] = og;
+                og += S * S;
+                lg = l + 1;
+            } else {
+                off[l] = o;
+                o += S * S;
+            }
+        }
+    }
+    auto level = [&](int l) -> cx<R> * { return (GS && l < lg) ? ws.gstack + off[l] : ws.stack + off[l]; };
     const cx<R> id = crcp(dv);  // pivot of vertex 1
     {
         // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
@@ -580,7 +639,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
                 base[0][0] = base[0][1] = nconj(ws.Rr[j * NP + i]);
                 base[1][0] = base[1][1] = nconj(ws.P[j * NP + i]);
             }
-            cx<R> *o = ws.stack + (2 * bx) * S0 + 2 * by;
+            cx<R> *o = level(0) + (2 * bx) * S0 + 2 * by;
 #pragma unroll
             for (int x = 0; x < 2; ++x)
 #pragma unroll
@@ -590,40 +649,31 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     if (lane == 0) ws.detD[0] = dv;
     __syncwarp();
     // 3. depth-first tree over a_2 .. a_{levels+1}
-    const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
     const int Rleaf = R0 - levels;
     const int B = Rleaf > RF ? Rleaf - RF : 0;
     const int Rf = Rleaf - B;
-    int off[kMaxOrder];
-    {
-        int o = 0;
-        for (int l = 0; l <= levels; ++l) {
-            off[l] = o;
-            int S = 2 * (R0 - l) + 2;
-            o += S * S;
-        }
-    }
     Acc<R> ar, ai;
     ar.init();
     ai.init();
-    const int nleaf = 1 << levels;
+    const int nleaf = 1 << (levels - split);
     const int node = lane >> Rf;
     const int path = lane & ((1 << Rf) - 1);
     const bool active = lane < (1 << Rleaf);
-    for (int b = 0; b < nleaf; ++b) {
-        int from = (b == 0) ? 0 : levels - (__ffs(b) - 1) - 1;
+    for (int bl = 0; bl < nleaf; ++bl) {
+        const int b = (sub << (levels - split)) | bl;  // tree path: the subtree's fixed prefix, then bl
+        int from = (bl == 0) ? 0 : levels - (__ffs(b) - 1) - 1;
         for (int l = from; l < levels; ++l) {
             const int a = (b >> (levels - 1 - l)) & 1;
             const int S = 2 * (R0 - l) + 2;
             if (S - 2 <= 32)
-                expand_one<R>(ws.stack + off[l], S, a, ws.stack + off[l + 1], ws.detD + l, ws.detD + l + 1, lane);
+                expand_one<R>(level(l), S, a, level(l + 1), ws.detD + l, ws.detD + l + 1, lane);
             else
-                expand_level<R>(ws.stack + off[l], S, 1, a, ws.stack + off[l + 1], ws.detD + l, ws.detD + l + 1,
-                                ws.wrow, ws.bip, lane);
+                expand_level<R>(level(l), S, 1, a, level(l + 1), ws.detD + l, ws.detD + l + 1, ws.wrow, ws.bip,
+                                lane);
         }
         const int tparity = __popc(b) & 1;
         // 4. breadth-first expansion of B levels below the tree leaf
-        const cx<R> *E = ws.stack + off[levels];
+        const cx<R> *E = level(levels);
         int S = 2 * Rleaf + 2;
         const cx<R> *ndet = ws.detD + levels;
         cx<R> *dbuf = ws.bdet;
@@ -725,7 +775,7 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
             }
         cx<R> detD = dv;
 #pragma unroll
-        for (int p = 2; p < M; ++p) {
+        for (int p = 2; p < M - 1; ++p) {
             cx<R> pv = m[p][p];
             detD = cmul(detD, pv);
             cx<R> iq = crcp(pv);
@@ -743,8 +793,13 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
                 }
             }
         }
-        cx<R> dd = cmul(detD, detD);
-        cx<R> term = cmul(dd, mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im));
+        cx<R> term;
+        if constexpr (M > 2) {
+            term = leaf_term(m[0][0], m[1][1], m[0][M - 1], m[M - 1][0], m[1][M - 1], m[M - 1][1], m[M - 1][M - 1],
+                             detD);
+        } else {  // order 1: vertex 1 was eliminated when the matrix was built
+            term = cmul(cmul(detD, detD), mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im));
+        }
         if (__popc(path) & 1) term = mk<R>(-term.re, -term.im);
         ar.add(term.re);
         ai.add(term.im);
@@ -836,7 +891,7 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     cx<R> *gst = nullptr;
-    if (GS) gst = gstack + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * stack_entries(n_max);
+    if (GS) gst = gstack + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * (stack_entries_split(n_max, true) + 1);
     WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, rf_min, GS), n_max, rf_min, gst);
     const int NU = n_max + 1;
     while (true) {
@@ -850,7 +905,9 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
         const int n = I.order;
         const long long local = (long long)c - I.chunk_begin;
         const int k = (int)(local / I.chunks_per_shift);
-        const long long blk = local - (long long)k * I.chunks_per_shift;
+        const long long unit = local - (long long)k * I.chunks_per_shift;
+        const long long blk = unit >> I.split;                   // chunk of 32 points
+        const int sub = (int)(unit & ((1ll << I.split) - 1));   // subtree of each point's Keldysh tree
         const long long idx = blk * kChunk + lane;
         const bool valid = idx < I.n_points;
         // point generation and warp (Sobol' integers are exact)
@@ -888,8 +945,8 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
             // every warp-per-point item of a launch shares the launch's flat depth
-            cx<double> s = keldysh_sum<R, RFMAX>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, item_col<R>(I), inv_h,
-                                                 s0, I.L, RFMAX, lane);
+            cx<double> s = keldysh_sum<R, RFMAX, GS>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, item_col<R>(I), inv_h,
+                                                     s0, I.L, RFMAX, lane, sub, I.split);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -905,7 +962,7 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             pp[1] = si;
             pp[2] = cr;
             pp[3] = ci;
-            I.inside[local] = __popc(mask);
+            I.inside[local] = sub == 0 ? __popc(mask) : 0u;  // a point counts once, in subtree 0
         }
     }
 }
@@ -1075,7 +1132,7 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     const int warp = threadIdx.x >> 5;
     const uint64_t wid = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
     cx<R> *gst = nullptr;
-    if (GS) gst = gstack + wid * stack_entries(n_max);
+    if (GS) gst = gstack + wid * (stack_entries_split(n_max, true) + 1);
     WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF, GS), n_max, RF, gst);
     const int n = I.order;
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
@@ -1084,7 +1141,7 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     for (uint64_t q = wid; q < count; q += (uint64_t)gridDim.x * (blockDim.x >> 5)) {
         if (lane <= n) ws.upt[lane] = lane == 0 ? I.t : u[q * n + lane - 1];
         __syncwarp();
-        cx<double> s = keldysh_sum<R, RF>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I), inv_h,
+        cx<double> s = keldysh_sum<R, RF, GS>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I), inv_h,
                                           I.T * inv_h, I.L, RF, lane);
         if (lane == 0) {
             cx<double> cval = times_i_pow(s, n);
@@ -1424,10 +1481,22 @@ size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
     return per * tune.warps_per_block;
 }
 
-// The FP64 tree stack moves to device memory when it does not fit in shared memory.
+// The tree stack is split (wide top levels in device memory) where it does not
+// fit in shared memory (FP64 orders >= 21), and from the order set by
+// qqmc_set_stack_policy (default 13, measured faster on GB300 in both
+// precisions): a large shared-memory stack limits the warps per SM, while the
+// wide levels are built only a few times per point.
+constexpr int kGsDefault[2] = {13, 13};
+static int g_gs_min_order[2] = {kGsDefault[0], kGsDefault[1]};
+
+void set_stack_policy(int precision, int min_order) {
+    const int p = precision == QQMC_PREC_FP64 ? 0 : 1;
+    g_gs_min_order[p] = min_order <= 0 ? kGsDefault[p] : min_order;
+}
+
 template <class R>
 static bool stack_in_global(int n_max, int rf_min) {
-    return sizeof(R) == 8 && warp_smem_bytes<R>(n_max, rf_min) > kSmemMax;
+    return warp_smem_bytes<R>(n_max, rf_min) > kSmemMax || n_max >= g_gs_min_order[sizeof(R) == 8 ? 0 : 1];
 }
 
 template <class R, int F, bool GS>
@@ -1465,11 +1534,10 @@ template <class R, int F>
 static cudaError_t launch_detsum_f(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
                                    long long gstack_warps, cudaStream_t s) {
-    if constexpr (sizeof(R) == 8) {
-        if (stack_in_global<R>(n_max, rf_min))
-            return launch_detsum_t<R, F, true>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack,
-                                               gstack_warps, s);
-    }
+    // without a device-memory buffer (the allocation-free entry) the shared-memory stack serves where it fits
+    if (stack_in_global<R>(n_max, rf_min) && (gstack || warp_smem_bytes<R>(n_max, rf_min) > kSmemMax))
+        return launch_detsum_t<R, F, true>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack,
+                                           gstack_warps, s);
     return launch_detsum_t<R, F, false>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, nullptr, 0, s);
 }
 
@@ -1477,17 +1545,30 @@ static int clamp_rf_min(const Tuning &tune) {
     return tune.flat_min < 2 ? 2 : (tune.flat_min > tune.flat ? tune.flat : tune.flat_min);
 }
 
-long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp) {
-    const int rf_min = clamp_rf_min(tune);
+template <class R>
+static long long gstack_warps_t(int n_max, int rf_min, size_t *bytes_per_warp) {
     *bytes_per_warp = 0;
-    if (precision != QQMC_PREC_FP64 || !stack_in_global<double>(n_max, rf_min)) return 0;
+    if (!stack_in_global<R>(n_max, rf_min)) return 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t per_warp = warp_smem_bytes<double>(n_max, rf_min, true);
-    const long long per_sm = (long long)(kSmemMax / per_warp);  // resident warps, bound by shared memory
-    *bytes_per_warp = stack_entries(n_max) * sizeof(cx<double>);
+    const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min, true);
+    long long per_sm = (long long)(kSmemMax / per_warp);  // resident warps, bound by shared memory
+    if (per_sm > 64) per_sm = 64;                          // and by the SM's warp slots
+    *bytes_per_warp = (stack_entries_split(n_max, true) + 1) * sizeof(cx<R>);
     return (long long)sms * (per_sm < 1 ? 1 : per_sm);
+}
+
+bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune) {
+    const int rf_min = clamp_rf_min(tune);
+    return precision == QQMC_PREC_FP64 ? warp_smem_bytes<double>(n_max, rf_min) <= kSmemMax
+                                       : warp_smem_bytes<float>(n_max, rf_min) <= kSmemMax;
+}
+
+long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp) {
+    const int rf_min = clamp_rf_min(tune);
+    return precision == QQMC_PREC_FP64 ? gstack_warps_t<double>(n_max, rf_min, bytes_per_warp)
+                                       : gstack_warps_t<float>(n_max, rf_min, bytes_per_warp);
 }
 
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
@@ -1575,7 +1656,7 @@ static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const
     cx<R> *gstack = nullptr;
     if (GS) {  // check path: a bounded number of warps, each with its own slice of device memory
         if (blocks > 304) blocks = 304;
-        e = cudaMalloc(&gstack, blocks * wpb * stack_entries(item.order) * sizeof(cx<R>));
+        e = cudaMalloc(&gstack, blocks * wpb * (stack_entries_split(item.order, true) + 1) * sizeof(cx<R>));
         if (e != cudaSuccess) return e;
     }
     integrand_kernel<R, F, GS><<<(unsigned)blocks, wpb * 32, smem, s>>>(item, count, d_u, d_out, item.order, gstack);
@@ -1591,9 +1672,7 @@ static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const
 template <class R, int F>
 static cudaError_t launch_integrand_f(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
                                       cudaStream_t s) {
-    if constexpr (sizeof(R) == 8) {
-        if (stack_in_global<R>(item.order, F)) return launch_integrand_t<R, F, true>(item, count, d_u, d_out, s);
-    }
+    if (stack_in_global<R>(item.order, F)) return launch_integrand_t<R, F, true>(item, count, d_u, d_out, s);
     return launch_integrand_t<R, F, false>(item, count, d_u, d_out, s);
 }
 

@@ -105,7 +105,7 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     it.col32 = P->params.observable == QQMC_OBS_CURRENT ? P->d_col32 : nullptr;
     it.lat_z = P->d_lat_z;
     it.lat_m = P->lat_m;
-    if (P->d_lat_z && (order > P->lat_dims || n_points > (1ull << P->lat_m)))
+    if (P->d_lat_z && (order > P->lat_dims || n_points > (1ull << (P->lat_m & 63))))
         return set_error(QQMC_E_INVAL, "points outside the problem's lattice (order > its dimension or index >= N)");
     it.proj = P->d_proj[order];
     it.proj_cells = P->proj_cells[order];
@@ -113,8 +113,7 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     it.flat = tu.flat;
     if (it.flat < 2 && order > 4) it.flat = 2;
     if (tu.flat < 2) tu.flat = tu.flat_min = 2;
-    size_t gs_bytes = 0;
-    if (!(it.flat == 1 && order <= kLaneMaxOrder) && detsum_gstack_warps(order, precision, tu, &gs_bytes) > 0)
+    if (!(it.flat == 1 && order <= kLaneMaxOrder) && !detsum_stack_fits_shared(order, precision, tu))
         return set_error(QQMC_E_INVAL,
                          "qqmc_integrate_noalloc: this order's FP64 tree stack needs device memory; use the mixed "
                          "precision or qqmc_integrate");

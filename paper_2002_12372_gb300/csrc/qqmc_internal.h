@@ -32,7 +32,7 @@ struct Problem {
     double c0_re = 0, c0_im = 0;  // gamma g^<_01(0)
     // rank-1 lattice point set (instead of Sobol'): generating vector and log2 of its size
     uint32_t *d_lat_z = nullptr;
-    int lat_m = 0;
+    int lat_m = 0;       // log2 N, plus 64 when the baker's transform follows the shift
     int lat_dims = 0;
 };
 
@@ -47,7 +47,9 @@ struct ItemDev {
     long long first_index;
     long long n_points;
     long long chunk_begin;   // first global chunk of this item
-    int order, n_shifts, L, chunks_per_shift;
+    int order, n_shifts, L;
+    int chunks_per_shift;    // work units per shift: point chunks << split
+    int split;               // each point's Keldysh tree in 2^split subtrees (separate work units)
     int flat;                // vertices resolved per lane for this item (its order's tuning)
     const double *proj;      // learned warp: [order][proj_cells + 1] CDF per dimension, or null (plain)
     int proj_cells;
@@ -55,7 +57,7 @@ struct ItemDev {
     const dbl4 *col;         // current: dot-lead column table [L/2 + 1] at nodes 0 .. L/2, else null
     const float4 *col32;
     const uint32_t *lat_z;   // rank-1 lattice generating vector, or null (Sobol')
-    int lat_m;               // lattice size 2^lat_m
+    int lat_m;               // lattice size 2^(lat_m & 63); lat_m >= 64: baker's transform
 };
 
 struct Tuning {
@@ -83,6 +85,8 @@ cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_c
 // Warps (and bytes per warp) of device memory the determinant launch needs for
 // its tree stack; 0 when the stack fits in shared memory.
 long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp);
+void set_stack_policy(int precision, int min_order);
+bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune);
 cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                         int precision, cudaStream_t s);
 constexpr int kLaneMaxOrder = 4;  // orders that may run one point per lane

@@ -43,7 +43,7 @@ EXPORTED = [
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
     "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola", "qqmc_set_projection",
     "qqmc_learn_projection", "qqmc_set_current_tables", "qqmc_problem_current_tables", "qqmc_set_lattice",
-    "qqmc_lattice_cbc",
+    "qqmc_lattice_cbc", "qqmc_set_stack_policy",
 ]
 
 
@@ -131,7 +131,8 @@ def load(path: str = LIB_PATH):
         "qqmc_learn_projection": [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_int, dp],
         "qqmc_set_current_tables": [vp, dp, dp, ctypes.c_double, ctypes.c_double],
-        "qqmc_set_lattice": [vp, ctypes.c_int, u32p, ctypes.c_int],
+        "qqmc_set_lattice": [vp, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int],
+        "qqmc_set_stack_policy": [ctypes.c_int, ctypes.c_int],
         "qqmc_lattice_cbc": [ctypes.c_int, ctypes.c_int, dp, u32p],
         "qqmc_problem_current_tables": [vp, dp, dp, dp],
     }
@@ -204,14 +205,20 @@ def qqmc_set_current_tables(pr: int, c_lesser: np.ndarray, c_greater: np.ndarray
                                           float(np.real(c0)), float(np.imag(c0))), "qqmc_set_current_tables")
 
 
-def qqmc_set_lattice(pr: int, log2_n: int, z: np.ndarray | None) -> None:
-    """Rank-1 lattice of 2^log2_n points with generating vector z (None: back to Sobol')."""
+def qqmc_set_lattice(pr: int, log2_n: int, z: np.ndarray | None, bakers: bool = False) -> None:
+    """Rank-1 lattice of 2^log2_n points with generating vector z (None: back to Sobol');
+    bakers: apply the baker's transform after the shift."""
     if z is None:
-        _check(load().qqmc_set_lattice(ctypes.c_void_p(pr), 0, None, 0), "qqmc_set_lattice")
+        _check(load().qqmc_set_lattice(ctypes.c_void_p(pr), 0, None, 0, 0), "qqmc_set_lattice")
         return
     zz = np.ascontiguousarray(np.asarray(z, dtype=np.uint32))
-    _check(load().qqmc_set_lattice(ctypes.c_void_p(pr), log2_n, _ptr(zz, ctypes.c_uint32), zz.size),
+    _check(load().qqmc_set_lattice(ctypes.c_void_p(pr), log2_n, _ptr(zz, ctypes.c_uint32), zz.size, int(bakers)),
            "qqmc_set_lattice")
+
+
+def qqmc_set_stack_policy(precision: int, min_order: int) -> None:
+    """Split tree stack from order min_order (<= 0: built-in default)."""
+    _check(load().qqmc_set_stack_policy(precision, min_order), "qqmc_set_stack_policy")
 
 
 def qqmc_lattice_cbc(log2_n: int, dims: int, gamma) -> np.ndarray:

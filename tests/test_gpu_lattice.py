@@ -33,34 +33,34 @@ def _korobov(a: int, dims: int) -> np.ndarray:
     return np.array([pow(a, d, 1 << M) for d in range(dims)], dtype=np.uint32)
 
 
-def _lattice_problem(Q, W, oracle, seed, T=10.0, L=4096, dims=12):
+def _lattice_problem(Q, W, oracle, seed, T=10.0, L=4096, dims=12, bakers=False):
     gl, gg, g0, _ = W.synthetic_tables(seed, L, T)
     pr = Q.qqmc_create_problem_tables(Q.make_params(t_max=T, n_table=L), gl, gg, g0)
     z = _korobov(17797, dims)
-    Q.qqmc_set_lattice(pr, M, z)
+    Q.qqmc_set_lattice(pr, M, z, bakers)
     return pr, (gl, gg, g0), z
 
 
-@pytest.mark.parametrize("order", [1, 4, 9, 12])
-def test_lattice_warp_points_match_oracle(Q, W, oracle, order):
+@pytest.mark.parametrize("order,bakers", [(1, False), (4, False), (9, False), (12, False), (3, True), (10, True)])
+def test_lattice_warp_points_match_oracle(Q, W, oracle, order, bakers):
     T = 10.0
-    pr, _, z = _lattice_problem(Q, W, oracle, 40 + order, T=T)
+    pr, _, z = _lattice_problem(Q, W, oracle, 40 + order, T=T, bakers=bakers)
     try:
         sh = W.shift_words(41 + order, 1, order)[0]
         u, w, ins = Q.qqmc_warp_points(pr, order, 1000, 20000, sh)
     finally:
         Q.qqmc_destroy_problem(pr)
-    u0, w0, ins0 = oracle.warp(order, 1000, 20000, None, sh, T, 1.0, lattice=(z, M))
+    u0, w0, ins0 = oracle.warp(order, 1000, 20000, None, sh, T, 1.0, lattice=(z, M, bakers))
     assert np.array_equal(ins, ins0)
     assert np.max(np.abs(u - u0)) <= 1e-13 * T
     assert np.max(np.abs(w / w0 - 1.0)) < 1e-13
 
 
-@pytest.mark.parametrize("lane", [False, True])
-def test_lattice_integration_matches_oracle(Q, W, oracle, lane):
+@pytest.mark.parametrize("lane,bakers", [(False, False), (True, False), (False, True)])
+def test_lattice_integration_matches_oracle(Q, W, oracle, lane, bakers):
     from paper_2002_12372_gb300 import autotune
     T, K = 10.0, 3
-    pr, tabs, z = _lattice_problem(Q, W, oracle, 51, T=T)
+    pr, tabs, z = _lattice_problem(Q, W, oracle, 51, T=T, bakers=bakers)
     try:
         for n in range(1, 5):
             Q.qqmc_set_tuning(Q.QQMC_PREC_FP64, n, 2, 1 if lane else 2)
@@ -70,7 +70,7 @@ def test_lattice_integration_matches_oracle(Q, W, oracle, lane):
             plan.launch()
             (res, S), = plan.results()
             plan.close()
-            S0, nin = oracle.estimate(n, N, sw, T, 1.0, tabs, T, i0=first, lattice=(z, M))
+            S0, nin = oracle.estimate(n, N, sw, T, 1.0, tabs, T, i0=first, lattice=(z, M, bakers))
             assert res.n_in_domain == int(nin.sum())
             assert np.all(np.abs(S - S0) <= 1e-10 * np.abs(S0)), (n, S, S0)
     finally:

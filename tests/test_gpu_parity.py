@@ -395,3 +395,29 @@ def test_order_22_plan_equals_its_points(Q, W):
     # cancels to |c| ~ 1e-11 of its terms, so an FP64 c is good to ~1e-4 relative; a bookkeeping
     # error (wrong point, weight or stack slice) would be O(1).
     assert abs(S[0] - ref) <= 1e-3 * np.sum(np.abs(w[ins] * c)) / N
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_split_stack_is_bit_identical(Q, W, precision):
+    """The split tree stack (wide levels in device memory, qqmc_set_stack_policy) runs the same
+    arithmetic as the shared-memory stack: the same per-shift sums bit for bit."""
+    T = 10.0
+    pr, _ = _problem(Q, W, seed=91, T=T)
+    items = [(pr, n, 2, N, W.shift_words(90 + n, 2, n)) for n, N in [(6, 700), (9, 130), (12, 33)]]
+    try:
+        Q.qqmc_set_stack_policy(precision, Q.QQMC_MAX_ORDER + 1)
+        plan = Q.Plan(items, precision)
+        plan.launch()
+        ref = plan.results()
+        plan.close()
+        Q.qqmc_set_stack_policy(precision, 1)
+        plan = Q.Plan(items, precision)
+        plan.launch()
+        out = plan.results()
+        plan.close()
+    finally:
+        Q.qqmc_set_stack_policy(precision, 0)
+        Q.qqmc_destroy_problem(pr)
+    for (r0, S0), (r1, S1) in zip(ref, out):
+        assert r0.n_in_domain == r1.n_in_domain
+        assert np.array_equal(S0, S1)
