@@ -39,13 +39,13 @@ static Tuning g_tune[2][kMaxOrder + 1];
 static bool g_tune_set[2][kMaxOrder + 1];
 
 static Tuning default_tuning(int precision, int order) {
-    (void)order;
     Tuning t;
     // FP64: breadth-first expansion below the tree leaf, 2 vertices per lane
-    // (the FP64 pipe is the bound, so fewer flops win); mixed: 5 vertices per
-    // lane in registers (shared-memory traffic of cooperative updates is the
-    // FP32 bound).
-    t.flat = precision == QQMC_PREC_FP64 ? 2 : 5;
+    // (the FP64 pipe is the bound, so fewer flops win), 3 from order 10 on
+    // (smaller breadth-first buffers: more warps per SM for the deep stacks);
+    // mixed: 5 vertices per lane in registers (shared-memory traffic of
+    // cooperative updates is the FP32 bound).
+    t.flat = precision == QQMC_PREC_FP64 ? (order >= 10 ? 3 : 2) : 5;
     t.flat_min = t.flat;
     t.warps_per_block = precision == QQMC_PREC_FP64 ? 2 : 4;
     return t;
@@ -386,22 +386,40 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     pl->items.assign(items, items + n_items);
     pl->precision = precision;
     size_t shift_words_total = 0, chunk_total = 0;
-    // High orders with few points: each point's Keldysh tree is cut into 2^split subtrees, each a
-    // separate work unit, until the item has about kTargetUnits units (the grid needs work for every
-    // warp; the points alone would leave most of it idle).  The split depends on the item alone.
+    // Work units.  A chunk is 32 consecutive point indices of one shift.  Items with few chunks are
+    // cut finer until an item has about kTargetUnits units (the persistent grid needs work for every
+    // warp; the chunks alone would leave most of it idle):
+    //  1. a chunk's points go to 2^pbits units of 32 >> pbits points each (pbits <= 5), which costs
+    //     nothing but the point generation of the idle lanes;
+    //  2. then each point's Keldysh tree goes to 2^split units, each a subtree with the first `split`
+    //     depth-first levels fixed.  Such a unit repeats the pair interpolation, the first
+    //     elimination and its subtree's fixed prefix, so a subtree keeps at least
+    //     2^kMinSubtreeLevels leaves, which holds that repeated work to a few per cent.
+    // The cut depends on the item alone (batched and single runs agree bit for bit).
     constexpr long long kTargetUnits = 1 << 14;
-    auto split_of = [&](const qqmc_item &it) {
+    constexpr int kMinSubtreeLevels = 4;
+    auto lane_mode = [&](int i) {
+        return items[i].order <= kLaneMaxOrder && get_tuning(precision, items[i].order).flat == 1;
+    };
+    std::vector<char> lmv(n_items);
+    std::vector<int> pbits_of(n_items, 0), split_of(n_items, 0);
+    for (int i = 0; i < n_items; ++i) {
+        const qqmc_item &it = items[i];
+        lmv[i] = lane_mode(i);
+        if (lmv[i]) continue;  // one point per lane: no cut
         const int levels = it.order - 1 > 5 ? it.order - 1 - 5 : 0;  // depth-first levels above the tree leaf
         const long long units = (long long)((it.n_points + kChunk - 1) / kChunk) * it.n_shifts;
-        int sp = 0;
-        while (sp < levels && (units << sp) < kTargetUnits) ++sp;
-        return sp;
-    };
+        int pb = 0, sp = 0;
+        while (pb < 5 && (units << pb) < kTargetUnits) ++pb;
+        while (sp < levels - kMinSubtreeLevels && (units << (pb + sp)) < kTargetUnits) ++sp;
+        pbits_of[i] = pb;
+        split_of[i] = sp;
+    }
     for (int i = 0; i < n_items; ++i) {
         const qqmc_item &it = items[i];
         pl->n_max = it.order > pl->n_max ? it.order : pl->n_max;
         shift_words_total += (size_t)it.n_shifts * it.order;
-        size_t cps = ((it.n_points + kChunk - 1) / kChunk) << split_of(it);
+        size_t cps = ((it.n_points + kChunk - 1) / kChunk) << (pbits_of[i] + split_of[i]);
         chunk_total += cps * it.n_shifts;
         pl->total_shifts += it.n_shifts;
     }
@@ -422,21 +440,18 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     // items (orders <= 4 whose tuning asks for it); within a group highest order
     // first, then more points first, so the longest items start early and the
     // persistent grid drains evenly.  Each launch has its own chunk numbering.
-    auto lane_mode = [&](int i) {
-        return items[i].order <= kLaneMaxOrder && get_tuning(precision, items[i].order).flat == 1;
-    };
     auto flat_of = [&](int i) {
         const int f = get_tuning(precision, items[i].order).flat;
         return f < 2 ? 2 : f;
     };
     int group_top[6] = {0, 0, 0, 0, 0, 0};  // highest order per flat depth 2..5
     for (int i = 0; i < n_items; ++i)
-        if (!lane_mode(i) && items[i].order > group_top[flat_of(i)]) group_top[flat_of(i)] = items[i].order;
+        if (!lmv[i] && items[i].order > group_top[flat_of(i)]) group_top[flat_of(i)] = items[i].order;
     pl->perm.resize(n_items);
     for (int i = 0; i < n_items; ++i) pl->perm[i] = i;
     std::stable_sort(pl->perm.begin(), pl->perm.end(), [&](int a, int b) {
-        if (lane_mode(a) != lane_mode(b)) return !lane_mode(a);
-        if (!lane_mode(a)) {
+        if (lmv[a] != lmv[b]) return !lmv[a];
+        if (!lmv[a]) {
             const int fa = flat_of(a), fb = flat_of(b);
             if (group_top[fa] != group_top[fb]) return group_top[fa] > group_top[fb];
             if (fa != fb) return fa > fb;
@@ -451,7 +466,7 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     for (int q = 0; q < n_items; ++q) {
         const int ci = pl->perm[q];
         const qqmc_item &it = items[ci];
-        const bool lm = lane_mode(ci);
+        const bool lm = lmv[ci];
         const qqmc_problem *pr = it.problem;
         if (it.shift_words)
             memcpy(hs.data() + so, it.shift_words, sizeof(uint32_t) * it.n_shifts * it.order);
@@ -461,9 +476,9 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         d.table = pr->d_table;
         d.table32 = pr->d_table32;
         d.shifts = pl->d_shifts + so;
-        const int split = lm ? 0 : split_of(it);
-        size_t cps = ((it.n_points + kChunk - 1) / kChunk) << split;  // work units per shift
-        d.split = split;
+        d.pbits = pbits_of[ci];
+        d.split = split_of[ci];
+        size_t cps = ((it.n_points + kChunk - 1) / kChunk) << (d.pbits + d.split);  // work units per shift
         d.partials = pl->d_partials + 4 * co;
         d.inside = pl->d_inside + co;
         d.g0_re = pr->g0_re;
@@ -695,10 +710,10 @@ extern "C" int qqmc_plan_chunk_sums(const qqmc_plan *pl, int item, int shift, co
     if (shift < 0 || shift >= d.n_shifts) return set_error(QQMC_E_INVAL, "qqmc_plan_chunk_sums: bad shift");
     cudaError_t e = cudaEventSynchronize(pl->ev1);
     if (e != cudaSuccess) return cuda_error(e, "plan execution");
-    const int nsub = 1 << d.split;  // a chunk's sum is split over its subtrees' work units
+    const int nsub = 1 << (d.pbits + d.split);  // a chunk's sum is split over its work units
     std::vector<double> buf(4 * (size_t)nsub);
     for (int i = 0; i < count; ++i) {
-        if (chunk[i] < 0 || chunk[i] >= (int64_t)(d.chunks_per_shift >> d.split))
+        if (chunk[i] < 0 || chunk[i] >= (int64_t)(d.chunks_per_shift >> (d.pbits + d.split)))
             return set_error(QQMC_E_INVAL, "qqmc_plan_chunk_sums: chunk index out of range");
         const double *src = d.partials + 4 * ((size_t)shift * d.chunks_per_shift + (size_t)chunk[i] * nsub);
         e = cudaMemcpy(buf.data(), src, 4 * sizeof(double) * nsub, cudaMemcpyDeviceToHost);

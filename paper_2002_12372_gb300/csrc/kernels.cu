@@ -230,16 +230,19 @@ constexpr int kTreeLeaf = 5;
 template <class R>
 struct WarpSmem {
     cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l (shared memory)
-    cx<R> *gstack;  // split stack: the levels wider than kSmemLevel in device memory, or null
+    cx<R> *gstack;  // split stack: the levels wider than gs_level in device memory, or null
     cx<R> *wrow;    // scaled pivot row(s): <= max(2 n_max, 64) entries
-    cx<R> *P;       // P[j*(n_max+1)+k] = g^>(u_j - u_k), j < k; P[k*(n_max+1)] = column entry (k, a_k=1)
-    cx<R> *Rr;      // Rr[...]          = g^<(u_j - u_k);      Rr[k*(n_max+1)] = column entry (k, a_k=0)
+    cx<R> *P;       // vertex k's block at o_k = (k-1)(k+2)/2: P[o_k + j] = g^>(u_j - u_k), 0 <= j < k,
+                    // and P[o_k + k] = measurement-column entry (k, a_k = 1)
+    cx<R> *Rr;      // Rr[o_k + j] = g^<(u_j - u_k); Rr[o_k + k] = column entry (k, a_k = 0)
     cx<R> *detD;    // per tree level
     cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
     cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
     cx<R> *bip;     // pivot reciprocal per child of the level being built (32)
-    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t)
+    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t); device memory with the split stack
+    int gs_level;   // split stack: levels with S > gs_level in device memory
 };
+
 
 // wrow, bdet and bip serve the general cooperative expansion: breadth-first
 // levels (flat depth below the tree leaf) and depth-first steps wider than a
@@ -260,17 +263,16 @@ __host__ __device__ inline size_t stack_entries(int n_max) {
     return tot;
 }
 
-// With the split stack the tree levels wider than kSmemLevel (the few top
-// levels, built 2, 4, 8 ... times per point) live in device memory and the
-// narrow, hot bottom levels stay in shared memory.
-constexpr int kSmemLevel = 20;
-__host__ __device__ inline size_t stack_entries_split(int n_max, bool global_part) {
+// With the split stack the tree levels wider than gs_level (the top levels,
+// built 1, 2, 4 ... times per point) live in device memory and the narrow, hot
+// bottom levels stay in shared memory.
+__host__ __device__ inline size_t stack_entries_split(int n_max, bool global_part, int gs_level) {
     size_t tot = 0;
     int R0 = n_max - 1;
     int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
     for (int l = 0; l <= levels; ++l) {
         size_t S = 2 * (size_t)(R0 - l) + 2;
-        if ((S > kSmemLevel) == global_part) tot += S * S;
+        if (((int)S > gs_level) == global_part) tot += S * S;
     }
     return tot;
 }
@@ -295,19 +297,50 @@ __host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
     return m;
 }
 
+// entries of the packed pair values with the measurement column (P and Rr:
+// blocks of k + 1 entries for the vertices k = 1 .. n_max)
+__host__ __device__ inline size_t pair_entries(int n_max) { return (size_t)n_max * (n_max + 3); }
+
+// Shared memory of one warp.  gs_level = 0: the whole tree stack and the point
+// times in shared memory.  gs_level > 0 (split stack): the levels wider than
+// gs_level and the point times in a per-warp slice of device memory.
+template <class R>
+__host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_level) {
+    size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
+    size_t c = (gs_level ? stack_entries_split(n_max, false, gs_level) : stack_entries(n_max)) + pair_entries(n_max) +
+               n_max + 1 + bfs_max_entries(n_max, RF) + wide;
+    size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
+    if (!gs_level) bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
+    return (bytes + 127) & ~(size_t)127;
+}
+
+// Split-stack boundary: the widest levels go to device memory, two rows at a
+// time, until a warp's shared memory lets the SM hold the warps its bound pipe
+// needs (FP64: 6 warps keep GB300's two FP64 lanes per SM busy; mixed: 12).
+// Never the tree leaf (S = 12), which the breadth-first and flat phases read.
+template <class R>
+__host__ __device__ inline int gs_level_of(int n_max, int RF) {
+    const size_t budget = sizeof(R) == 8 ? 36 * 1024 : 18 * 1024;
+    int lev = 20;
+    while (lev > 2 * kTreeLeaf + 2 && warp_smem_bytes_at<R>(n_max, RF, lev) > budget) lev -= 2;
+    return lev;
+}
+
 // Shared memory of one warp; with the split stack (gs) the wide top levels of
 // the Schur tree live in a per-warp slice of device memory (FP64 orders >= 21,
 // whose whole stack exceeds the 227 KB a block can address, and the orders the
 // stack policy names).
 template <class R>
 __host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF, bool gs = false) {
-    size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
-    size_t c = (gs ? stack_entries_split(n_max, false) : stack_entries(n_max)) + 2 * (size_t)(n_max + 1) * (n_max + 1) +
-               n_max + 1 +
-               bfs_max_entries(n_max, RF) + wide;
-    size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
-    bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
-    return (bytes + 127) & ~(size_t)127;
+    return warp_smem_bytes_at<R>(n_max, RF, gs ? gs_level_of<R>(n_max, RF) : 0);
+}
+
+// Device-memory slice of one warp with the split stack: the wide levels, one
+// spare entry, and the point times of the chunk.
+template <class R>
+__host__ __device__ inline size_t gstack_entries(int n_max, int RF) {
+    return stack_entries_split(n_max, true, gs_level_of<R>(n_max, RF)) + 1 +
+           (32 * (size_t)(n_max + 1) * sizeof(double) + sizeof(cx<R>) - 1) / sizeof(cx<R>);
 }
 
 template <class R>
@@ -315,12 +348,14 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     WarpSmem<R> w;
     cx<R> *p = reinterpret_cast<cx<R> *>(base);
     w.gstack = gstack;
+    w.gs_level = gstack ? gs_level_of<R>(n_max, RF) : 0;
     w.stack = p;
-    p += gstack ? stack_entries_split(n_max, false) : stack_entries(n_max);
+    p += gstack ? stack_entries_split(n_max, false, w.gs_level) : stack_entries(n_max);
+    const int npair = n_max * (n_max + 3) / 2;
     w.P = p;
-    p += (n_max + 1) * (n_max + 1);
+    p += npair;
     w.Rr = p;
-    p += (n_max + 1) * (n_max + 1);
+    p += npair;
     w.detD = p;
     p += n_max + 1;
     w.bfs = p;
@@ -335,7 +370,8 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
         p += 32;
     }
     size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
-    w.upt = reinterpret_cast<double *>(base + off);
+    w.upt = gstack ? reinterpret_cast<double *>(gstack + stack_entries_split(n_max, true, w.gs_level) + 1)
+                   : reinterpret_cast<double *>(base + off);
     return w;
 }
 
@@ -548,7 +584,6 @@ template <class R, int RFMAX, bool GS>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                   double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
-    const int NP = n_max + 1;
     // 1. pair interpolation, 0 <= j < k <= n
     const int npairs = n * (n + 1) / 2;
     for (int p = lane; p < npairs; p += 32) {
@@ -558,13 +593,14 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         int j = p - k * (k - 1) / 2;
         cx<R> gl, gg;
         interp_pair<R>(tab, inv_h, s0, L, u[j] - u[k], gl, gg);
-        ws.P[j * NP + k] = gg;
-        ws.Rr[j * NP + k] = gl;
+        const int ok = p - j + k - 1;  // vertex k's block: (k-1)(k+2)/2
+        ws.P[ok + j] = gg;
+        ws.Rr[ok + j] = gl;
         if (j == 0) {  // measurement column of vertex k: g^<(u_k - t), g^>(u_k - t) for the charge
             cx<R> c0 = nconj(gl), c1 = nconj(gg);
             if (col) interp_col<R>(col, inv_h, s0, L, u[k] - u[0], c0, c1);
-            ws.Rr[k * NP] = c0;
-            ws.P[k * NP] = c1;
+            ws.Rr[ok + k] = c0;
+            ws.P[ok + k] = c1;
         }
     }
     __syncwarp();
@@ -583,7 +619,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         int o = 0, og = 0;
         for (int l = 0; l <= levels; ++l) {
             const int S = 2 * (R0 - l) + 2;
-            if (GS && S > kSmemLevel) {
+            if (GS && S > ws.gs_level) {
                 off[l] = og;
                 og += S * S;
                 lg = l + 1;
@@ -597,53 +633,58 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     const cx<R> id = crcp(dv);  // pivot of vertex 1
     {
         // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
-        const cx<R> P01 = ws.P[1], R01 = ws.Rr[1];
+        const cx<R> P01 = ws.P[0], R01 = ws.Rr[0];  // pair (0, 1)
         const cx<R> r1[2] = {P01, R01};
-        const cx<R> c1d[2] = {cmul(ws.Rr[1 * NP], id), cmul(ws.P[1 * NP], id)};
+        const cx<R> c1d[2] = {cmul(ws.Rr[1], id), cmul(ws.P[1], id)};  // column entries of vertex 1
+        // lane -> block (bx, by), stepped by 32 blocks without divisions; i = bx + 1 and
+        // j = by + 1 are the vertices, ti and tj the offsets of their packed blocks
+        const int sq = 32 / n, sr = 32 - sq * n;
+        int bx = lane / n, by = lane - bx * n;
         for (int bid = lane; bid < n * n; bid += 32) {
-            const int bx = bid / n, by = bid - bx * n;
+            const int i = bx + 1, j = by + 1;
+            const int ti = (int)((unsigned)((i - 1) * (i + 2)) >> 1), tj = (int)((unsigned)((j - 1) * (j + 2)) >> 1);
             cx<R> base[2][2], left[2], right[2];
             if (bx == 0) {
                 left[0] = r1[0];
                 left[1] = r1[1];
-            } else {  // vertex i = bx + 1 > 1, lower entries of column vertex 1
-                const int i = bx + 1;
-                left[0] = nconj(ws.Rr[1 * NP + i]);
-                left[1] = nconj(ws.P[1 * NP + i]);
+            } else {  // vertex i > 1: lower entries of column vertex 1, pair (1, i)
+                left[0] = nconj(ws.Rr[ti + 1]);
+                left[1] = nconj(ws.P[ti + 1]);
             }
             if (by == 0) {
                 right[0] = c1d[0];
                 right[1] = c1d[1];
-            } else {  // vertex j = by + 1 > 1, upper entries of row vertex 1
-                const int j = by + 1;
-                right[0] = cmul(ws.P[1 * NP + j], id);
-                right[1] = cmul(ws.Rr[1 * NP + j], id);
+            } else {  // vertex j > 1: upper entries of row vertex 1, pair (1, j)
+                right[0] = cmul(ws.P[tj + 1], id);
+                right[1] = cmul(ws.Rr[tj + 1], id);
             }
             if (bx == by) {  // measurement pair (bx = 0) or a vertex with itself
                 const cx<R> dd = bx == 0 ? d : dv;
                 base[0][0] = base[0][1] = base[1][0] = base[1][1] = dd;
-            } else if (bx == 0) {  // measurement row: r_j(aj)
-                const int j = by + 1;
-                base[0][0] = base[1][0] = ws.P[j];
-                base[0][1] = base[1][1] = ws.Rr[j];
+            } else if (bx == 0) {  // measurement row: r_j(aj), pair (0, j)
+                base[0][0] = base[1][0] = ws.P[tj];
+                base[0][1] = base[1][1] = ws.Rr[tj];
             } else if (by == 0) {  // measurement column: c_i(ai)
-                const int i = bx + 1;
-                base[0][0] = base[0][1] = ws.Rr[i * NP];
-                base[1][0] = base[1][1] = ws.P[i * NP];
-            } else if (bx < by) {  // upper: depends on aj
-                const int i = bx + 1, j = by + 1;
-                base[0][0] = base[1][0] = ws.P[i * NP + j];
-                base[0][1] = base[1][1] = ws.Rr[i * NP + j];
-            } else {  // lower: depends on ai
-                const int i = bx + 1, j = by + 1;
-                base[0][0] = base[0][1] = nconj(ws.Rr[j * NP + i]);
-                base[1][0] = base[1][1] = nconj(ws.P[j * NP + i]);
+                base[0][0] = base[0][1] = ws.Rr[ti + i];
+                base[1][0] = base[1][1] = ws.P[ti + i];
+            } else if (bx < by) {  // upper: depends on aj, pair (i, j)
+                base[0][0] = base[1][0] = ws.P[tj + i];
+                base[0][1] = base[1][1] = ws.Rr[tj + i];
+            } else {  // lower: depends on ai, pair (j, i)
+                base[0][0] = base[0][1] = nconj(ws.Rr[ti + j]);
+                base[1][0] = base[1][1] = nconj(ws.P[ti + j]);
             }
             cx<R> *o = level(0) + (2 * bx) * S0 + 2 * by;
 #pragma unroll
             for (int x = 0; x < 2; ++x)
 #pragma unroll
                 for (int y = 0; y < 2; ++y) o[x * S0 + y] = cfms(base[x][y], left[x], right[y]);
+            by += sr;
+            bx += sq;
+            if (by >= n) {
+                by -= n;
+                ++bx;
+            }
         }
     }
     if (lane == 0) ws.detD[0] = dv;
@@ -891,7 +932,7 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     cx<R> *gst = nullptr;
-    if (GS) gst = gstack + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * (stack_entries_split(n_max, true) + 1);
+    if (GS) gst = gstack + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * gstack_entries<R>(n_max, rf_min);
     WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, rf_min, GS), n_max, rf_min, gst);
     const int NU = n_max + 1;
     while (true) {
@@ -906,10 +947,11 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
         const long long local = (long long)c - I.chunk_begin;
         const int k = (int)(local / I.chunks_per_shift);
         const long long unit = local - (long long)k * I.chunks_per_shift;
-        const long long blk = unit >> I.split;                   // chunk of 32 points
+        const long long blk = unit >> (I.pbits + I.split);      // chunk of 32 points
         const int sub = (int)(unit & ((1ll << I.split) - 1));   // subtree of each point's Keldysh tree
+        const int grp = (int)(unit >> I.split) & ((1 << I.pbits) - 1);  // the chunk's lanes [grp * g, grp * g + g)
         const long long idx = blk * kChunk + lane;
-        const bool valid = idx < I.n_points;
+        const bool valid = idx < I.n_points && (lane >> (5 - I.pbits)) == grp;
         // point generation and warp (Sobol' integers are exact)
         bool inside = false;
         double w = 0.0;
@@ -1132,7 +1174,7 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     const int warp = threadIdx.x >> 5;
     const uint64_t wid = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
     cx<R> *gst = nullptr;
-    if (GS) gst = gstack + wid * (stack_entries_split(n_max, true) + 1);
+    if (GS) gst = gstack + wid * gstack_entries<R>(n_max, RF);
     WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF, GS), n_max, RF, gst);
     const int n = I.order;
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
@@ -1482,11 +1524,11 @@ size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
 }
 
 // The tree stack is split (wide top levels in device memory) where it does not
-// fit in shared memory (FP64 orders >= 21), and from the order set by
-// qqmc_set_stack_policy (default 13, measured faster on GB300 in both
-// precisions): a large shared-memory stack limits the warps per SM, while the
-// wide levels are built only a few times per point.
-constexpr int kGsDefault[2] = {13, 13};
+// fit in shared memory, and from the order set by qqmc_set_stack_policy
+// (default: FP64 from 11, mixed from 12, measured fastest on GB300): a large
+// shared-memory stack limits the warps per SM, while the wide levels are built
+// only a few times per point.
+constexpr int kGsDefault[2] = {11, 12};
 static int g_gs_min_order[2] = {kGsDefault[0], kGsDefault[1]};
 
 void set_stack_policy(int precision, int min_order) {
@@ -1555,7 +1597,7 @@ static long long gstack_warps_t(int n_max, int rf_min, size_t *bytes_per_warp) {
     const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min, true);
     long long per_sm = (long long)(kSmemMax / per_warp);  // resident warps, bound by shared memory
     if (per_sm > 64) per_sm = 64;                          // and by the SM's warp slots
-    *bytes_per_warp = (stack_entries_split(n_max, true) + 1) * sizeof(cx<R>);
+    *bytes_per_warp = gstack_entries<R>(n_max, rf_min) * sizeof(cx<R>);
     return (long long)sms * (per_sm < 1 ? 1 : per_sm);
 }
 
@@ -1656,7 +1698,7 @@ static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const
     cx<R> *gstack = nullptr;
     if (GS) {  // check path: a bounded number of warps, each with its own slice of device memory
         if (blocks > 304) blocks = 304;
-        e = cudaMalloc(&gstack, blocks * wpb * (stack_entries_split(item.order, true) + 1) * sizeof(cx<R>));
+        e = cudaMalloc(&gstack, blocks * wpb * gstack_entries<R>(item.order, F) * sizeof(cx<R>));
         if (e != cudaSuccess) return e;
     }
     integrand_kernel<R, F, GS><<<(unsigned)blocks, wpb * 32, smem, s>>>(item, count, d_u, d_out, item.order, gstack);

@@ -48,7 +48,8 @@ struct ItemDev {
     long long n_points;
     long long chunk_begin;   // first global chunk of this item
     int order, n_shifts, L;
-    int chunks_per_shift;    // work units per shift: point chunks << split
+    int chunks_per_shift;    // work units per shift: point chunks << (pbits + split)
+    int pbits;               // a chunk's 32 points in 2^pbits units of 32 >> pbits points
     int split;               // each point's Keldysh tree in 2^split subtrees (separate work units)
     int flat;                // vertices resolved per lane for this item (its order's tuning)
     const double *proj;      // learned warp: [order][proj_cells + 1] CDF per dimension, or null (plain)
