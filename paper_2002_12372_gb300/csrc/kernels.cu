@@ -526,28 +526,84 @@ __device__ __forceinline__ void expand_level(const cx<R> *__restrict__ in, int S
 
 // Single child (a depth-first step, S - 2 <= 32): each lane owns one column of
 // the child and a fixed row offset, so the scaled pivot-row entry of its
-// column stays in a register, the pivot-column entry of a row is a broadcast
-// load, and the index arithmetic per entry is one multiply-add.
+// column stays in a register and the pivot-column entry of a row is a
+// broadcast load.  A step is latency-bound (a few hundred flops per warp), so
+// every load of the step is issued before the pivot's reciprocal is formed,
+// and the lane mapping needs no division.
+//
+// Children of 2T = 12, 14 or 16 rows (the deep, frequent steps): lanes 0-15
+// take the even rows, lanes 16-31 the odd rows, column c2 = lane & 15.
+template <class R, int T>
+__device__ __forceinline__ void expand_one_t(const cx<R> *__restrict__ in, int a, cx<R> *__restrict__ out,
+                                             const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    constexpr int S2 = 2 * T, S = S2 + 2;
+    const int pr = 2 + a;
+    const int c2 = lane & 15, rsub = lane >> 4;
+    const bool act = c2 < S2;
+    const int c = c2 < 2 ? c2 : c2 + 2;
+    const cx<R> piv = in[pr * S + pr];
+    cx<R> prc = mk<R>(0, 0), ev[T], cv[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) ev[t] = cv[t] = mk<R>(0, 0);
+    if (act) {
+        prc = in[pr * S + c];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int r2 = rsub + 2 * t;
+            const int r = r2 < 2 ? r2 : r2 + 2;
+            ev[t] = in[r * S + c];
+            cv[t] = in[r * S + pr];
+        }
+    }
+    const cx<R> ip = crcp(piv);
+    if (lane == 0) *detD_out = cmul(*detD_in, piv);
+    if (act) {
+        const cx<R> w = cmul(prc, ip);
+#pragma unroll
+        for (int t = 0; t < T; ++t) out[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv[t], w);
+    }
+    __syncwarp();
+}
+
+// Wider children (S - 2 = 18 .. 32 rows, the rare top steps): lane = column,
+// rows in batches of four with the batch's loads issued first.
 template <class R>
-__device__ __forceinline__ void expand_one(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
-                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+__device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
+                                                const cx<R> *detD_in, cx<R> *detD_out, int lane) {
     const int S2 = S - 2;
     const int pr = 2 + a;
     const cx<R> piv = in[pr * S + pr];
     const cx<R> ip = crcp(piv);
     if (lane == 0) *detD_out = cmul(*detD_in, piv);
-    const int rows = 32 / S2;  // child rows per pass
-    const int rsub = lane / S2;
-    const int c2 = lane - rsub * S2;
-    if (rsub < rows) {
-        const int c = c2 < 2 ? c2 : c2 + 2;
+    if (lane < S2) {
+        const int c = lane < 2 ? lane : lane + 2;
         const cx<R> w = cmul(in[pr * S + c], ip);
-        for (int r2 = rsub; r2 < S2; r2 += rows) {
-            const int r = r2 < 2 ? r2 : r2 + 2;
-            out[r2 * S2 + c2] = cfms(in[r * S + c], in[r * S + pr], w);
+        for (int r0 = 0; r0 < S2; r0 += 4) {
+            cx<R> ev[4], cv[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int r2 = r0 + t < S2 ? r0 + t : S2 - 1;  // a clamped duplicate of the last row
+                const int r = r2 < 2 ? r2 : r2 + 2;
+                ev[t] = in[r * S + c];
+                cv[t] = in[r * S + pr];
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (r0 + t < S2) out[(r0 + t) * S2 + lane] = cfms(ev[t], cv[t], w);
         }
     }
     __syncwarp();
+}
+
+template <class R>
+__device__ __forceinline__ void expand_one(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
+                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    switch (S - 2) {
+        case 12: expand_one_t<R, 6>(in, a, out, detD_in, detD_out, lane); break;
+        case 14: expand_one_t<R, 7>(in, a, out, detD_in, detD_out, lane); break;
+        case 16: expand_one_t<R, 8>(in, a, out, detD_in, detD_out, lane); break;
+        default: expand_one_wide<R>(in, S, a, out, detD_in, detD_out, lane); break;
+    }
 }
 
 // Float-float or double-double style butterfly of the lane accumulators:
@@ -611,25 +667,21 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     // right = M(vertex 1, .) / d.
     const int R0 = n - 1;
     const int S0 = 2 * R0 + 2;
-    // tree levels: offsets in shared memory, or (split stack) in device memory for the wide ones
+    // tree levels: offsets in shared memory, or (split stack) in device memory for the wide ones.
+    // Level l holds S_l^2 = 4 (R0 + 1 - l)^2 entries, so the offset of level l within its part is
+    // 4 (Q(R0 + 1 - l0) - Q(R0 + 1 - l)), Q(x) = x(x+1)(2x+1)/6, l0 = the part's first level.
     const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
-    int off[kMaxOrder];
-    int lg = 0;  // levels [0, lg) in device memory
-    {
-        int o = 0, og = 0;
-        for (int l = 0; l <= levels; ++l) {
-            const int S = 2 * (R0 - l) + 2;
-            if (GS && S > ws.gs_level) {
-                off[l] = og;
-                og += S * S;
-                lg = l + 1;
-            } else {
-                off[l] = o;
-                o += S * S;
-            }
-        }
+    int lg = 0;  // levels [0, lg) in device memory: S_l > gs_level
+    if (GS) {
+        lg = R0 + 1 - ws.gs_level / 2;
+        lg = lg < 0 ? 0 : (lg > levels + 1 ? levels + 1 : lg);
     }
-    auto level = [&](int l) -> cx<R> * { return (GS && l < lg) ? ws.gstack + off[l] : ws.stack + off[l]; };
+    auto sq_sum = [](int x) { return x * (x + 1) * (2 * x + 1) / 6; };
+    const int qtop = sq_sum(R0 + 1), qsplit = sq_sum(R0 + 1 - lg);
+    auto level = [&](int l) -> cx<R> * {
+        const int ql = sq_sum(R0 + 1 - l);
+        return (GS && l < lg) ? ws.gstack + 4 * (qtop - ql) : ws.stack + 4 * (qsplit - ql);
+    };
     const cx<R> id = crcp(dv);  // pivot of vertex 1
     {
         // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
