@@ -235,7 +235,8 @@ struct WarpSmem {
     cx<R> *P;       // vertex k's block at o_k = (k-1)(k+2)/2: P[o_k + j] = g^>(u_j - u_k), 0 <= j < k,
                     // and P[o_k + k] = measurement-column entry (k, a_k = 1)
     cx<R> *Rr;      // Rr[o_k + j] = g^<(u_j - u_k); Rr[o_k + k] = column entry (k, a_k = 0)
-    cx<R> *detD;    // per tree level
+    cx<R> *detD;    // per tree level, and (after the last) the sibling leaf's
+    cx<R> *sib;     // the second leaf of a sibling pair (2 kTreeLeaf + 2)^2 entries
     cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
     cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
     cx<R> *bip;     // pivot reciprocal per child of the level being built (32)
@@ -297,6 +298,18 @@ __host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
     return m;
 }
 
+// The mixed-precision path builds sibling leaves in pairs (one depth-first step
+// for two leaves: its steps are latency-bound); the FP64 path, bound by its
+// FP64 pipe, gains nothing from it and keeps the shared memory for warps.
+template <class R>
+__host__ __device__ constexpr bool twin_leaves() { return sizeof(R) == 4; }
+
+// the sibling leaf buffer, used when the tree has depth-first levels
+template <class R>
+__host__ __device__ inline size_t sib_entries(int n_max) {
+    return twin_leaves<R>() && n_max - 1 > kTreeLeaf ? (size_t)(2 * kTreeLeaf + 2) * (2 * kTreeLeaf + 2) : 0;
+}
+
 // entries of the packed pair values with the measurement column (P and Rr:
 // blocks of k + 1 entries for the vertices k = 1 .. n_max)
 __host__ __device__ inline size_t pair_entries(int n_max) { return (size_t)n_max * (n_max + 3); }
@@ -308,7 +321,7 @@ template <class R>
 __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_level) {
     size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
     size_t c = (gs_level ? stack_entries_split(n_max, false, gs_level) : stack_entries(n_max)) + pair_entries(n_max) +
-               n_max + 1 + bfs_max_entries(n_max, RF) + wide;
+               n_max + 1 + sib_entries<R>(n_max) + bfs_max_entries(n_max, RF) + wide;
     size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
     if (!gs_level) bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
     return (bytes + 127) & ~(size_t)127;
@@ -317,12 +330,13 @@ __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_l
 // Split-stack boundary: the widest levels go to device memory, two rows at a
 // time, until a warp's shared memory lets the SM hold the warps its bound pipe
 // needs (FP64: 6 warps keep GB300's two FP64 lanes per SM busy; mixed: 12).
-// Never the tree leaf (S = 12), which the breadth-first and flat phases read.
+// Never the tree leaf (S = 12) or its parent (S = 14): the last depth-first
+// step and the breadth-first and flat phases work in shared memory only.
 template <class R>
 __host__ __device__ inline int gs_level_of(int n_max, int RF) {
     const size_t budget = sizeof(R) == 8 ? 36 * 1024 : 18 * 1024;
     int lev = 20;
-    while (lev > 2 * kTreeLeaf + 2 && warp_smem_bytes_at<R>(n_max, RF, lev) > budget) lev -= 2;
+    while (lev > 2 * kTreeLeaf + 4 && warp_smem_bytes_at<R>(n_max, RF, lev) > budget) lev -= 2;
     return lev;
 }
 
@@ -358,6 +372,8 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     p += npair;
     w.detD = p;
     p += n_max + 1;
+    w.sib = p;
+    p += sib_entries<R>(n_max);
     w.bfs = p;
     p += bfs_max_entries(n_max, RF);
     w.wrow = w.bdet = w.bip = nullptr;
@@ -565,6 +581,47 @@ __device__ __forceinline__ void expand_one_t(const cx<R> *__restrict__ in, int a
     __syncwarp();
 }
 
+// Both children (a = 0 into out0, a = 1 into out1) of a parent of 2T + 2 rows:
+// the last depth-first step, whose two children are consecutive leaves.  The
+// parent entries are loaded once for both, and both pivots' latencies overlap.
+template <class R, int T>
+__device__ __forceinline__ void expand_both_t(const cx<R> *__restrict__ in, cx<R> *__restrict__ out0,
+                                              cx<R> *__restrict__ out1, const cx<R> *detD_in, cx<R> *detD_out0,
+                                              cx<R> *detD_out1, int lane) {
+    constexpr int S2 = 2 * T, S = S2 + 2;
+    const int c2 = lane & 15, rsub = lane >> 4;
+    const bool act = c2 < S2;
+    const int c = c2 < 2 ? c2 : c2 + 2;
+    const cx<R> piv0 = in[2 * S + 2], piv1 = in[3 * S + 3];
+    cx<R> prc0 = mk<R>(0, 0), prc1 = mk<R>(0, 0), ev[T], cv0[T], cv1[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) ev[t] = cv0[t] = cv1[t] = mk<R>(0, 0);
+    if (act) {
+        prc0 = in[2 * S + c];
+        prc1 = in[3 * S + c];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int r2 = rsub + 2 * t;
+            const int r = r2 < 2 ? r2 : r2 + 2;
+            ev[t] = in[r * S + c];
+            cv0[t] = in[r * S + 2];
+            cv1[t] = in[r * S + 3];
+        }
+    }
+    const cx<R> ip0 = crcp(piv0), ip1 = crcp(piv1);
+    if (lane == 0) *detD_out0 = cmul(*detD_in, piv0);
+    if (lane == 1) *detD_out1 = cmul(*detD_in, piv1);
+    if (act) {
+        const cx<R> w0 = cmul(prc0, ip0), w1 = cmul(prc1, ip1);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            out0[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv0[t], w0);
+            out1[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv1[t], w1);
+        }
+    }
+    __syncwarp();
+}
+
 // Wider children (S - 2 = 18 .. 32 rows, the rare top steps): lane = column,
 // rows in batches of four with the batch's loads issued first.
 template <class R>
@@ -682,6 +739,8 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         const int ql = sq_sum(R0 + 1 - l);
         return (GS && l < lg) ? ws.gstack + 4 * (qtop - ql) : ws.stack + 4 * (qsplit - ql);
     };
+    // the leaf and its parent are always in shared memory (gs_level >= 14)
+    auto level_smem = [&](int l) -> cx<R> * { return ws.stack + 4 * (qsplit - sq_sum(R0 + 1 - l)); };
     const cx<R> id = crcp(dv);  // pivot of vertex 1
     {
         // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
@@ -752,10 +811,13 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     const int node = lane >> Rf;
     const int path = lane & ((1 << Rf) - 1);
     const bool active = lane < (1 << Rleaf);
-    for (int bl = 0; bl < nleaf; ++bl) {
+    // With two or more leaves in the walk, leaves come in sibling pairs: the last depth-first step
+    // builds both (the second into ws.sib) and the pair is resolved one after the other.
+    const int twin = twin_leaves<R>() && levels - split >= 1 ? 1 : 0;
+    for (int bl = 0; bl < nleaf; bl += 1 + twin) {
         const int b = (sub << (levels - split)) | bl;  // tree path: the subtree's fixed prefix, then bl
         int from = (bl == 0) ? 0 : levels - (__ffs(b) - 1) - 1;
-        for (int l = from; l < levels; ++l) {
+        for (int l = from; l < levels - twin; ++l) {
             const int a = (b >> (levels - 1 - l)) & 1;
             const int S = 2 * (R0 - l) + 2;
             if (S - 2 <= 32)
@@ -764,30 +826,36 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
                 expand_level<R>(level(l), S, 1, a, level(l + 1), ws.detD + l, ws.detD + l + 1, ws.wrow, ws.bip,
                                 lane);
         }
-        const int tparity = __popc(b) & 1;
-        // 4. breadth-first expansion of B levels below the tree leaf
-        const cx<R> *E = level(levels);
-        int S = 2 * Rleaf + 2;
-        const cx<R> *ndet = ws.detD + levels;
-        cx<R> *dbuf = ws.bdet;
-        size_t bo = 0;
-        for (int lb = 0; lb < B; ++lb) {
-            const int nparent = 1 << lb;
-            cx<R> *out = ws.bfs + bo;
-            expand_level<R>(E, S, 2 * nparent, 0, out, ndet, dbuf, ws.wrow, ws.bip, lane);
-            bo += (size_t)(2 * nparent) * (S - 2) * (S - 2);
-            E = out;
-            S -= 2;
-            ndet = dbuf;
-            dbuf = (dbuf == ws.bdet) ? ws.bdet + 32 : ws.bdet;
+        if (twin)  // the leaves' parent has 2 kTreeLeaf + 4 rows
+            expand_both_t<R, kTreeLeaf + 1>(level_smem(levels - 1), level_smem(levels), ws.sib,
+                                            ws.detD + levels - 1, ws.detD + levels, ws.detD + levels + 1, lane);
+#pragma unroll 1
+        for (int h = 0; h <= twin; ++h) {
+            const int tparity = __popc(b + h) & 1;
+            // 4. breadth-first expansion of B levels below the tree leaf
+            const cx<R> *E = h ? ws.sib : level_smem(levels);
+            int S = 2 * Rleaf + 2;
+            const cx<R> *ndet = ws.detD + levels + h;
+            cx<R> *dbuf = ws.bdet;
+            size_t bo = 0;
+            for (int lb = 0; lb < B; ++lb) {
+                const int nparent = 1 << lb;
+                cx<R> *out = ws.bfs + bo;
+                expand_level<R>(E, S, 2 * nparent, 0, out, ndet, dbuf, ws.wrow, ws.bip, lane);
+                bo += (size_t)(2 * nparent) * (S - 2) * (S - 2);
+                E = out;
+                S -= 2;
+                ndet = dbuf;
+                dbuf = (dbuf == ws.bdet) ? ws.bdet + 32 : ws.bdet;
+            }
+            // 5. per-lane flat phase on the last Rf vertices
+            if (active) {
+                const cx<R> *En = E + (size_t)node * S * S;
+                const int parity = tparity ^ (__popc(node) & 1);
+                flat_dispatch<R, RFMAX>(Rf, En, ndet[B > 0 ? node : 0], parity, path, ar, ai);
+            }
+            __syncwarp();
         }
-        // 5. per-lane flat phase on the last Rf vertices
-        if (active) {
-            const cx<R> *En = E + (size_t)node * S * S;
-            const int parity = tparity ^ (__popc(node) & 1);
-            flat_dispatch<R, RFMAX>(Rf, En, ndet[B > 0 ? node : 0], parity, path, ar, ai);
-        }
-        __syncwarp();
     }
     return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
 }
@@ -1577,10 +1645,10 @@ size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
 
 // The tree stack is split (wide top levels in device memory) where it does not
 // fit in shared memory, and from the order set by qqmc_set_stack_policy
-// (default: FP64 from 11, mixed from 12, measured fastest on GB300): a large
+// (default: from order 11 in both precisions, measured fastest on GB300): a large
 // shared-memory stack limits the warps per SM, while the wide levels are built
 // only a few times per point.
-constexpr int kGsDefault[2] = {11, 12};
+constexpr int kGsDefault[2] = {11, 11};
 static int g_gs_min_order[2] = {kGsDefault[0], kGsDefault[1]};
 
 void set_stack_policy(int precision, int min_order) {
