@@ -77,7 +77,15 @@ __device__ __forceinline__ cx<R> cfms(cx<R> c, cx<R> a, cx<R> b) {
 // rcp.approx.ftz.f32) refined by one Newton-Raphson step r' = r + r (1 - x r),
 // which leaves ~1 ulp, well inside the FP32 path's error budget and without
 // the division's special-case branch.
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// FP64 reciprocal: the hardware approximation refined by two Newton-Raphson
+// steps r <- r + r (1 - x r) (each squares the relative error), fewer FP64
+// instructions than an IEEE division; within an ulp or two of 1/x.
+__device__ __forceinline__ double recip(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
 __device__ __forceinline__ float recip(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
