@@ -245,6 +245,7 @@ struct WarpSmem {
     cx<R> *Rr;      // Rr[o_k + j] = g^<(u_j - u_k); Rr[o_k + k] = column entry (k, a_k = 0)
     cx<R> *detD;    // per tree level, and (after the last) the sibling leaf's
     cx<R> *sib;     // the second leaf of a sibling pair (2 kTreeLeaf + 2)^2 entries
+    cx<R> *lr;      // level 0: left and right factors of vertex 1 per block index (4 n_max)
     cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
     cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
     cx<R> *bip;     // pivot reciprocal per child of the level being built (32)
@@ -329,7 +330,7 @@ template <class R>
 __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_level) {
     size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
     size_t c = (gs_level ? stack_entries_split(n_max, false, gs_level) : stack_entries(n_max)) + pair_entries(n_max) +
-               n_max + 1 + sib_entries<R>(n_max) + bfs_max_entries(n_max, RF) + wide;
+               n_max + 1 + sib_entries<R>(n_max) + 4 * (size_t)n_max + bfs_max_entries(n_max, RF) + wide;
     size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
     if (!gs_level) bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
     return (bytes + 127) & ~(size_t)127;
@@ -382,6 +383,8 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     p += n_max + 1;
     w.sib = p;
     p += sib_entries<R>(n_max);
+    w.lr = p;
+    p += 4 * n_max;
     w.bfs = p;
     p += bfs_max_entries(n_max, RF);
     w.wrow = w.bdet = w.bip = nullptr;
@@ -631,10 +634,11 @@ __device__ __forceinline__ void expand_both_t(const cx<R> *__restrict__ in, cx<R
 }
 
 // Wider children (S - 2 = 18 .. 32 rows, the rare top steps): lane = column,
-// rows in batches of four with the batch's loads issued first.
+// rows in batches (eight in FP32, four in FP64) with the batch's loads issued first.
 template <class R>
 __device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
                                                 const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    constexpr int NB = sizeof(R) == 4 ? 8 : 4;  // rows per batch (FP64: register budget)
     const int S2 = S - 2;
     const int pr = 2 + a;
     const cx<R> piv = in[pr * S + pr];
@@ -643,17 +647,17 @@ __device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, in
     if (lane < S2) {
         const int c = lane < 2 ? lane : lane + 2;
         const cx<R> w = cmul(in[pr * S + c], ip);
-        for (int r0 = 0; r0 < S2; r0 += 4) {
-            cx<R> ev[4], cv[4];
+        for (int r0 = 0; r0 < S2; r0 += NB) {
+            cx<R> ev[NB], cv[NB];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < NB; ++t) {
                 const int r2 = r0 + t < S2 ? r0 + t : S2 - 1;  // a clamped duplicate of the last row
                 const int r = r2 < 2 ? r2 : r2 + 2;
                 ev[t] = in[r * S + c];
                 cv[t] = in[r * S + pr];
             }
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
+            for (int t = 0; t < NB; ++t)
                 if (r0 + t < S2) out[(r0 + t) * S2 + lane] = cfms(ev[t], cv[t], w);
         }
     }
@@ -751,53 +755,54 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     auto level_smem = [&](int l) -> cx<R> * { return ws.stack + 4 * (qsplit - sq_sum(R0 + 1 - l)); };
     const cx<R> id = crcp(dv);  // pivot of vertex 1
     {
-        // measurement row entries r_1(a) and column entries c_1(a) / d of vertex 1
-        const cx<R> P01 = ws.P[0], R01 = ws.Rr[0];  // pair (0, 1)
-        const cx<R> r1[2] = {P01, R01};
-        const cx<R> c1d[2] = {cmul(ws.Rr[1], id), cmul(ws.P[1], id)};  // column entries of vertex 1
+        // Block row b's left factors M(., vertex 1) and block column b's right factors
+        // M(vertex 1, .) / d, once per block index: b = 0 the measurement copies (row entries
+        // r_1(a), column entries c_1(a) / d), b >= 1 vertex b + 1 (pair (1, b + 1)).
+        if (lane < n) {
+            cx<R> l0, l1, r0, r1;
+            if (lane == 0) {
+                l0 = ws.P[0];  // pair (0, 1)
+                l1 = ws.Rr[0];
+                r0 = cmul(ws.Rr[1], id);  // column entries of vertex 1
+                r1 = cmul(ws.P[1], id);
+            } else {
+                const int t = (lane * (lane + 3)) >> 1;  // vertex lane + 1's block
+                l0 = nconj(ws.Rr[t + 1]);
+                l1 = nconj(ws.P[t + 1]);
+                r0 = cmul(ws.P[t + 1], id);
+                r1 = cmul(ws.Rr[t + 1], id);
+            }
+            ws.lr[4 * lane] = l0;
+            ws.lr[4 * lane + 1] = l1;
+            ws.lr[4 * lane + 2] = r0;
+            ws.lr[4 * lane + 3] = r1;
+        }
+        __syncwarp();
         // lane -> block (bx, by), stepped by 32 blocks without divisions; i = bx + 1 and
-        // j = by + 1 are the vertices, ti and tj the offsets of their packed blocks
+        // j = by + 1 are the vertices, ti and tj the offsets of their packed blocks.  Within a
+        // block the entry is base(ai, aj) - left(ai) right(aj); base is the pair value of the
+        // later vertex's index: above the diagonal (row 0: the measurement row) it follows aj,
+        // below it (column 0: the measurement column, stored as is) it follows ai.
         const int sq = 32 / n, sr = 32 - sq * n;
         int bx = lane / n, by = lane - bx * n;
         for (int bid = lane; bid < n * n; bid += 32) {
             const int i = bx + 1, j = by + 1;
             const int ti = (int)((unsigned)((i - 1) * (i + 2)) >> 1), tj = (int)((unsigned)((j - 1) * (j + 2)) >> 1);
-            cx<R> base[2][2], left[2], right[2];
-            if (bx == 0) {
-                left[0] = r1[0];
-                left[1] = r1[1];
-            } else {  // vertex i > 1: lower entries of column vertex 1, pair (1, i)
-                left[0] = nconj(ws.Rr[ti + 1]);
-                left[1] = nconj(ws.P[ti + 1]);
-            }
-            if (by == 0) {
-                right[0] = c1d[0];
-                right[1] = c1d[1];
-            } else {  // vertex j > 1: upper entries of row vertex 1, pair (1, j)
-                right[0] = cmul(ws.P[tj + 1], id);
-                right[1] = cmul(ws.Rr[tj + 1], id);
-            }
-            if (bx == by) {  // measurement pair (bx = 0) or a vertex with itself
-                const cx<R> dd = bx == 0 ? d : dv;
-                base[0][0] = base[0][1] = base[1][0] = base[1][1] = dd;
-            } else if (bx == 0) {  // measurement row: r_j(aj), pair (0, j)
-                base[0][0] = base[1][0] = ws.P[tj];
-                base[0][1] = base[1][1] = ws.Rr[tj];
-            } else if (by == 0) {  // measurement column: c_i(ai)
-                base[0][0] = base[0][1] = ws.Rr[ti + i];
-                base[1][0] = base[1][1] = ws.P[ti + i];
-            } else if (bx < by) {  // upper: depends on aj, pair (i, j)
-                base[0][0] = base[1][0] = ws.P[tj + i];
-                base[0][1] = base[1][1] = ws.Rr[tj + i];
-            } else {  // lower: depends on ai, pair (j, i)
-                base[0][0] = base[0][1] = nconj(ws.Rr[ti + j]);
-                base[1][0] = base[1][1] = nconj(ws.P[ti + j]);
-            }
+            const bool up = bx < by, diag = bx == by;
+            const int idx = up ? tj + (bx ? i : 0) : ti + (by ? j : i);
+            const cx<R> vP = ws.P[idx], vR = ws.Rr[idx];
+            const cx<R> left0 = ws.lr[4 * bx], left1 = ws.lr[4 * bx + 1];
+            const cx<R> right0 = ws.lr[4 * by + 2], right1 = ws.lr[4 * by + 3];
+            const R sg = (!up && by) ? R(-1) : R(1);  // lower entries of vertex pairs: -conj
+            const cx<R> lo0 = mk<R>(sg * vR.re, vR.im), lo1 = mk<R>(sg * vP.re, vP.im);
+            const cx<R> dd = bx == 0 ? d : dv;
+            const cx<R> b00 = diag ? dd : (up ? vP : lo0), b01 = diag ? dd : (up ? vR : lo0);
+            const cx<R> b10 = diag ? dd : (up ? vP : lo1), b11 = diag ? dd : (up ? vR : lo1);
             cx<R> *o = level(0) + (2 * bx) * S0 + 2 * by;
-#pragma unroll
-            for (int x = 0; x < 2; ++x)
-#pragma unroll
-                for (int y = 0; y < 2; ++y) o[x * S0 + y] = cfms(base[x][y], left[x], right[y]);
+            o[0] = cfms(b00, left0, right0);
+            o[1] = cfms(b01, left0, right1);
+            o[S0] = cfms(b10, left1, right0);
+            o[S0 + 1] = cfms(b11, left1, right1);
             by += sr;
             bx += sq;
             if (by >= n) {
