@@ -529,23 +529,27 @@ __device__ __forceinline__ void expand_level(const cx<R> *__restrict__ in, int S
         wrow[q] = cmul(in[(size_t)pj * S * S + pr * S + c], ip_buf[j]);
     }
     __syncwarp();
-    // lane -> (child j, row r2, column c2) stepped by 32 entries without divisions
-    const int dr = 32 / S2, dc = 32 - dr * S2;
-    int r2 = lane / S2, c2 = lane - r2 * S2, j = 0;
+    // Only entries that are ever read are built: a choice path takes one copy of every vertex
+    // (and one measurement copy per determinant), so the entry joining row r2 to its row's
+    // other copy, column r2 ^ 1, is never used (1 / S2 of the updates).  lane -> (child j,
+    // row r2, used column cc of W = S2 - 1) stepped by 32 entries without divisions.
+    const int W = S2 - 1;
+    const int dr = 32 / W, dc = 32 - dr * W;
+    int r2 = lane / W, cc = lane - r2 * W, j = 0;
     while (r2 >= S2) { r2 -= S2; ++j; }
-    const int total = nchild * S2 * S2;
-    cx<R> *o = out + lane;
-    for (int e = lane; e < total; e += 32, o += 32) {
+    const int total = nchild * S2 * W;
+    for (int e = lane; e < total; e += 32) {
+        const int c2 = cc < (r2 ^ 1) ? cc : cc + 1;
         const int a = nchild == 1 ? first_a : (j & 1);
         const int pj = nchild == 1 ? 0 : (j >> 1);
         const int pr = 2 + a;
         const int r = r2 < 2 ? r2 : r2 + 2;
         const int c = c2 < 2 ? c2 : c2 + 2;
         const cx<R> *P = in + (size_t)pj * S * S;
-        *o = cfms(P[r * S + c], P[r * S + pr], wrow[j * S2 + c2]);
-        c2 += dc;
+        out[((size_t)j * S2 + r2) * S2 + c2] = cfms(P[r * S + c], P[r * S + pr], wrow[j * S2 + c2]);
+        cc += dc;
         r2 += dr;
-        if (c2 >= S2) { c2 -= S2; ++r2; }
+        if (cc >= W) { cc -= W; ++r2; }
         while (r2 >= S2) { r2 -= S2; ++j; }
     }
     __syncwarp();

@@ -53,21 +53,26 @@ def flops_per_point(n: int, RF: int = 2) -> float:
     fl = 0.0
     # pair interpolation: 2 complex lerps + position arithmetic
     fl += (n * (n + 1) // 2) * 12
-    # level 0: cmul (right * 1/d) + cfms per entry, one reciprocal
-    fl += S0 * S0 * (CMUL + CFMS) + CRCP
+    # level 0: one cfms per entry, the right factors M(1, .) / d once per block index
+    # (2 cmul each), one reciprocal
+    fl += S0 * S0 * CFMS + 2 * n * CMUL + CRCP
     levels = R0 - TREE_LEAF if R0 > TREE_LEAF else 0
     Rleaf = R0 - levels
-    # depth-first tree: level l -> l+1 computed 2^(l+1) times in the walk
+    # depth-first tree: level l -> l+1 computed 2^(l+1) times in the walk; children wider
+    # than a warp (S2 > 32) take the general step, which skips the never-read entries that
+    # join a row to its other copy (S2 of the S2^2)
     for l in range(levels):
         S2 = 2 * (R0 - l)
-        fl += 2 ** (l + 1) * (S2 * CMUL + S2 * S2 * CFMS + CRCP + CMUL)
-    # below each tree leaf: breadth-first levels, then the per-lane flat phase
+        upd = S2 * (S2 - 1) if S2 > 32 else S2 * S2
+        fl += 2 ** (l + 1) * (S2 * CMUL + upd * CFMS + CRCP + CMUL)
+    # below each tree leaf: breadth-first levels (the general step, S2 (S2 - 1) updates),
+    # then the per-lane flat phase
     B = Rleaf - RF if Rleaf > RF else 0
     Rf = Rleaf - B
     leaf = 0.0
     for lb in range(B):
         S2 = 2 * (Rleaf - lb)
-        leaf += 2 ** (lb + 1) * (CRCP + CMUL + S2 * CMUL + S2 * S2 * CFMS)
+        leaf += 2 ** (lb + 1) * (CRCP + CMUL + S2 * CMUL + S2 * (S2 - 1) * CFMS)
     leaf += 2 ** Rleaf * _flat_lane(Rf)
     return fl + 2 ** levels * leaf
 
