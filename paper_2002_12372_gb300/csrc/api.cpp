@@ -41,11 +41,11 @@ static bool g_tune_set[2][kMaxOrder + 1];
 static Tuning default_tuning(int precision, int order) {
     Tuning t;
     // FP64: breadth-first expansion below the tree leaf, 2 vertices per lane
-    // (the FP64 pipe is the bound, so fewer flops win), 3 from order 10 on
-    // (smaller breadth-first buffers: more warps per SM for the deep stacks);
-    // mixed: 5 vertices per lane in registers (shared-memory traffic of
-    // cooperative updates is the FP32 bound).
-    t.flat = precision == QQMC_PREC_FP64 ? (order >= 10 ? 3 : 2) : 5;
+    // (the FP64 pipe is the bound, so fewer flops win; measured best on GB300
+    // at orders 11..16); mixed: 5 vertices per lane in registers (the
+    // cooperative steps are latency-bound in FP32).
+    (void)order;
+    t.flat = precision == QQMC_PREC_FP64 ? 2 : 5;
     t.flat_min = t.flat;
     t.warps_per_block = precision == QQMC_PREC_FP64 ? 2 : 4;
     return t;
