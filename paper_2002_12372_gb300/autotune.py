@@ -1,8 +1,11 @@
 """Autotuner of the determinant kernel's launch shape.
 
-A batched plan runs with the tuning of its highest order, so the tuner times,
-for each highest order n, a batch holding every order 1..n of the plain dot
-(the shape of the benchmark batch and of a served request).  The candidates
+A plan groups its items by their orders' tuned flat depth and launches each
+group with the shape of the group's highest order.  For each order n the tuner
+times a batch holding every order 1..n of the plain dot (the shape of the
+benchmark batch and of a served request) with the candidate shape installed
+for n and the shapes already chosen for 1..n-1, so n's choice is measured in
+the launch it will share.  The candidates
 are warps per block (points in flight per block) and vertices resolved per
 lane in the flat phase (a lane's Keldysh chunk: one of 2^flat choice paths of
 the last vertices).  The fastest shape is installed with ``qqmc_set_tuning``
