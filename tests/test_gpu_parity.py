@@ -325,6 +325,33 @@ def test_checkpoint_resume_by_index_cursor(Q, W, oracle):
         Q.qqmc_destroy_problem(pr)
 
 
+def test_cut_work_units_match_oracle(Q, W, oracle):
+    """Few points at a high order: the plan cuts each 32-point chunk into single-point units and
+    each point's Keldysh tree into subtrees (order 13, 64 points, 1 shift: 2 chunks -> 64 point
+    units -> 512 subtree units).  Each chunk's sum (over its units), the per-shift sum and the
+    in-domain count match the oracle over the same points (FP64, relative 1e-10)."""
+    T, n, N = 10.0, 13, 64
+    pr, tabs = _problem(Q, W, seed=313, T=T)
+    try:
+        sw = W.shift_words(1313, 1, n)
+        plan = Q.Plan([(pr, n, 1, N, sw)], Q.QQMC_PREC_FP64)
+        plan.launch()
+        (res, S), = plan.results()
+        got = plan.chunk_sums(0, 0, [0, 1])
+        plan.close()
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    refs, nin = [], 0
+    for c in range(2):
+        S0, cnt = oracle.estimate(n, 32, sw, T, 1.0, tabs, T, i0=32 * c)
+        refs.append(S0[0] * 32)
+        nin += int(cnt.sum())
+    assert res.n_in_domain == nin
+    for g, ref in zip(got, refs):
+        assert abs(g - ref) <= 1e-10 * abs(ref), (g, ref)
+    assert abs(S[0] - (refs[0] + refs[1]) / N) <= 1e-10 * abs(S[0])
+
+
 @pytest.mark.parametrize("order", [13, 14, 16, 17, 18])
 def test_high_orders_match_oracle(Q, W, oracle, order):
     """Orders beyond the benchmark table (the paper reaches 22): integrand parity at a few points
