@@ -212,6 +212,31 @@ def test_integration_mixed_within_stated_bound_of_fp64(Q, W, oracle, order, N):
     assert abs(r32.q_mean - r64.q_mean) <= 0.05 * r64.q_err
 
 
+@pytest.mark.parametrize("flat", [2, 3, 4, 5])
+def test_mixed_every_flat_depth_within_bound_of_fp64(Q, W, oracle, flat):
+    """Every flat depth of the mixed kernel, with the breadth-first levels above it (the first one
+    built as both children of the leaf in one pass), against the FP64 path on the same shifts:
+    equal in-domain counts, per-shift sums within 1e-4 of the shifts' scale (the largest |S_k|:
+    a shift sum that cancels between points keeps the absolute FP32 error of the others) and the
+    shift mean within 5% of its error bar."""
+    from paper_2002_12372_gb300 import autotune
+    T, K = 10.0, 8
+    pr, tabs = _problem(Q, W, seed=90, T=T)
+    try:
+        for n, N in [(6, 1024), (7, 1024), (10, 256)]:
+            Q.qqmc_set_tuning(Q.QQMC_PREC_MIXED, n, 2, flat)
+            sw = W.shift_words(4000 + n, K, n)
+            r64, S64 = Q.qqmc_integrate(pr, n, N, K, Q.QQMC_PREC_FP64, sw)
+            r32, S32 = Q.qqmc_integrate(pr, n, N, K, Q.QQMC_PREC_MIXED, sw)
+            assert r32.n_in_domain == r64.n_in_domain
+            scale = np.max(np.abs(S64))
+            assert np.all(np.abs(S32 - S64) <= 1e-4 * scale), (n, np.abs(S32 - S64) / scale)
+            assert abs(r32.q_mean - r64.q_mean) <= 0.05 * r64.q_err
+    finally:
+        Q.qqmc_destroy_problem(pr)
+        autotune.reset()
+
+
 @pytest.mark.slow
 def test_full_size_bench_launch_sampled_chunks(Q, W, oracle):
     """The benchmark's launch shape at full size (three problems, n = 1..10, N = 2^20 x 32 shifts,
