@@ -319,6 +319,7 @@ struct qqmc_plan {
         int first = 0, count = 0, n_max = 0;
         long long chunks = 0;
         Tuning tune{};
+        long long gstack_warps = 0;  // warps with a device-memory stack slice, fixed at creation
     };
     std::vector<Group> groups;
     int precision = 0;
@@ -524,10 +525,13 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     }
     pl->chunks_lane = cl;
     // the groups launch one after another on the plan's stream and share one tree-stack buffer
+    // (each group keeps the warp count it was sized for, so a later change of the stack policy
+    // cannot make a launch index past the buffer)
     size_t gs_bytes = 0;
-    for (const auto &g : pl->groups) {
+    for (auto &g : pl->groups) {
         size_t bpw = 0;
         const long long w = detsum_gstack_warps(g.n_max, precision, g.tune, &bpw);
+        g.gstack_warps = w;
         if ((size_t)w * bpw > gs_bytes) gs_bytes = (size_t)w * bpw;
         if (w > pl->gstack_warps) pl->gstack_warps = w;
     }
@@ -560,11 +564,11 @@ static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
     if (timed && (e = cudaEventRecord(pl->ek0, s)) != cudaSuccess) return e;
     for (int gi = 0; gi < ng; ++gi) {
         const auto &g = pl->groups[gi];
-        // a group's share of the device-memory stack: the buffer holds the largest group's need
-        size_t bpw = 0;
-        const long long w = detsum_gstack_warps(g.n_max, pl->precision, g.tune, &bpw);
+        // a group's share of the device-memory stack (the buffer holds the largest group's need);
+        // a group sized without one gets none, and then runs the shared-memory stack or fails cleanly
+        const long long w = g.gstack_warps;
         e = launch_detsum(pl->d_items + g.first, g.count, g.chunks, pl->d_counter + gi, g.n_max, pl->precision, g.tune,
-                          pl->d_gstack, w, s);
+                          w > 0 ? pl->d_gstack : nullptr, w, s);
         if (e != cudaSuccess) return e;
     }
     const int n_lane = (int)pl->items.size() - pl->n_warp;

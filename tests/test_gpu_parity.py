@@ -473,3 +473,32 @@ def test_split_stack_is_bit_identical(Q, W, precision):
     for (r0, S0), (r1, S1) in zip(ref, out):
         assert r0.n_in_domain == r1.n_in_domain
         assert np.array_equal(S0, S1)
+
+
+def test_stack_policy_change_after_plan_creation(Q, W):
+    """A plan keeps the device-memory stack it was sized for: changing the stack policy between
+    creating and launching it leaves the sums unchanged (the split and the shared-memory stacks run
+    the same arithmetic)."""
+    T = 10.0
+    pr, _ = _problem(Q, W, seed=93, T=T)
+    items = [(pr, n, 2, N, W.shift_words(190 + n, 2, n)) for n, N in [(6, 700), (9, 130), (12, 33)]]
+    try:
+        Q.qqmc_set_stack_policy(0, Q.QQMC_MAX_ORDER + 1)
+        ref = Q.Plan(items, 0)
+        ref.launch()
+        ref_out = ref.results()
+        Q.qqmc_set_stack_policy(0, 1)  # after creation: the plan was sized without a split stack
+        ref.launch()
+        out1 = ref.results()
+        ref.close()
+        split = Q.Plan(items, 0)  # sized with the split stack for every group
+        Q.qqmc_set_stack_policy(0, Q.QQMC_MAX_ORDER + 1)
+        split.launch()
+        out2 = split.results()
+        split.close()
+    finally:
+        Q.qqmc_set_stack_policy(0, 0)
+        Q.qqmc_destroy_problem(pr)
+    for (r0, S0), (r1, S1), (r2, S2) in zip(ref_out, out1, out2):
+        assert r0.n_in_domain == r1.n_in_domain == r2.n_in_domain
+        assert np.array_equal(S0, S1) and np.array_equal(S0, S2)
