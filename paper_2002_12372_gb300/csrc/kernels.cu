@@ -35,6 +35,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "qqmc_internal.h"
 
 namespace qqmc {
@@ -1666,16 +1668,16 @@ size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
 // shared-memory stack limits the warps per SM, while the wide levels are built
 // only a few times per point.
 constexpr int kGsDefault[2] = {11, 11};
-static int g_gs_min_order[2] = {kGsDefault[0], kGsDefault[1]};
+static std::atomic<int> g_gs_min_order[2] = {{kGsDefault[0]}, {kGsDefault[1]}};  // read by plans on any thread
 
 void set_stack_policy(int precision, int min_order) {
     const int p = precision == QQMC_PREC_FP64 ? 0 : 1;
-    g_gs_min_order[p] = min_order <= 0 ? kGsDefault[p] : min_order;
+    g_gs_min_order[p].store(min_order <= 0 ? kGsDefault[p] : min_order);
 }
 
 template <class R>
 static bool stack_in_global(int n_max, int rf_min) {
-    return warp_smem_bytes<R>(n_max, rf_min) > kSmemMax || n_max >= g_gs_min_order[sizeof(R) == 8 ? 0 : 1];
+    return warp_smem_bytes<R>(n_max, rf_min) > kSmemMax || n_max >= g_gs_min_order[sizeof(R) == 8 ? 0 : 1].load();
 }
 
 template <class R, int F, bool GS>
