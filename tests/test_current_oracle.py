@@ -5,7 +5,6 @@ Each pin compares with something other than the oracle's own formulas: a
 30-digit mpmath quadrature, the wide-band closed form, equal-time identities of
 the operators, the Landauer formula, and the first-order (Hartree) relation.
 """
-import math
 
 import numpy as np
 import pytest
