@@ -462,7 +462,7 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     });
     std::vector<uint32_t> hs(shift_words_total);
     size_t so = 0, co = 0;
-    long long cw = 0, cl = 0;
+    long long cl = 0;
     pl->hitems.resize(n_items);
     for (int q = 0; q < n_items; ++q) {
         const int ci = pl->perm[q];
