@@ -251,15 +251,20 @@ typedef struct qqmc_plan qqmc_plan;
 
 /*
  * Batched, device-resident execution.  qqmc_plan_create uploads the items'
- * shift words and allocates the partial-sum buffers (the problems must
- * outlive the plan).  qqmc_plan_launch enqueues the whole batch -- one
- * persistent kernel over all items (uneven orders and point counts share
- * one launch) and one reduction kernel -- on `stream` (a cudaStream_t, or
- * NULL for the legacy default stream) and returns without waiting; with
- * use_graph != 0 the pair is captured once into a CUDA graph and replayed.
+ * shift words and allocates the partial-sum buffers and, where the stack
+ * policy in force at creation splits the Schur-tree stack, its device-memory
+ * part (the problems must outlive the plan).  Items with few chunks of 32
+ * points are cut into finer work units -- a chunk's points into groups, then
+ * each point's Keldysh tree into subtrees -- until an item has about 16384
+ * units; the cut depends on the item alone.  qqmc_plan_launch enqueues the
+ * whole batch -- one persistent launch per tuned flat depth (uneven orders
+ * and point counts share it), one for the orders tuned to one point per
+ * lane, and one reduction kernel -- on `stream` (a cudaStream_t, or NULL for
+ * the legacy default stream) and returns without waiting; with use_graph !=
+ * 0 the launches are captured once into a CUDA graph and replayed.
  * qqmc_plan_results waits for the last launch and copies per-item results
  * (results: [n_items]; per_shift: concatenated [sum_k n_shifts][2] S_k, or
- * NULL).  qqmc_plan_device_ms returns the device time of the last launch.
+ * NULL).
  */
 int qqmc_plan_create(const qqmc_item *items, int n_items, int precision, qqmc_plan **out);
 int qqmc_plan_launch(qqmc_plan *plan, void *stream, int use_graph);
@@ -278,9 +283,9 @@ int qqmc_plan_timing(const qqmc_plan *plan, double *kernel_ms, double *total_ms)
  * chunk[0..count-1] (chunk c holds Sobol' indices first_index + 32c ..
  * first_index + 32c + 31 of that sequence), out[4*q..4*q+3] = (sum.re,
  * sum.im, compensation.re, compensation.im) of w_i c_n(u_i) over the chunk's
- * in-domain points, as the determinant kernel wrote it.  For checking a
- * full-size launch point by point against a reference.  E_INVAL on bad
- * indices.
+ * in-domain points: the sum of the partials of the chunk's work units
+ * (point groups and subtrees, in unit order).  For checking a full-size
+ * launch point by point against a reference.  E_INVAL on bad indices.
  */
 int qqmc_plan_chunk_sums(const qqmc_plan *plan, int item, int shift, const int64_t *chunk, int count, double *out);
 
@@ -291,8 +296,9 @@ int qqmc_plan_chunk_sums(const qqmc_plan *plan, int item, int shift, const int64
  * the depth-first tree leaf, 5 vertices, and the flat phase are expanded
  * breadth first), or 1 for one point per lane (orders <= 4: each lane runs
  * the whole Keldysh sum of its own point).  Values <= 0 restore the built-in defaults.  Applies to
- * plans created afterwards; a batched plan uses the tuning of its highest
- * order.
+ * plans created afterwards; in a plan every item runs with its own order's
+ * flat depth, and the items of one flat depth share a launch with the warps
+ * per block of their highest order.
  */
 int qqmc_set_tuning(int precision, int order, int warps_per_block, int flat_vertices);
 int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_vertices);
