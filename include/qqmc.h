@@ -318,7 +318,10 @@ int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_ve
  *   d_counts: DEVICE [n_shifts] uint64 in-domain counts, or NULL;
  *   stream: cudaStream_t or NULL.  The call only enqueues work; the outputs
  *   are ready when the stream reaches that point.
- * Limit: n_shifts * ceil(n_points / 32) <= 465792 (E_INVAL beyond).
+ * Limits (E_INVAL beyond): n_shifts * ceil(n_points / 32) <= 465792; the
+ * whole Schur-tree stack in shared memory, so FP64 orders whose stack
+ * exceeds a block's 227 KB (21 and 22) are refused -- qqmc_integrate or the
+ * mixed precision serve them.  No work-unit cut: one unit per chunk.
  * The first call on a device resolves the array's device address and uploads
  * the kernels' constant tables; make that first call before any stream
  * capture.  Every call shares the array and leaves its contents behind (the
