@@ -320,7 +320,7 @@ int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_ve
  *   are ready when the stream reaches that point.
  * Limits (E_INVAL beyond): n_shifts * ceil(n_points / 32) <= 465792; the
  * whole Schur-tree stack in shared memory, so FP64 orders whose stack
- * exceeds a block's 227 KB (21 and 22) are refused -- qqmc_integrate or the
+ * exceeds a block's 227 KB (21 and 22 with the built-in shapes) are refused -- qqmc_integrate or the
  * mixed precision serve them.  No work-unit cut: one unit per chunk.
  * The first call on a device resolves the array's device address and uploads
  * the kernels' constant tables; make that first call before any stream
