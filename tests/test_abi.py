@@ -19,7 +19,8 @@ def Q():
 
 
 def declared_symbols():
-    txt = open(os.path.join(ROOT, "include", "qqmc.h")).read()
+    with open(os.path.join(ROOT, "include", "qqmc.h")) as f:
+        txt = f.read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(qqmc_[a-z0-9_]+)\s*\(", txt)))
 
