@@ -89,7 +89,7 @@ def lib():
         i64 = ctypes.c_int64
         L.oracle_integrand.argtypes = [ctypes.c_int, i64, dp, ctypes.c_double, dp, dp, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double,
-                                       dp]
+                                       dp, dp]
         L.oracle_sobol.argtypes = [ctypes.c_int, i64, i64, u32p, u32p]
         L.oracle_estimate.argtypes = [ctypes.c_int, i64, i64, u32p, u32p, ctypes.c_double,
                                       ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_double,
@@ -443,10 +443,12 @@ def _cp(a):
 
 
 def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: bool = False, alpha: float = 0.0,
-              col=None):
+              col=None, return_had: bool = False):
     """c(u) of App. E Eq. (integral_gf) at each row of u ([count, n], any time order);
     alpha: quadratic shift of the vertex diagonals (App. E); col: dot-lead tables
-    (gamma g^<_01, gamma g^>_01, gamma g^<_01(0)) for the current, None for the charge."""
+    (gamma g^<_01, gamma g^>_01, gamma g^<_01(0)) for the current, None for the charge.
+    return_abs adds sum_a |term_a|; return_had adds sum_a of the Hadamard bounds
+    prod_rows ||row|| of det M_up and det M_down (finite where det M_down vanishes)."""
     gl, gg, gl0 = tables
     u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)).reshape(-1, n))
     count = u.shape[0]
@@ -454,14 +456,16 @@ def integrand(n: int, u: np.ndarray, t: float, tables, T: float, return_abs: boo
     L = gl_t.size // 2
     out = np.zeros(2 * count)
     ab = np.zeros(count)
+    hd = np.zeros(count)
     cp = _col(col, L)
     rc = lib().oracle_integrand(n, count, _dp(u), t, _dp(gl_t), _dp(gg_t), L, T,
                                 float(np.real(gl0)), float(np.imag(gl0)), _dp(out), _dp(ab), float(alpha),
-                                _cp(cp))
+                                _cp(cp), _dp(hd) if return_had else None)
     if rc != 0:
         raise ValueError("oracle_integrand rejected its arguments")
     val = out[0::2] + 1j * out[1::2]
-    return (val, ab) if return_abs else val
+    ret = (val,) + ((ab,) if return_abs else ()) + ((hd,) if return_had else ())
+    return ret if len(ret) > 1 else val
 
 
 def det(A: np.ndarray) -> complex:

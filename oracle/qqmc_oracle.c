@@ -151,14 +151,28 @@ static cplx det_lu(cplx *A, int m) {
  * with U_k = (0, u_k, a_k); i = 1 (current) when g->cl is set, else 0.  The left Wick determinant is the spin-up one
  * ((n+1)x(n+1), row 0 / column 0 = the measurement points), the right one is
  * spin-down (n x n).  Both are formed from scratch for every a.
- * Also returns sum_a |term| (before the i^n factor) in *abs_sum if non-NULL.
+ * Also returns sum_a |term| (before the i^n factor) in *abs_sum if non-NULL,
+ * and in *had_sum if non-NULL the sum over a of the Hadamard bounds of both
+ * determinants (|det A| <= product of the Euclidean norms of A's rows): the
+ * scale of the rounding error of a determinant, which stays finite where the
+ * determinant itself vanishes.
  * With alpha != 0 the vertex diagonals are shifted (see keldysh_g).
  */
-static cplx integrand(const gf_t *g, int n, const double *u, double t, double *abs_sum) {
+static double hadamard(const cplx *A, int m) {
+    double h = 1.0;
+    for (int r = 0; r < m; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < m; ++c) s += creal(A[r * m + c]) * creal(A[r * m + c]) + cimag(A[r * m + c]) * cimag(A[r * m + c]);
+        h *= sqrt(s);
+    }
+    return h;
+}
+
+static cplx integrand(const gf_t *g, int n, const double *u, double t, double *abs_sum, double *had_sum) {
     cplx up[(ORACLE_MAX_ORDER + 1) * (ORACLE_MAX_ORDER + 1)];
     cplx dn[ORACLE_MAX_ORDER * ORACLE_MAX_ORDER];
     int a[ORACLE_MAX_ORDER];
-    double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0, asum = 0.0;
+    double re_acc = 0.0, re_c = 0.0, im_acc = 0.0, im_c = 0.0, asum = 0.0, hsum = 0.0;
     uint32_t nconf = 1u << n;
     int m = n + 1;
     for (uint32_t conf = 0; conf < nconf; ++conf) {
@@ -178,6 +192,7 @@ static cplx integrand(const gf_t *g, int n, const double *u, double t, double *a
         for (int r = 0; r < n; ++r)
             for (int c = 0; c < n; ++c)
                 dn[r * n + c] = keldysh_g(g, u[r], a[r], u[c], a[c], r == c ? 2 : 0, 0);
+        if (had_sum) hsum += hadamard(up, m) * hadamard(dn, n);
         cplx term = det_lu(up, m) * det_lu(dn, n);
         if (parity) term = -term;
         asum += cabs(term);
@@ -193,26 +208,29 @@ static cplx integrand(const gf_t *g, int n, const double *u, double t, double *a
     cplx in = 1.0;
     for (int k = 0; k < n; ++k) in *= I;
     if (abs_sum) *abs_sum = asum;
+    if (had_sum) *had_sum = hsum;
     return in * sum;
 }
 
 /* ------------------------------ exported API ------------------------------ */
 
 /* Integrand at `count` points; u is count x n row-major (any time order).
- * out: 2*count doubles (re, im) of c(u); abs_out (optional): sum_a |term|.
+ * out: 2*count doubles (re, im) of c(u); abs_out (optional): sum_a |term|;
+ * had_out (optional): sum_a of the Hadamard bounds of the two determinants.
  * col: NULL for the charge, else the dot-lead tables (see make_gf). */
 int oracle_integrand(int n, int64_t count, const double *u, double t,
                      const double *gl, const double *gg, int L, double T,
                      double gl0_re, double gl0_im, double *out, double *abs_out, double alpha,
-                     const double *col) {
+                     const double *col, double *had_out) {
     if (n < 0 || n > ORACLE_MAX_ORDER || L < 2 || count < 0) return -1;
     gf_t g = make_gf(gl, gg, L, T, gl0_re, gl0_im, alpha, col);
     for (int64_t i = 0; i < count; ++i) {
-        double as;
-        cplx v = integrand(&g, n, u + i * n, t, &as);
+        double as, hs;
+        cplx v = integrand(&g, n, u + i * n, t, &as, had_out ? &hs : NULL);
         out[2 * i] = creal(v);
         out[2 * i + 1] = cimag(v);
         if (abs_out) abs_out[i] = as;
+        if (had_out) had_out[i] = hs;
     }
     return 0;
 }
@@ -304,7 +322,7 @@ int oracle_estimate(int n, int64_t i0, int64_t i1, const uint32_t *V, const uint
         double C = pow(tau, (double)n);
         double p = exp(-vsum / tau);
         double w = C / p;
-        cplx val = w * integrand(&g, n, u, t, NULL);
+        cplx val = w * integrand(&g, n, u, t, NULL, NULL);
         double x = creal(val), s = re_acc + x;
         re_c += (fabs(re_acc) >= fabs(x)) ? (re_acc - s) + x : (x - s) + re_acc;
         re_acc = s;
@@ -412,7 +430,7 @@ int oracle_estimate_proj(int n, int64_t i0, int64_t i1, const uint32_t *V, const
         if (!(u[n - 1] > 0.0)) continue;
         ++inside;
         double wgt = pow(tau, (double)n) / exp(-vsum / tau) * jt;
-        cplx val = wgt * integrand(&g, n, u, t, NULL);
+        cplx val = wgt * integrand(&g, n, u, t, NULL, NULL);
         double x = creal(val), s = re_acc + x;
         re_c += (fabs(re_acc) >= fabs(x)) ? (re_acc - s) + x : (x - s) + re_acc;
         re_acc = s;

@@ -393,9 +393,9 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     //  1. a chunk's points go to 2^pbits units of 32 >> pbits points each (pbits <= 5), which costs
     //     nothing but the point generation of the idle lanes;
     //  2. then each point's Keldysh tree goes to 2^split units, each a subtree with the first `split`
-    //     depth-first levels fixed.  Such a unit repeats the pair interpolation, the first
-    //     elimination and its subtree's fixed prefix, so a subtree keeps at least
-    //     2^kMinSubtreeLevels leaves, which holds that repeated work to a few per cent.
+    //     bits of its leaf index fixed (a_2, then two per depth-first level).  Such a unit repeats
+    //     the pair interpolation, the root and its subtree's fixed prefix, so a subtree keeps at
+    //     least 2^kMinSubtreeLevels leaves, which holds that repeated work to a few per cent.
     // The cut depends on the item alone (batched and single runs agree bit for bit).
     constexpr long long kTargetUnits = 1 << 14;
     constexpr int kMinSubtreeLevels = 4;
@@ -408,7 +408,7 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         const qqmc_item &it = items[i];
         lmv[i] = lane_mode(i);
         if (lmv[i]) continue;  // one point per lane: no cut
-        const int levels = it.order - 1 > 5 ? it.order - 1 - 5 : 0;  // depth-first levels above the tree leaf
+        const int levels = tree_leaf_bits(it.order);  // bits of the tree's leaf index
         const long long units = (long long)((it.n_points + kChunk - 1) / kChunk) * it.n_shifts;
         int pb = 0, sp = 0;
         while (pb < 5 && (units << pb) < kTargetUnits) ++pb;

@@ -227,102 +227,119 @@ __device__ __forceinline__ void interp_col(const typename TabT<R>::V *col, doubl
 }
 
 // ----------------------------------------------------------------------------
-// Per-warp shared-memory layout for the Keldysh sum.
+// Pair-block Schur tree for the Keldysh sum.
 //
-// The depth-first tree stops when kTreeLeaf vertices remain (or earlier for
-// small n).  From there, B = Rleaf - RF levels are expanded breadth first
-// (2, 4, ... 2^B sibling matrices, all lanes cooperating), and each lane
-// resolves the last RF vertices of one node along one choice path in
-// registers: 2^B nodes x 2^RF paths = 2^Rleaf <= 32 lanes.
+// Every vertex diagonal of M_down is g^<(0) - i alpha.  With alpha at the
+// occupation Im g^<(0) (the Hartree-cancelling choice of App. E) that diagonal
+// is zero, and at particle-hole symmetry M_down is then skew-symmetric for
+// every Keldysh index vector (g^>(tau) = conj g^<(tau)), so every odd leading
+// minor vanishes.  The tree therefore eliminates the vertices two at a time,
+// (1,2), (3,4), ..., with 2x2 block pivots B whose determinants are the even
+// leading minors, and resolves a lone last vertex (odd n) without a reciprocal.
+//
+// A node with R remaining vertices is an S x S matrix, S = 2R + 2: rows and
+// columns 0, 1 are the two copies of the measurement row/column (a_1 = 0, 1),
+// row 2 + 2i + a is the i-th remaining vertex with Keldysh index a.  Entries
+// joining a row to its own other copy are never read and not formed.
+//
+//   root    vertices 1, 2 eliminated from the pair values for a_2 = s (two
+//           roots), R_r = n - 2 vertices left;
+//   levels  depth first, one vertex pair (a_{2l+1}, a_{2l+2}) per level, four
+//           children per node, down to a leaf of at most kLeafMax vertices;
+//   leaf    breadth-first pair levels (all four children of every node), then
+//           each lane resolves the last F vertices of one node along one
+//           choice path in registers (2^F paths per node).
+// For n <= 6 both roots form one leaf group and there is no walk.
 // ----------------------------------------------------------------------------
-constexpr int kTreeLeaf = 5;
+constexpr int kLeafMax = 6;
 
-template <class R>
-struct WarpSmem {
-    cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l (shared memory)
-    cx<R> *gstack;  // split stack: the levels wider than gs_level in device memory, or null
-    cx<R> *wrow;    // scaled pivot row(s): <= max(2 n_max, 64) entries
-    cx<R> *P;       // vertex k's block at o_k = (k-1)(k+2)/2: P[o_k + j] = g^>(u_j - u_k), 0 <= j < k,
-                    // and P[o_k + k] = measurement-column entry (k, a_k = 1)
-    cx<R> *Rr;      // Rr[o_k + j] = g^<(u_j - u_k); Rr[o_k + k] = column entry (k, a_k = 0)
-    cx<R> *detD;    // per tree level, and (after the last) the sibling leaf's
-    cx<R> *sib;     // the second leaf of a sibling pair (2 kTreeLeaf + 2)^2 entries
-    cx<R> *lr;      // level 0: left and right factors of vertex 1 per block index (4 n_max)
-    cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
-    cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
-    cx<R> *bip;     // pivot reciprocal per child of the level being built (32)
-    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t); device memory with the split stack
-    int gs_level;   // split stack: levels with S > gs_level in device memory
+struct TreeShape {
+    int Rr;     // vertices left after the root block, n - 2
+    int dfl;    // depth-first pair levels below the root
+    int Rleaf;  // vertices left at a leaf
+    int g;      // 1: both roots form one leaf group (no walk)
+    int lbits;  // bits of a leaf's index: a_2, then two per depth-first level
 };
 
-
-// wrow, bdet and bip serve the general cooperative expansion: breadth-first
-// levels (flat depth below the tree leaf) and depth-first steps wider than a
-// warp (children of more than 32 rows, orders >= 18).
-__host__ __device__ inline bool needs_wide_buffers(int n_max, int RF) {
-    const int rl = n_max - 1 < kTreeLeaf ? n_max - 1 : kTreeLeaf;
-    return RF < rl || 2 * (n_max - 1) > 32;
+__host__ __device__ inline TreeShape tree_shape(int n) {
+    TreeShape t;
+    t.Rr = n > 2 ? n - 2 : 0;
+    t.dfl = t.Rr > kLeafMax ? (t.Rr - kLeafMax + 1) / 2 : 0;
+    t.Rleaf = t.Rr - 2 * t.dfl;
+    t.g = t.Rr <= 4 ? 1 : 0;
+    t.lbits = t.g ? 0 : 1 + 2 * t.dfl;
+    return t;
 }
 
-__host__ __device__ inline size_t stack_entries(int n_max) {
+// Breadth-first pair levels below a leaf of Rleaf vertices for the tuned flat
+// depth RF; each lane then resolves F = Rleaf - 2 B vertices (RF - 1 <= F <= RF).
+__host__ __device__ inline int bfs_levels(int Rleaf, int RF) { return Rleaf > RF ? (Rleaf - RF + 1) / 2 : 0; }
+
+__host__ __device__ inline size_t zmax(size_t a, size_t b) { return a > b ? a : b; }
+
+// entries of tree level l (the root level holds both roots when g = 1)
+__host__ __device__ inline size_t level_entries(const TreeShape &t, int l) {
+    const size_t S = 2 * (size_t)(t.Rr - 2 * l) + 2;
+    return (l == 0 && t.g ? 2 : 1) * S * S;
+}
+
+// Tree-stack entries of order n: all levels (part 0), or with the split stack
+// the levels of S <= gs_level (part 1, shared memory) or S > gs_level (part 2,
+// device memory).
+__host__ __device__ inline size_t stack_entries_n(int n, int part, int gs_level) {
+    if (n < 3) return 0;
+    const TreeShape t = tree_shape(n);
     size_t tot = 0;
-    int R0 = n_max - 1;
-    int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
-    for (int l = 0; l <= levels; ++l) {
-        size_t S = 2 * (size_t)(R0 - l) + 2;
-        tot += S * S;
+    for (int l = 0; l <= t.dfl; ++l) {
+        const int S = 2 * (t.Rr - 2 * l) + 2;
+        if (part == 0 || ((S > gs_level) == (part == 2))) tot += level_entries(t, l);
     }
     return tot;
 }
 
-// With the split stack the tree levels wider than gs_level (the top levels,
-// built 1, 2, 4 ... times per point) live in device memory and the narrow, hot
-// bottom levels stay in shared memory.
-__host__ __device__ inline size_t stack_entries_split(int n_max, bool global_part, int gs_level) {
-    size_t tot = 0;
-    int R0 = n_max - 1;
-    int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
-    for (int l = 0; l <= levels; ++l) {
-        size_t S = 2 * (size_t)(R0 - l) + 2;
-        if (((int)S > gs_level) == global_part) tot += S * S;
-    }
-    return tot;
-}
-
-// entries of the breadth-first levels below a tree leaf of Rleaf vertices
-__host__ __device__ inline size_t bfs_entries(int Rleaf, int RF) {
-    size_t tot = 0;
-    int B = Rleaf > RF ? Rleaf - RF : 0;
-    for (int b = 1; b <= B; ++b) {
-        size_t S = 2 * (size_t)(Rleaf - b) + 2;
-        tot += ((size_t)1 << b) * S * S;
-    }
-    return tot;
-}
-
-__host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
+// a launch serves every order up to n_max with one layout
+__host__ __device__ inline size_t stack_cap(int n_max, int part, int gs_level) {
     size_t m = 0;
-    for (int Rl = 0; Rl <= kTreeLeaf && Rl <= n_max - 1; ++Rl) {
-        size_t e = bfs_entries(Rl, RF);
-        m = e > m ? e : m;
+    for (int n = 3; n <= n_max; ++n) m = zmax(m, stack_entries_n(n, part, gs_level));
+    return m;
+}
+
+// Buffers of the breadth-first levels and of the general pair step.
+struct LeafBufs {
+    size_t bfs;   // all breadth-first levels of one leaf group
+    size_t wrow;  // scaled pivot rows, 2 per child column
+    size_t bip;   // B^-1 per child (4 entries)
+    size_t half;  // nodes of the widest breadth-first level (det buffer: two levels)
+};
+
+__host__ __device__ inline LeafBufs leaf_bufs(int n_max, int RF) {
+    LeafBufs m = {0, 0, 0, 0};
+    for (int n = 3; n <= n_max; ++n) {
+        const TreeShape t = tree_shape(n);
+        const int B = bfs_levels(t.Rleaf, RF);
+        size_t nodes = (size_t)1 << t.g, bfs = 0;
+        for (int b = 1; b <= B; ++b) {
+            nodes *= 4;
+            const size_t S = 2 * (size_t)(t.Rleaf - 2 * b) + 2;
+            bfs += nodes * S * S;
+            m.wrow = zmax(m.wrow, 2 * nodes * S);
+            m.bip = zmax(m.bip, 4 * nodes);
+            m.half = zmax(m.half, nodes);
+        }
+        m.bfs = zmax(m.bfs, bfs);
+        for (int l = 1; l <= t.dfl; ++l) {  // depth-first children wider than a warp: the general step
+            const size_t S = 2 * (size_t)(t.Rr - 2 * l) + 2;
+            if (S > 32) {
+                m.wrow = zmax(m.wrow, 2 * S);
+                m.bip = zmax(m.bip, 4);
+            }
+        }
     }
     return m;
 }
 
-// The mixed-precision path builds sibling leaves in pairs (one depth-first step
-// for two leaves: its steps are latency-bound); the FP64 path, bound by its
-// FP64 pipe, gains nothing from it and keeps the shared memory for warps.
-template <class R>
-__host__ __device__ constexpr bool twin_leaves() { return sizeof(R) == 4; }
-
-// the sibling leaf buffer, used when the tree has depth-first levels
-template <class R>
-__host__ __device__ inline size_t sib_entries(int n_max) {
-    return twin_leaves<R>() && n_max - 1 > kTreeLeaf ? (size_t)(2 * kTreeLeaf + 2) * (2 * kTreeLeaf + 2) : 0;
-}
-
-// entries of the packed pair values with the measurement column (P and Rr:
-// blocks of k + 1 entries for the vertices k = 1 .. n_max)
+// packed pair values with the measurement column (P and Rr: blocks of k + 1
+// entries for the vertices k = 1 .. n_max)
 __host__ __device__ inline size_t pair_entries(int n_max) { return (size_t)n_max * (n_max + 3); }
 
 // Shared memory of one warp.  gs_level = 0: the whole tree stack and the point
@@ -330,9 +347,9 @@ __host__ __device__ inline size_t pair_entries(int n_max) { return (size_t)n_max
 // gs_level and the point times in a per-warp slice of device memory.
 template <class R>
 __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_level) {
-    size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
-    size_t c = (gs_level ? stack_entries_split(n_max, false, gs_level) : stack_entries(n_max)) + pair_entries(n_max) +
-               n_max + 1 + sib_entries<R>(n_max) + 4 * (size_t)n_max + bfs_max_entries(n_max, RF) + wide;
+    const LeafBufs lb = leaf_bufs(n_max, RF);
+    size_t c = (gs_level ? stack_cap(n_max, 1, gs_level) : stack_cap(n_max, 0, 0)) + pair_entries(n_max) +
+               n_max + 2 + 8 * (size_t)n_max + lb.bfs + lb.wrow + lb.bip + 2 * lb.half;
     size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
     if (!gs_level) bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
     return (bytes + 127) & ~(size_t)127;
@@ -341,20 +358,20 @@ __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_l
 // Split-stack boundary: the widest levels go to device memory, two rows at a
 // time, until a warp's shared memory lets the SM hold the warps its bound pipe
 // needs (FP64: 6 warps keep GB300's two FP64 lanes per SM busy; mixed: 12).
-// Never the tree leaf (S = 12) or its parent (S = 14): the last depth-first
-// step and the breadth-first and flat phases work in shared memory only.
+// Never a leaf (S <= 14) or its parent (S <= 18): the last depth-first step and
+// the breadth-first and flat phases work in shared memory only.
 template <class R>
 __host__ __device__ inline int gs_level_of(int n_max, int RF) {
     const size_t budget = sizeof(R) == 8 ? 36 * 1024 : 18 * 1024;
-    int lev = 20;
-    while (lev > 2 * kTreeLeaf + 4 && warp_smem_bytes_at<R>(n_max, RF, lev) > budget) lev -= 2;
+    int lev = 2 * n_max;
+    while (lev > 18 && warp_smem_bytes_at<R>(n_max, RF, lev) > budget) lev -= 2;
     return lev;
 }
 
 // Shared memory of one warp; with the split stack (gs) the wide top levels of
-// the Schur tree live in a per-warp slice of device memory (FP64 orders >= 21,
-// whose whole stack exceeds the 227 KB a block can address, and the orders the
-// stack policy names).
+// the tree live in a per-warp slice of device memory (FP64 orders whose whole
+// stack exceeds the 227 KB a block can address, and the orders the stack
+// policy names).
 template <class R>
 __host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF, bool gs = false) {
     return warp_smem_bytes_at<R>(n_max, RF, gs ? gs_level_of<R>(n_max, RF) : 0);
@@ -364,321 +381,483 @@ __host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF, bool gs = f
 // spare entry, and the point times of the chunk.
 template <class R>
 __host__ __device__ inline size_t gstack_entries(int n_max, int RF) {
-    return stack_entries_split(n_max, true, gs_level_of<R>(n_max, RF)) + 1 +
+    return stack_cap(n_max, 2, gs_level_of<R>(n_max, RF)) + 1 +
            (32 * (size_t)(n_max + 1) * sizeof(double) + sizeof(cx<R>) - 1) / sizeof(cx<R>);
 }
 
 template <class R>
+struct WarpSmem {
+    cx<R> *stack;   // tree levels with S <= gs_level (every level without the split stack)
+    cx<R> *gstack;  // split stack: the levels with S > gs_level in device memory, or null
+    cx<R> *P;       // vertex k's block at o_k = (k-1)(k+2)/2: P[o_k + j] = g^>(u_j - u_k), 0 <= j < k,
+                    // and P[o_k + k] = measurement-column entry (k, a_k = 1)
+    cx<R> *Rr;      // Rr[o_k + j] = g^<(u_j - u_k); Rr[o_k + k] = column entry (k, a_k = 0)
+    cx<R> *detD;    // det M_down of the eliminated vertices per tree level (level 0: both roots when g = 1)
+    cx<R> *lr;      // root: per block index L(., 0), L(., 1), B^-1 R(., 0), B^-1 R(., 1) (8 entries)
+    cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
+    cx<R> *wrow;    // general pair step: B^-1 (row p; row q) per child column
+    cx<R> *bip;     // general pair step: B^-1 per child
+    cx<R> *bdet;    // det M_down per breadth-first node, two levels of `half` nodes
+    int half;
+    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t); device memory with the split stack
+    int gs_level;   // split stack: levels with S > gs_level in device memory
+};
+
+template <class R>
 __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack = nullptr) {
     WarpSmem<R> w;
+    const LeafBufs lb = leaf_bufs(n_max, RF);
     cx<R> *p = reinterpret_cast<cx<R> *>(base);
     w.gstack = gstack;
     w.gs_level = gstack ? gs_level_of<R>(n_max, RF) : 0;
     w.stack = p;
-    p += gstack ? stack_entries_split(n_max, false, w.gs_level) : stack_entries(n_max);
+    p += gstack ? stack_cap(n_max, 1, w.gs_level) : stack_cap(n_max, 0, 0);
     const int npair = n_max * (n_max + 3) / 2;
     w.P = p;
     p += npair;
     w.Rr = p;
     p += npair;
     w.detD = p;
-    p += n_max + 1;
-    w.sib = p;
-    p += sib_entries<R>(n_max);
+    p += n_max + 2;
     w.lr = p;
-    p += 4 * n_max;
+    p += 8 * n_max;
     w.bfs = p;
-    p += bfs_max_entries(n_max, RF);
-    w.wrow = w.bdet = w.bip = nullptr;
-    if (needs_wide_buffers(n_max, RF)) {
-        w.wrow = p;
-        p += 2 * n_max > 64 ? 2 * n_max : 64;
-        w.bdet = p;
-        p += 64;
-        w.bip = p;
-        p += 32;
-    }
+    p += lb.bfs;
+    w.wrow = p;
+    p += lb.wrow;
+    w.bip = p;
+    p += lb.bip;
+    w.bdet = p;
+    p += 2 * lb.half;
+    w.half = (int)lb.half;
     size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
-    w.upt = gstack ? reinterpret_cast<double *>(gstack + stack_entries_split(n_max, true, w.gs_level) + 1)
+    w.upt = gstack ? reinterpret_cast<double *>(gstack + stack_cap(n_max, 2, w.gs_level) + 1)
                    : reinterpret_cast<double *>(base + off);
     return w;
 }
 
-// Leaf term after the last vertex p: with pivot pv and the copies' entries,
-//   det' = det pv,   S_aa = m_aa - m_ap m_pa / pv   (a = copy 0, 1),
+template <class R>
+__device__ __forceinline__ cx<R> sel(int bit, cx<R> one, cx<R> zero) {
+    return mk<R>(bit ? one.re : zero.re, bit ? one.im : zero.im);
+}
+template <class R>
+__device__ __forceinline__ cx<R> cneg(cx<R> a) {
+    return mk<R>(-a.re, -a.im);
+}
+template <class R>
+__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
+    return mk<R>(a.re - b.re, a.im - b.im);
+}
+// c + a * b
+template <class R>
+__device__ __forceinline__ cx<R> cfma(cx<R> c, cx<R> a, cx<R> b) {
+    return mk<R>(fmaR(a.re, b.re, fmaR(-a.im, b.im, c.re)), fmaR(a.re, b.im, fmaR(a.im, b.re, c.im)));
+}
+
+// packed offset of vertex k's block
+__device__ __forceinline__ int vblk(int k) { return (int)((unsigned)((k - 1) * (k + 2)) >> 1); }
+
+// Leaf term after a lone last vertex p: with pivot pv and the copies' entries,
+//   det' = det pv,   S_cc = m_cc - m_cp m_pc / pv   (c = copy 0, 1),
 //   det'^2 (S_00 - S_11) = det^2 pv (pv (m_00 - m_11) - (m_0p m_p0 - m_1p m_p1)):
-// the last elimination needs no reciprocal.
+// no reciprocal, so a vanishing pivot (det M_down = 0) gives a zero term.
 template <class R>
 __device__ __forceinline__ cx<R> leaf_term(cx<R> m00, cx<R> m11, cx<R> m0p, cx<R> mp0, cx<R> m1p, cx<R> mp1, cx<R> pv,
                                            cx<R> det) {
-    const cx<R> q = cfms(cmul(m0p, mp0), m1p, mp1);                        // m0p mp0 - m1p mp1
-    const cx<R> r = cfms(q, pv, mk<R>(m00.re - m11.re, m00.im - m11.im));  // q - pv (m00 - m11)
-    return cmul(cmul(det, det), cmul(pv, mk<R>(-r.re, -r.im)));
+    const cx<R> q = cfms(cmul(m0p, mp0), m1p, mp1);  // m0p mp0 - m1p mp1
+    const cx<R> r = cfms(q, pv, csub(m00, m11));      // q - pv (m00 - m11)
+    return cmul(cmul(det, det), cmul(pv, cneg(r)));
+}
+
+// Leaf term after the last vertex pair (p, q), also without a reciprocal:
+//   delta = det B,  x_c = (m_cp, m_cq) adj(B) (m_pc, m_qc)^T,
+//   det'^2 (S_00 - S_11) = det^2 delta (delta (m_00 - m_11) - (x_0 - x_1)).
+template <class R>
+__device__ __forceinline__ cx<R> leaf_pair(cx<R> m00, cx<R> m11, cx<R> m0p, cx<R> m0q, cx<R> mp0, cx<R> mq0,
+                                           cx<R> m1p, cx<R> m1q, cx<R> mp1, cx<R> mq1, cx<R> mpp, cx<R> mpq,
+                                           cx<R> mqp, cx<R> mqq, cx<R> det) {
+    const cx<R> del = cfms(cmul(mpp, mqq), mpq, mqp);
+    // adj(B) (m_pc; m_qc) = (mqq m_pc - mpq m_qc; mpp m_qc - mqp m_pc)
+    const cx<R> v00 = cfms(cmul(mqq, mp0), mpq, mq0), v01 = cfms(cmul(mpp, mq0), mqp, mp0);
+    const cx<R> v10 = cfms(cmul(mqq, mp1), mpq, mq1), v11 = cfms(cmul(mpp, mq1), mqp, mp1);
+    const cx<R> x0 = cfma(cmul(m0p, v00), m0q, v01);
+    const cx<R> x1 = cfma(cmul(m1p, v10), m1q, v11);
+    const cx<R> r = cfms(csub(x0, x1), del, csub(m00, m11));  // (x0 - x1) - delta (m00 - m11)
+    return cmul(cmul(det, det), cmul(del, cneg(r)));
+}
+
+// Register tail of a path: m is M x M (copies 0, 1 and M - 2 <= 3 vertices).
+template <class R, int M>
+__device__ __forceinline__ cx<R> reg_tail(cx<R> (&m)[M][M], cx<R> det) {
+    if constexpr (M == 3) {
+        return leaf_term(m[0][0], m[1][1], m[0][2], m[2][0], m[1][2], m[2][1], m[2][2], det);
+    } else if constexpr (M == 4) {
+        return leaf_pair(m[0][0], m[1][1], m[0][2], m[0][3], m[2][0], m[3][0], m[1][2], m[1][3], m[2][1], m[3][1],
+                         m[2][2], m[2][3], m[3][2], m[3][3], det);
+    } else {
+        static_assert(M == 5, "at most three vertices after the first pair");
+        // pair (2, 3) with its pivot, then the lone vertex 4
+        const cx<R> del = cfms(cmul(m[2][2], m[3][3]), m[2][3], m[3][2]);
+        det = cmul(det, del);
+        const cx<R> id = crcp(del);
+        const int keep[3] = {0, 1, 4};
+        cx<R> w0[3], w1[3], t[3][3];
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            const cx<R> e2 = m[2][keep[y]], e3 = m[3][keep[y]];
+            w0[y] = cmul(cfms(cmul(m[3][3], e2), m[2][3], e3), id);
+            w1[y] = cmul(cfms(cmul(m[2][2], e3), m[3][2], e2), id);
+        }
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+            for (int y = 0; y < 3; ++y) {
+                if (x < 2 && y < 2 && x != y) continue;
+                t[x][y] = cfms(cfms(m[keep[x]][keep[y]], m[keep[x]][2], w0[y]), m[keep[x]][3], w1[y]);
+            }
+        return leaf_term(t[0][0], t[1][1], t[0][2], t[2][0], t[1][2], t[2][1], t[2][2], det);
+    }
 }
 
 // Flat phase: one lane resolves the F remaining vertices of node matrix E
-// (size S = 2F + 2) along the choice path `path` (bit q = Keldysh index of the
-// q-th remaining vertex).  The first elimination is fused with the gather;
-// the rest runs on an (F+1) x (F+1) register matrix whose rows and columns
-// are {copy a_1 = 0, copy a_1 = 1, remaining vertices}.
-template <class R, int F, int STRIDE = 1>
-__device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &acc_re,
-                                           Acc<R> &acc_im) {
+// (S = 2F + 2) along the choice path `path` (bit q = Keldysh index of the q-th
+// remaining vertex) and returns its (unsigned) leaf term.  F <= 2: the leaf
+// formulas straight from E.  F >= 3: the first pair is eliminated with its
+// pivot while the rows and columns of the path are gathered into registers.
+template <class R, int F>
+__device__ __forceinline__ cx<R> flat_term(const cx<R> *E, cx<R> det, int path) {
     constexpr int S = 2 * F + 2;
-    if (F == 0) {
-        cx<R> dd = cmul(detD, detD);
-        cx<R> diff = mk<R>(E[0].re - E[(S + 1) * STRIDE].re, E[0].im - E[(S + 1) * STRIDE].im);
-        cx<R> term = cmul(dd, diff);
-        if (parity) term = mk<R>(-term.re, -term.im);
-        acc_re.add(term.re);
-        acc_im.add(term.im);
-        return;
-    }
-    constexpr int M = F + 1;  // after the first elimination: 2 copies + F-1 vertices
-    int idx[M];
-    idx[0] = 0;
-    idx[1] = 1;
+    const int p = 2 + (path & 1);
+    if constexpr (F == 1) {
+        return leaf_term(E[0], E[S + 1], E[p], E[p * S], E[S + p], E[p * S + 1], E[p * S + p], det);
+    } else {
+        const int q = 4 + ((path >> 1) & 1);
+        if constexpr (F == 2) {
+            return leaf_pair(E[0], E[S + 1], E[p], E[q], E[p * S], E[q * S], E[S + p], E[S + q], E[p * S + 1],
+                             E[q * S + 1], E[p * S + p], E[p * S + q], E[q * S + p], E[q * S + q], det);
+        } else {
+            constexpr int M = F;  // copies + the F - 2 vertices after the first pair
+            int idx[M];
+            idx[0] = 0;
+            idx[1] = 1;
 #pragma unroll
-    for (int q = 1; q < F; ++q) idx[q + 1] = 2 + 2 * q + ((path >> q) & 1);
-    const int p0 = 2 + (path & 1);
-    cx<R> piv = E[(p0 * S + p0) * STRIDE];
-    detD = cmul(detD, piv);
-    cx<R> ip = crcp(piv);
-    cx<R> m[M][M];
-    cx<R> prow[M];
-#pragma unroll
-    for (int y = 0; y < M; ++y) prow[y] = cmul(E[(p0 * S + idx[y]) * STRIDE], ip);
-#pragma unroll
-    for (int x = 0; x < M; ++x) {
-        cx<R> cf = E[(idx[x] * S + p0) * STRIDE];
-#pragma unroll
-        for (int y = 0; y < M; ++y) {
-            if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
-            m[x][y] = cfms(E[(idx[x] * S + idx[y]) * STRIDE], cf, prow[y]);
-        }
-    }
-#pragma unroll
-    for (int q = 1; q < F - 1; ++q) {
-        const int p = q + 1;
-        cx<R> pv = m[p][p];
-        detD = cmul(detD, pv);
-        cx<R> iq = crcp(pv);
-#pragma unroll
-        for (int y = 0; y < M; ++y)
-            if (y < 2 || y > p) m[p][y] = cmul(m[p][y], iq);
-#pragma unroll
-        for (int x = 0; x < M; ++x) {
-            if (!(x < 2 || x > p)) continue;
+            for (int r = 2; r < M; ++r) idx[r] = 2 + 2 * r + ((path >> r) & 1);
+            const cx<R> bpp = E[p * S + p], bpq = E[p * S + q], bqp = E[q * S + p], bqq = E[q * S + q];
+            const cx<R> del = cfms(cmul(bpp, bqq), bpq, bqp);
+            det = cmul(det, del);
+            const cx<R> id = crcp(del);
+            cx<R> w0[M], w1[M], m[M][M];
 #pragma unroll
             for (int y = 0; y < M; ++y) {
-                if (!(y < 2 || y > p)) continue;
-                if (x < 2 && y < 2 && x != y) continue;
-                m[x][y] = cfms(m[x][y], m[x][p], m[p][y]);
+                const cx<R> epy = E[p * S + idx[y]], eqy = E[q * S + idx[y]];
+                w0[y] = cmul(cfms(cmul(bqq, epy), bpq, eqy), id);
+                w1[y] = cmul(cfms(cmul(bpp, eqy), bqp, epy), id);
             }
+#pragma unroll
+            for (int x = 0; x < M; ++x) {
+                const cx<R> exp = E[idx[x] * S + p], exq = E[idx[x] * S + q];
+#pragma unroll
+                for (int y = 0; y < M; ++y) {
+                    if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
+                    m[x][y] = cfms(cfms(E[idx[x] * S + idx[y]], exp, w0[y]), exq, w1[y]);
+                }
+            }
+            return reg_tail<R, M>(m, det);
         }
     }
-    cx<R> term;
-    if constexpr (F >= 2) {  // the last vertex is eliminated inside the leaf term
-        term = leaf_term(m[0][0], m[1][1], m[0][M - 1], m[M - 1][0], m[1][M - 1], m[M - 1][1], m[M - 1][M - 1], detD);
-    } else {  // F = 1: the gather step eliminated the only vertex
-        term = cmul(cmul(detD, detD), mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im));
-    }
-    parity ^= __popc(path) & 1;
-    if (parity) term = mk<R>(-term.re, -term.im);
-    acc_re.add(term.re);
-    acc_im.add(term.im);
 }
 
-template <class R, int RF>
-__device__ __forceinline__ void flat_dispatch(int Rf, const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &ar,
-                                              Acc<R> &ai) {
-    switch (Rf) {  // Rf <= RF
-        case 0: flat_phase<R, 0>(E, detD, parity, path, ar, ai); break;
-        case 1: flat_phase<R, 1>(E, detD, parity, path, ar, ai); break;
-        case 2: flat_phase<R, 2>(E, detD, parity, path, ar, ai); break;
-        case 3: if (RF >= 3) flat_phase<R, (RF >= 3 ? 3 : 0)>(E, detD, parity, path, ar, ai); break;
-        case 4: if (RF >= 4) flat_phase<R, (RF >= 4 ? 4 : 0)>(E, detD, parity, path, ar, ai); break;
-        default: if (RF >= 5) flat_phase<R, (RF >= 5 ? 5 : 0)>(E, detD, parity, path, ar, ai); break;
+template <class R, int RFMAX>
+__device__ __forceinline__ cx<R> flat_dispatch(int F, const cx<R> *E, cx<R> det, int path) {
+    switch (F) {  // 1 <= F <= RFMAX
+        case 1: return flat_term<R, 1>(E, det, path);
+        case 2: return flat_term<R, 2>(E, det, path);
+        case 3: if (RFMAX >= 3) return flat_term<R, (RFMAX >= 3 ? 3 : 2)>(E, det, path); break;
+        case 4: if (RFMAX >= 4) return flat_term<R, (RFMAX >= 4 ? 4 : 2)>(E, det, path); break;
+        default: if (RFMAX >= 5) return flat_term<R, (RFMAX >= 5 ? 5 : 2)>(E, det, path); break;
     }
+    return mk<R>(0, 0);
 }
 
-// One cooperative elimination: child(ren) of S x S parent matrices.  Child j
-// of the new level comes from parent j >> 1 with Keldysh index a = j & 1 on the
-// parent's first remaining vertex (pivot row/column 2 + a).  The new matrices
-// are (S-2) x (S-2), all children contiguous in `out`.
+// Root for a_2 = s: vertices 1 and 2 eliminated with the pivot block
+// B = [[dv, M(1,2)], [M(2,1), dv]] (M(1,2) and M(2,1) follow a_2; vertex 1's own
+// index only reaches the measurement row and column, so the two copies carry
+// it).  Block index i: 0 = the copies, i >= 1 = vertex i + 2 with both indices.
+// Entry (x, y) = base(x, y) - L_x . B^-1 R_y with L_x = (M(x,1), M(x,2)) and
+// R_y = (M(1,y), M(2,y)).  Writes the S x S root (S = 2n - 2) and det B.
 template <class R>
-__device__ __forceinline__ void expand_level(const cx<R> *__restrict__ in, int S, int nchild, int first_a,
-                                             cx<R> *__restrict__ out, const cx<R> *detD_in, cx<R> *detD_out,
-                                             cx<R> *__restrict__ wrow, cx<R> *ip_buf, int lane) {
-    const int S2 = S - 2;
-    // child pivots: reciprocal and running det M_down
-    for (int j = lane; j < nchild; j += 32) {
-        const int a = nchild == 1 ? first_a : (j & 1);
-        const int pj = nchild == 1 ? 0 : (j >> 1);
-        const int pr = 2 + a;
-        cx<R> piv = in[(size_t)pj * S * S + pr * S + pr];
-        ip_buf[j] = crcp(piv);
-        detD_out[j] = cmul(detD_in[pj], piv);
+__device__ void build_root(const WarpSmem<R> &ws, int n, int s, cx<R> d, cx<R> dv, cx<R> *__restrict__ out,
+                           cx<R> *det_out, int lane) {
+    const int nb = n - 1, S = 2 * nb;
+    const cx<R> m12 = sel<R>(s, ws.Rr[3], ws.P[3]);
+    const cx<R> m21 = nconj(sel<R>(s, ws.P[3], ws.Rr[3]));
+    const cx<R> del = cfms(cmul(dv, dv), m12, m21);
+    const cx<R> id = crcp(del);
+    if (lane < nb) {
+        cx<R> l00, l01, l10, l11, r00, r01, r10, r11;  // l_a = L(i, a), r_b = R(i, b), two components each
+        if (lane == 0) {
+            l00 = ws.P[0];  // M(0,1), a_1 = 0
+            l10 = ws.Rr[0];
+            l01 = l11 = sel<R>(s, ws.Rr[2], ws.P[2]);  // M(0,2)
+            r00 = ws.Rr[1];  // M(1,0), a_1 = 0
+            r10 = ws.P[1];
+            r01 = r11 = sel<R>(s, ws.P[4], ws.Rr[4]);  // M(2,0)
+        } else {
+            const int o = vblk(lane + 2);
+            l00 = nconj(ws.Rr[o + 1]);  // M(v,1), a_v = 0
+            l10 = nconj(ws.P[o + 1]);
+            l01 = nconj(ws.Rr[o + 2]);  // M(v,2)
+            l11 = nconj(ws.P[o + 2]);
+            r00 = ws.P[o + 1];  // M(1,v), a_v = 0
+            r10 = ws.Rr[o + 1];
+            r01 = ws.P[o + 2];  // M(2,v)
+            r11 = ws.Rr[o + 2];
+        }
+        // B^-1 = (1 / delta) [[dv, -M12], [-M21, dv]]
+        cx<R> *lr = ws.lr + 8 * lane;
+        lr[0] = l00;
+        lr[1] = l01;
+        lr[2] = l10;
+        lr[3] = l11;
+        lr[4] = cmul(cfms(cmul(dv, r00), m12, r01), id);
+        lr[5] = cmul(cfms(cmul(dv, r01), m21, r00), id);
+        lr[6] = cmul(cfms(cmul(dv, r10), m12, r11), id);
+        lr[7] = cmul(cfms(cmul(dv, r11), m21, r10), id);
     }
     __syncwarp();
-    // scaled pivot rows
-    for (int q = lane; q < nchild * S2; q += 32) {
-        const int j = q / S2, c2 = q - j * S2;
-        const int a = nchild == 1 ? first_a : (j & 1);
-        const int pj = nchild == 1 ? 0 : (j >> 1);
-        const int pr = 2 + a;
-        const int c = c2 < 2 ? c2 : c2 + 2;
-        wrow[q] = cmul(in[(size_t)pj * S * S + pr * S + c], ip_buf[j]);
+    // lane -> block (bx, by), stepped by 32 blocks without divisions.  The base entry follows
+    // the later vertex's index: above the diagonal (row 0: the measurement row) the column's,
+    // below it (column 0: the measurement column, stored as is) the row's.
+    const int sq = 32 / nb, sr = 32 - sq * nb;
+    int bx = lane / nb, by = lane - bx * nb;
+    for (int bid = lane; bid < nb * nb; bid += 32) {
+        const bool up = bx < by, diag = bx == by;
+        const int v = bx + 2, w = by + 2;
+        const int idx = up ? vblk(w) + (bx ? v : 0) : vblk(v) + (by ? w : v);
+        const cx<R> vP = ws.P[diag ? 0 : idx], vR = ws.Rr[diag ? 0 : idx];
+        const cx<R> *lx = ws.lr + 8 * bx, *wy = ws.lr + 8 * by + 4;
+        const R sg = (!up && by) ? R(-1) : R(1);  // lower entries of vertex pairs: -conj
+        const cx<R> lo0 = mk<R>(sg * vR.re, vR.im), lo1 = mk<R>(sg * vP.re, vP.im);
+        const cx<R> dd = bx == 0 ? d : dv;
+        const cx<R> b00 = diag ? dd : (up ? vP : lo0), b01 = up ? vR : lo0;
+        const cx<R> b10 = up ? vP : lo1, b11 = diag ? dd : (up ? vR : lo1);
+        cx<R> *o = out + (2 * bx) * S + 2 * by;
+        o[0] = cfms(cfms(b00, lx[0], wy[0]), lx[1], wy[1]);
+        o[S + 1] = cfms(cfms(b11, lx[2], wy[2]), lx[3], wy[3]);
+        if (!diag) {
+            o[1] = cfms(cfms(b01, lx[0], wy[2]), lx[1], wy[3]);
+            o[S] = cfms(cfms(b10, lx[2], wy[0]), lx[3], wy[1]);
+        }
+        by += sr;
+        bx += sq;
+        if (by >= nb) {
+            by -= nb;
+            ++bx;
+        }
     }
-    __syncwarp();
-    // Only entries that are ever read are built: a choice path takes one copy of every vertex
-    // (and one measurement copy per determinant), so the entry joining row r2 to its row's
-    // other copy, column r2 ^ 1, is never used (1 / S2 of the updates).  lane -> (child j,
-    // row r2, used column cc of W = S2 - 1) stepped by 32 entries without divisions.
-    const int W = S2 - 1;
-    const int dr = 32 / W, dc = 32 - dr * W;
-    int r2 = lane / W, cc = lane - r2 * W, j = 0;
-    while (r2 >= S2) { r2 -= S2; ++j; }
-    const int total = nchild * S2 * W;
-    for (int e = lane; e < total; e += 32) {
-        const int c2 = cc < (r2 ^ 1) ? cc : cc + 1;
-        const int a = nchild == 1 ? first_a : (j & 1);
-        const int pj = nchild == 1 ? 0 : (j >> 1);
-        const int pr = 2 + a;
-        const int r = r2 < 2 ? r2 : r2 + 2;
-        const int c = c2 < 2 ? c2 : c2 + 2;
-        const cx<R> *P = in + (size_t)pj * S * S;
-        out[((size_t)j * S2 + r2) * S2 + c2] = cfms(P[r * S + c], P[r * S + pr], wrow[j * S2 + c2]);
-        cc += dc;
-        r2 += dr;
-        if (cc >= W) { cc -= W; ++r2; }
-        while (r2 >= S2) { r2 -= S2; ++j; }
-    }
+    if (lane == 0) *det_out = del;
     __syncwarp();
 }
 
-// Single child (a depth-first step, S - 2 <= 32): each lane owns one column of
-// the child and a fixed row offset, so the scaled pivot-row entry of its
-// column stays in a register and the pivot-column entry of a row is a
-// broadcast load.  A step is latency-bound (a few hundred flops per warp), so
-// every load of the step is issued before the pivot's reciprocal is formed,
-// and the lane mapping needs no division.
-//
-// Children of 2T = 12, 14 or 16 rows (the deep, frequent steps): lanes 0-15
-// take the even rows, lanes 16-31 the odd rows, column c2 = lane & 15.
+// One child of a depth-first pair step: the vertices in rows 2-3 and 4-5 of
+// the S x S parent fixed to (a, b), pivot block B = E[{p,q},{p,q}] (p = 2 + a,
+// q = 4 + b); the (S - 4) x (S - 4) child keeps parent rows/columns 0, 1, 6, 7,
+// ...  Entry E_xy - E_xp W0_y - E_xq W1_y with (W0; W1) = B^-1 (E_p.; E_q.).
+// A step is latency-bound, so every load is issued before the pivot's
+// reciprocal.  Children of 2T = 12, 14 or 16 rows: lanes 0-15 take the even
+// rows, lanes 16-31 the odd rows, column c2 = lane & 15.
 template <class R, int T>
-__device__ __forceinline__ void expand_one_t(const cx<R> *__restrict__ in, int a, cx<R> *__restrict__ out,
-                                             const cx<R> *detD_in, cx<R> *detD_out, int lane) {
-    constexpr int S2 = 2 * T, S = S2 + 2;
-    const int pr = 2 + a;
+__device__ __forceinline__ void pair_one_t(const cx<R> *__restrict__ in, int a, int b, cx<R> *__restrict__ out,
+                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    constexpr int S2 = 2 * T, S = S2 + 4;
+    const int p = 2 + a, q = 4 + b;
     const int c2 = lane & 15, rsub = lane >> 4;
     const bool act = c2 < S2;
-    const int c = c2 < 2 ? c2 : c2 + 2;
-    const cx<R> piv = in[pr * S + pr];
-    cx<R> prc = mk<R>(0, 0), ev[T], cv[T];
+    const int c = c2 < 2 ? c2 : c2 + 4;
+    const cx<R> bpp = in[p * S + p], bpq = in[p * S + q], bqp = in[q * S + p], bqq = in[q * S + q];
+    cx<R> epc = mk<R>(0, 0), eqc = mk<R>(0, 0), ev[T], ep[T], eq[T];
 #pragma unroll
-    for (int t = 0; t < T; ++t) ev[t] = cv[t] = mk<R>(0, 0);
+    for (int t = 0; t < T; ++t) ev[t] = ep[t] = eq[t] = mk<R>(0, 0);
     if (act) {
-        prc = in[pr * S + c];
+        epc = in[p * S + c];
+        eqc = in[q * S + c];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int r2 = rsub + 2 * t;
-            const int r = r2 < 2 ? r2 : r2 + 2;
+            const int r = r2 < 2 ? r2 : r2 + 4;
             ev[t] = in[r * S + c];
-            cv[t] = in[r * S + pr];
+            ep[t] = in[r * S + p];
+            eq[t] = in[r * S + q];
         }
     }
-    const cx<R> ip = crcp(piv);
-    if (lane == 0) *detD_out = cmul(*detD_in, piv);
+    const cx<R> del = cfms(cmul(bpp, bqq), bpq, bqp);
+    const cx<R> id = crcp(del);
+    if (lane == 0) *detD_out = cmul(*detD_in, del);
     if (act) {
-        const cx<R> w = cmul(prc, ip);
+        const cx<R> w0 = cmul(cfms(cmul(bqq, epc), bpq, eqc), id);
+        const cx<R> w1 = cmul(cfms(cmul(bpp, eqc), bqp, epc), id);
 #pragma unroll
-        for (int t = 0; t < T; ++t) out[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv[t], w);
+        for (int t = 0; t < T; ++t) out[(rsub + 2 * t) * S2 + c2] = cfms(cfms(ev[t], ep[t], w0), eq[t], w1);
     }
     __syncwarp();
 }
 
-// Both children (a = 0 into out0, a = 1 into out1) of a parent of 2T + 2 rows:
-// the last depth-first step, whose two children are consecutive leaves.  The
-// parent entries are loaded once for both, and both pivots' latencies overlap.
-template <class R, int T>
-__device__ __forceinline__ void expand_both_t(const cx<R> *__restrict__ in, cx<R> *__restrict__ out0,
-                                              cx<R> *__restrict__ out1, const cx<R> *detD_in, cx<R> *detD_out0,
-                                              cx<R> *detD_out1, int lane) {
-    constexpr int S2 = 2 * T, S = S2 + 2;
-    const int c2 = lane & 15, rsub = lane >> 4;
-    const bool act = c2 < S2;
-    const int c = c2 < 2 ? c2 : c2 + 2;
-    const cx<R> piv0 = in[2 * S + 2], piv1 = in[3 * S + 3];
-    cx<R> prc0 = mk<R>(0, 0), prc1 = mk<R>(0, 0), ev[T], cv0[T], cv1[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) ev[t] = cv0[t] = cv1[t] = mk<R>(0, 0);
-    if (act) {
-        prc0 = in[2 * S + c];
-        prc1 = in[3 * S + c];
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int r2 = rsub + 2 * t;
-            const int r = r2 < 2 ? r2 : r2 + 2;
-            ev[t] = in[r * S + c];
-            cv0[t] = in[r * S + 2];
-            cv1[t] = in[r * S + 3];
-        }
-    }
-    const cx<R> ip0 = crcp(piv0), ip1 = crcp(piv1);
-    if (lane == 0) *detD_out0 = cmul(*detD_in, piv0);
-    if (lane == 1) *detD_out1 = cmul(*detD_in, piv1);
-    if (act) {
-        const cx<R> w0 = cmul(prc0, ip0), w1 = cmul(prc1, ip1);
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            out0[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv0[t], w0);
-            out1[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv1[t], w1);
-        }
-    }
-    __syncwarp();
-}
-
-// Wider children (S - 2 = 18 .. 32 rows, the rare top steps): lane = column,
-// rows in batches (eight in FP32, four in FP64) with the batch's loads issued first.
+// Wider children (S - 4 = 18 .. 32 rows): lane = column, rows in batches
+// (eight in FP32, four in FP64) with the batch's loads issued first.
 template <class R>
-__device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
-                                                const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+__device__ __forceinline__ void pair_one_wide(const cx<R> *__restrict__ in, int S, int a, int b,
+                                              cx<R> *__restrict__ out, const cx<R> *detD_in, cx<R> *detD_out,
+                                              int lane) {
     constexpr int NB = sizeof(R) == 4 ? 8 : 4;  // rows per batch (FP64: register budget)
-    const int S2 = S - 2;
-    const int pr = 2 + a;
-    const cx<R> piv = in[pr * S + pr];
-    const cx<R> ip = crcp(piv);
-    if (lane == 0) *detD_out = cmul(*detD_in, piv);
+    const int S2 = S - 4;
+    const int p = 2 + a, q = 4 + b;
+    const cx<R> bpp = in[p * S + p], bpq = in[p * S + q], bqp = in[q * S + p], bqq = in[q * S + q];
+    const cx<R> del = cfms(cmul(bpp, bqq), bpq, bqp);
+    const cx<R> id = crcp(del);
+    if (lane == 0) *detD_out = cmul(*detD_in, del);
     if (lane < S2) {
-        const int c = lane < 2 ? lane : lane + 2;
-        const cx<R> w = cmul(in[pr * S + c], ip);
+        const int c = lane < 2 ? lane : lane + 4;
+        const cx<R> epc = in[p * S + c], eqc = in[q * S + c];
+        const cx<R> w0 = cmul(cfms(cmul(bqq, epc), bpq, eqc), id);
+        const cx<R> w1 = cmul(cfms(cmul(bpp, eqc), bqp, epc), id);
         for (int r0 = 0; r0 < S2; r0 += NB) {
-            cx<R> ev[NB], cv[NB];
+            cx<R> ev[NB], ep[NB], eq[NB];
 #pragma unroll
             for (int t = 0; t < NB; ++t) {
                 const int r2 = r0 + t < S2 ? r0 + t : S2 - 1;  // a clamped duplicate of the last row
-                const int r = r2 < 2 ? r2 : r2 + 2;
+                const int r = r2 < 2 ? r2 : r2 + 4;
                 ev[t] = in[r * S + c];
-                cv[t] = in[r * S + pr];
+                ep[t] = in[r * S + p];
+                eq[t] = in[r * S + q];
             }
 #pragma unroll
             for (int t = 0; t < NB; ++t)
-                if (r0 + t < S2) out[(r0 + t) * S2 + lane] = cfms(ev[t], cv[t], w);
+                if (r0 + t < S2) out[(r0 + t) * S2 + lane] = cfms(cfms(ev[t], ep[t], w0), eq[t], w1);
         }
     }
     __syncwarp();
 }
 
+// General cooperative pair step.  nchild = 4 nparent children of the S x S
+// parents (contiguous in `in`): child j from parent j >> 2 with
+// (a, b) = ((j >> 1) & 1, j & 1); or one child (nchild = 1) with (a1, b1).  The
+// (S-4) x (S-4) children are contiguous in `out`.  Breadth-first levels, and
+// depth-first children wider than a warp.
 template <class R>
-__device__ __forceinline__ void expand_one(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
-                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
-    switch (S - 2) {
-        case 12: expand_one_t<R, 6>(in, a, out, detD_in, detD_out, lane); break;
-        case 14: expand_one_t<R, 7>(in, a, out, detD_in, detD_out, lane); break;
-        case 16: expand_one_t<R, 8>(in, a, out, detD_in, detD_out, lane); break;
-        default: expand_one_wide<R>(in, S, a, out, detD_in, detD_out, lane); break;
+__device__ void pair_level(const cx<R> *__restrict__ in, int S, int nchild, int a1, int b1, cx<R> *__restrict__ out,
+                           const cx<R> *detD_in, cx<R> *detD_out, cx<R> *__restrict__ wrow, cx<R> *binv, int lane) {
+    const int S2 = S - 4;
+    // pivot blocks: B^-1 and the running det M_down per child
+    for (int j = lane; j < nchild; j += 32) {
+        const int a = nchild == 1 ? a1 : (j >> 1) & 1, b = nchild == 1 ? b1 : j & 1;
+        const int pj = nchild == 1 ? 0 : j >> 2;
+        const cx<R> *E = in + (size_t)pj * S * S;
+        const int p = 2 + a, q = 4 + b;
+        const cx<R> bpp = E[p * S + p], bpq = E[p * S + q], bqp = E[q * S + p], bqq = E[q * S + q];
+        const cx<R> del = cfms(cmul(bpp, bqq), bpq, bqp);
+        const cx<R> id = crcp(del);
+        binv[4 * j] = cmul(bqq, id);
+        binv[4 * j + 1] = cneg(cmul(bpq, id));
+        binv[4 * j + 2] = cneg(cmul(bqp, id));
+        binv[4 * j + 3] = cmul(bpp, id);
+        detD_out[j] = cmul(detD_in[pj], del);
     }
+    __syncwarp();
+    // scaled pivot rows (W0; W1) = B^-1 (row p; row q) on the child's columns
+    for (int e = lane; e < nchild * S2; e += 32) {
+        const int j = e / S2, c2 = e - j * S2;
+        const int a = nchild == 1 ? a1 : (j >> 1) & 1, b = nchild == 1 ? b1 : j & 1;
+        const int pj = nchild == 1 ? 0 : j >> 2;
+        const cx<R> *E = in + (size_t)pj * S * S;
+        const int p = 2 + a, q = 4 + b, c = c2 < 2 ? c2 : c2 + 4;
+        const cx<R> epc = E[p * S + c], eqc = E[q * S + c];
+        const cx<R> *bi = binv + 4 * j;
+        wrow[2 * e] = cfma(cmul(bi[0], epc), bi[1], eqc);
+        wrow[2 * e + 1] = cfma(cmul(bi[2], epc), bi[3], eqc);
+    }
+    __syncwarp();
+    // Only entries that are ever read are built: a choice path takes one copy of every vertex (and
+    // one measurement copy per determinant), so the entry joining row r2 to its row's other copy,
+    // column r2 ^ 1, is never used.  lane -> (child j, row r2, used column cc of W = S2 - 1) stepped
+    // by 32 entries without divisions.
+    const int W = S2 - 1;
+    const int dr = 32 / W, dc = 32 - dr * W;
+    int r2 = lane / W, cc = lane - r2 * W, j = 0;
+    while (r2 >= S2) {
+        r2 -= S2;
+        ++j;
+    }
+    const int total = nchild * S2 * W;
+    for (int e = lane; e < total; e += 32) {
+        const int c2 = cc < (r2 ^ 1) ? cc : cc + 1;
+        const int a = nchild == 1 ? a1 : (j >> 1) & 1, b = nchild == 1 ? b1 : j & 1;
+        const int pj = nchild == 1 ? 0 : j >> 2;
+        const int p = 2 + a, q = 4 + b;
+        const int r = r2 < 2 ? r2 : r2 + 4;
+        const int c = c2 < 2 ? c2 : c2 + 4;
+        const cx<R> *E = in + (size_t)pj * S * S;
+        const cx<R> *wr = wrow + 2 * (j * S2 + c2);
+        out[((size_t)j * S2 + r2) * S2 + c2] = cfms(cfms(E[r * S + c], E[r * S + p], wr[0]), E[r * S + q], wr[1]);
+        cc += dc;
+        r2 += dr;
+        if (cc >= W) {
+            cc -= W;
+            ++r2;
+        }
+        while (r2 >= S2) {
+            r2 -= S2;
+            ++j;
+        }
+    }
+    __syncwarp();
+}
+
+// One depth-first pair step from an S x S parent.
+template <class R>
+__device__ __forceinline__ void pair_step(const WarpSmem<R> &ws, const cx<R> *in, int S, int a, int b, cx<R> *out,
+                                          const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    switch (S - 4) {
+        case 12: pair_one_t<R, 6>(in, a, b, out, detD_in, detD_out, lane); break;
+        case 14: pair_one_t<R, 7>(in, a, b, out, detD_in, detD_out, lane); break;
+        case 16: pair_one_t<R, 8>(in, a, b, out, detD_in, detD_out, lane); break;
+        default:
+            if (S - 4 <= 32)
+                pair_one_wide<R>(in, S, a, b, out, detD_in, detD_out, lane);
+            else
+                pair_level<R>(in, S, 1, a, b, out, detD_in, detD_out, ws.wrow, ws.bip, lane);
+            break;
+    }
+}
+
+// Below a leaf group (1 << g matrices of Rleaf vertices at E, dets at ndet):
+// B breadth-first pair levels, then the per-lane flat phase over the
+// nodes x 2^F choice paths.  tpar: parity of the Keldysh indices fixed above.
+template <class R, int RFMAX>
+__device__ __forceinline__ void leaf_group(const WarpSmem<R> &ws, const cx<R> *E, const cx<R> *ndet, int g,
+                                           int Rleaf, int B, int F, int tpar, Acc<R> &ar, Acc<R> &ai, int lane) {
+    int S = 2 * Rleaf + 2;
+    int nodes = 1 << g;
+    cx<R> *dbuf = ws.bdet;
+    size_t bo = 0;
+    for (int lb = 0; lb < B; ++lb) {
+        cx<R> *out = ws.bfs + bo;
+        pair_level<R>(E, S, 4 * nodes, 0, 0, out, ndet, dbuf, ws.wrow, ws.bip, lane);
+        bo += (size_t)(4 * nodes) * (S - 4) * (S - 4);
+        E = out;
+        S -= 4;
+        nodes *= 4;
+        ndet = dbuf;
+        dbuf = (dbuf == ws.bdet) ? ws.bdet + ws.half : ws.bdet;
+    }
+    const int combos = nodes << F;
+    for (int cb = lane; cb < combos; cb += 32) {
+        const int node = cb >> F, path = cb & ((1 << F) - 1);
+        cx<R> term = flat_dispatch<R, RFMAX>(F, E + (size_t)node * S * S, ndet[node], path);
+        if ((tpar ^ __popc(node) ^ __popc(path)) & 1) term = cneg(term);
+        ar.add(term.re);
+        ai.add(term.im);
+    }
+    __syncwarp();
 }
 
 // Float-float or double-double style butterfly of the lane accumulators:
@@ -710,7 +889,8 @@ __device__ __forceinline__ double warp_total(Acc<R> acc) {
 // Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
 // The depth-first walk covers the subtree `sub` of 2^split: the first `split`
-// tree levels follow the bits of sub (split <= levels); split = 0: whole tree.
+// bits of the leaf index (a_2, then two per level) follow sub; split = 0: the
+// whole tree.
 template <class R, int RFMAX, bool GS>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
@@ -735,168 +915,89 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         }
     }
     __syncwarp();
-    // 2. level 0: vertex 1 eliminated (both a_1 kept in the two measurement copies).
-    // Built by 2x2 blocks: block row/column 0 = the measurement copies, block
-    // q >= 1 = vertex q+1 with its two Keldysh indices.  Within a block the
-    // entry is base(ai, aj) - left(ai) right(aj), with left = M(., vertex 1),
-    // right = M(vertex 1, .) / d.
-    const int R0 = n - 1;
-    const int S0 = 2 * R0 + 2;
-    // tree levels: offsets in shared memory, or (split stack) in device memory for the wide ones.
-    // Level l holds S_l^2 = 4 (R0 + 1 - l)^2 entries, so the offset of level l within its part is
-    // 4 (Q(R0 + 1 - l0) - Q(R0 + 1 - l)), Q(x) = x(x+1)(2x+1)/6, l0 = the part's first level.
-    const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
-    int lg = 0;  // levels [0, lg) in device memory: S_l > gs_level
-    if (GS) {
-        lg = R0 + 1 - ws.gs_level / 2;
-        lg = lg < 0 ? 0 : (lg > levels + 1 ? levels + 1 : lg);
-    }
-    auto sq_sum = [](int x) { return x * (x + 1) * (2 * x + 1) / 6; };
-    const int qtop = sq_sum(R0 + 1), qsplit = sq_sum(R0 + 1 - lg);
-    auto level = [&](int l) -> cx<R> * {
-        const int ql = sq_sum(R0 + 1 - l);
-        return (GS && l < lg) ? ws.gstack + 4 * (qtop - ql) : ws.stack + 4 * (qsplit - ql);
-    };
-    // the leaf and its parent are always in shared memory (gs_level >= 14)
-    auto level_smem = [&](int l) -> cx<R> * { return ws.stack + 4 * (qsplit - sq_sum(R0 + 1 - l)); };
-    const cx<R> id = crcp(dv);  // pivot of vertex 1
-    {
-        // Block row b's left factors M(., vertex 1) and block column b's right factors
-        // M(vertex 1, .) / d, once per block index: b = 0 the measurement copies (row entries
-        // r_1(a), column entries c_1(a) / d), b >= 1 vertex b + 1 (pair (1, b + 1)).
-        if (lane < n) {
-            cx<R> l0, l1, r0, r1;
-            if (lane == 0) {
-                l0 = ws.P[0];  // pair (0, 1)
-                l1 = ws.Rr[0];
-                r0 = cmul(ws.Rr[1], id);  // column entries of vertex 1
-                r1 = cmul(ws.P[1], id);
-            } else {
-                const int t = (lane * (lane + 3)) >> 1;  // vertex lane + 1's block
-                l0 = nconj(ws.Rr[t + 1]);
-                l1 = nconj(ws.P[t + 1]);
-                r0 = cmul(ws.P[t + 1], id);
-                r1 = cmul(ws.Rr[t + 1], id);
-            }
-            ws.lr[4 * lane] = l0;
-            ws.lr[4 * lane + 1] = l1;
-            ws.lr[4 * lane + 2] = r0;
-            ws.lr[4 * lane + 3] = r1;
-        }
-        __syncwarp();
-        // lane -> block (bx, by), stepped by 32 blocks without divisions; i = bx + 1 and
-        // j = by + 1 are the vertices, ti and tj the offsets of their packed blocks.  Within a
-        // block the entry is base(ai, aj) - left(ai) right(aj); base is the pair value of the
-        // later vertex's index: above the diagonal (row 0: the measurement row) it follows aj,
-        // below it (column 0: the measurement column, stored as is) it follows ai.
-        const int sq = 32 / n, sr = 32 - sq * n;
-        int bx = lane / n, by = lane - bx * n;
-        for (int bid = lane; bid < n * n; bid += 32) {
-            const int i = bx + 1, j = by + 1;
-            const int ti = (int)((unsigned)((i - 1) * (i + 2)) >> 1), tj = (int)((unsigned)((j - 1) * (j + 2)) >> 1);
-            const bool up = bx < by, diag = bx == by;
-            const int idx = up ? tj + (bx ? i : 0) : ti + (by ? j : i);
-            const cx<R> vP = ws.P[idx], vR = ws.Rr[idx];
-            const cx<R> left0 = ws.lr[4 * bx], left1 = ws.lr[4 * bx + 1];
-            const cx<R> right0 = ws.lr[4 * by + 2], right1 = ws.lr[4 * by + 3];
-            const R sg = (!up && by) ? R(-1) : R(1);  // lower entries of vertex pairs: -conj
-            const cx<R> lo0 = mk<R>(sg * vR.re, vR.im), lo1 = mk<R>(sg * vP.re, vP.im);
-            const cx<R> dd = bx == 0 ? d : dv;
-            const cx<R> b00 = diag ? dd : (up ? vP : lo0), b01 = diag ? dd : (up ? vR : lo0);
-            const cx<R> b10 = diag ? dd : (up ? vP : lo1), b11 = diag ? dd : (up ? vR : lo1);
-            cx<R> *o = level(0) + (2 * bx) * S0 + 2 * by;
-            o[0] = cfms(b00, left0, right0);
-            o[1] = cfms(b01, left0, right1);
-            o[S0] = cfms(b10, left1, right0);
-            o[S0 + 1] = cfms(b11, left1, right1);
-            by += sr;
-            bx += sq;
-            if (by >= n) {
-                by -= n;
-                ++bx;
-            }
-        }
-    }
-    if (lane == 0) ws.detD[0] = dv;
-    __syncwarp();
-    // 3. depth-first tree over a_2 .. a_{levels+1}
-    const int Rleaf = R0 - levels;
-    const int B = Rleaf > RF ? Rleaf - RF : 0;
-    const int Rf = Rleaf - B;
     Acc<R> ar, ai;
     ar.init();
     ai.init();
-    const int nleaf = 1 << (levels - split);
-    const int node = lane >> Rf;
-    const int path = lane & ((1 << Rf) - 1);
-    const bool active = lane < (1 << Rleaf);
-    // With two or more leaves in the walk, leaves come in sibling pairs: the last depth-first step
-    // builds both (the second into ws.sib) and the pair is resolved one after the other.
-    const int twin = twin_leaves<R>() && levels - split >= 1 ? 1 : 0;
-    for (int bl = 0; bl < nleaf; bl += 1 + twin) {
-        const int b = (sub << (levels - split)) | bl;  // tree path: the subtree's fixed prefix, then bl
-        int from = (bl == 0) ? 0 : levels - (__ffs(b) - 1) - 1;
-        for (int l = from; l < levels - twin; ++l) {
-            const int a = (b >> (levels - 1 - l)) & 1;
-            const int S = 2 * (R0 - l) + 2;
-            if (S - 2 <= 32)
-                expand_one<R>(level(l), S, a, level(l + 1), ws.detD + l, ws.detD + l + 1, lane);
-            else
-                expand_level<R>(level(l), S, 1, a, level(l + 1), ws.detD + l, ws.detD + l + 1, ws.wrow, ws.bip,
-                                lane);
+    if (n <= 2) {
+        // orders 1 and 2 in closed form (every lane computes it, lane 0 adds it)
+        cx<R> term;
+        if (n == 1) {  // det M_up(a_1) = d dv - M(0,1) M(1,0), det M_down = dv
+            term = cmul(dv, csub(cmul(ws.Rr[0], ws.P[1]), cmul(ws.P[0], ws.Rr[1])));
+        } else {  // the root pair is the last pair
+            const cx<R> one = mk<R>(1, 0);
+            term = mk<R>(0, 0);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const cx<R> m12 = sel<R>(s, ws.Rr[3], ws.P[3]), m21 = nconj(sel<R>(s, ws.P[3], ws.Rr[3]));
+                const cx<R> m02 = sel<R>(s, ws.Rr[2], ws.P[2]), m20 = sel<R>(s, ws.P[4], ws.Rr[4]);
+                const cx<R> t = leaf_pair(d, d, ws.P[0], m02, ws.Rr[1], m20, ws.Rr[0], m02, ws.P[1], m20, dv, m12,
+                                          m21, dv, one);
+                term = s ? csub(term, t) : t;
+            }
         }
-        if (twin)  // the leaves' parent has 2 kTreeLeaf + 4 rows
-            expand_both_t<R, kTreeLeaf + 1>(level_smem(levels - 1), level_smem(levels), ws.sib,
-                                            ws.detD + levels - 1, ws.detD + levels, ws.detD + levels + 1, lane);
-#pragma unroll 1
-        for (int h = 0; h <= twin; ++h) {
-            const int tparity = __popc(b + h) & 1;
-            // 4. breadth-first expansion of B levels below the tree leaf
-            const cx<R> *E = h ? ws.sib : level_smem(levels);
-            int S = 2 * Rleaf + 2;
-            const cx<R> *ndet = ws.detD + levels + h;
-            cx<R> *dbuf = ws.bdet;
-            size_t bo = 0;
-            for (int lb = 0; lb < B; ++lb) {
-                const int nparent = 1 << lb;
-                cx<R> *out = ws.bfs + bo;
-                expand_level<R>(E, S, 2 * nparent, 0, out, ndet, dbuf, ws.wrow, ws.bip, lane);
-                bo += (size_t)(2 * nparent) * (S - 2) * (S - 2);
-                E = out;
-                S -= 2;
-                ndet = dbuf;
-                dbuf = (dbuf == ws.bdet) ? ws.bdet + 32 : ws.bdet;
+        if (lane == 0) {
+            ar.add(term.re);
+            ai.add(term.im);
+        }
+    } else {
+        const TreeShape ts = tree_shape(n);
+        const int B = bfs_levels(ts.Rleaf, RF);
+        const int F = ts.Rleaf - 2 * B;
+        const int Sr = 2 * ts.Rr + 2;
+        // tree levels: [0, lg) in device memory (split stack, S > gs_level), the rest in shared memory
+        int lg = 0;
+        if (GS)
+            while (lg <= ts.dfl && Sr - 4 * lg > ws.gs_level) ++lg;
+        auto level = [&](int l) -> cx<R> * {
+            const bool dev = GS && l < lg;
+            size_t off = 0;
+            for (int j = dev ? 0 : lg; j < l; ++j) off += level_entries(ts, j);
+            return (dev ? ws.gstack : ws.stack) + off;
+        };
+        if (ts.g) {
+            cx<R> *root = level(0);
+            build_root<R>(ws, n, 0, d, dv, root, ws.detD, lane);
+            build_root<R>(ws, n, 1, d, dv, root + Sr * Sr, ws.detD + 1, lane);
+            leaf_group<R, RFMAX>(ws, root, ws.detD, 1, ts.Rleaf, B, F, 0, ar, ai, lane);
+        } else {
+            const int free_bits = ts.lbits - split;
+            const int nleaf = 1 << free_bits;
+            for (int bl = 0; bl < nleaf; ++bl) {
+                const int b = (sub << free_bits) | bl;  // leaf index: the subtree's fixed prefix, then bl
+                int from = 0;
+                if (bl) {  // rebuild from the level of the highest index bit that changed
+                    const int pos = __ffs(b) - 1;
+                    from = pos == ts.lbits - 1 ? 0 : (ts.lbits - pos) >> 1;
+                }
+                for (int l = from; l <= ts.dfl; ++l) {
+                    if (l == 0) {
+                        build_root<R>(ws, n, (b >> (ts.lbits - 1)) & 1, d, dv, level(0), ws.detD, lane);
+                    } else {
+                        const int a = (b >> (ts.lbits - 2 * l)) & 1, c = (b >> (ts.lbits - 2 * l - 1)) & 1;
+                        pair_step<R>(ws, level(l - 1), Sr - 4 * (l - 1), a, c, level(l), ws.detD + l - 1,
+                                     ws.detD + l, lane);
+                    }
+                }
+                leaf_group<R, RFMAX>(ws, level(ts.dfl), ws.detD + ts.dfl, 0, ts.Rleaf, B, F, __popc(b) & 1, ar, ai,
+                                     lane);
             }
-            // 5. per-lane flat phase on the last Rf vertices
-            if (active) {
-                const cx<R> *En = E + (size_t)node * S * S;
-                const int parity = tparity ^ (__popc(node) & 1);
-                flat_dispatch<R, RFMAX>(Rf, En, ndet[B > 0 ? node : 0], parity, path, ar, ai);
-            }
-            __syncwarp();
         }
     }
     return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
 }
 
-// One point per lane (small orders), registers only: the lane interpolates
-// its own pairs, and for every choice path of vertices 2..N builds the path's
-// (N+1) x (N+1) matrix -- rows/columns {copy a_1 = 0, copy a_1 = 1, vertices
-// 2..N with their chosen Keldysh index}, vertex 1 already eliminated -- from
-// the pair values, then eliminates vertices 2..N.  All loops are unrolled, so
-// every array index is static.
-template <class R>
-__device__ __forceinline__ cx<R> sel(int bit, cx<R> one, cx<R> zero) {
-    return mk<R>(bit ? one.re : zero.re, bit ? one.im : zero.im);
-}
-
+// One point per lane (small orders), registers only: the lane interpolates its
+// own pairs, and for each a_2 and every choice path of vertices 3..N builds the
+// path's N x N matrix -- rows/columns {copy a_1 = 0, copy a_1 = 1, vertices
+// 3..N with their chosen Keldysh index}, vertices 1 and 2 already eliminated
+// with their pivot block -- from the pair values, then resolves the rest with
+// the leaf formulas.  All loops are unrolled, so every array index is static.
 template <class R, int N>
 __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d, cx<R> dv,
                                                        const typename TabT<R>::V *tab,
                                                        const typename TabT<R>::V *col, double inv_h, double s0,
                                                        int L) {
-    constexpr int M = N + 1;
-    cx<R> P[N + 1][N + 1], Rr[N + 1][N + 1];
+    cx<R> P[N + 1][N + 1], Rr[N + 1][N + 1];  // P[j][k] = g^>(u_j - u_k), Rr[j][k] = g^<(u_j - u_k), j < k
     double uu[N + 1];
 #pragma unroll
     for (int m = 0; m <= N; ++m) uu[m] = u[m];
@@ -912,77 +1013,82 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
         C1[k] = nconj(P[0][k]);
         if (col) interp_col<R>(col, inv_h, s0, L, uu[k] - uu[0], C0[k], C1[k]);
     }
-    const cx<R> id = crcp(dv);
-    // row/column factors of vertex 1 (eliminated first, pivot dv)
-    const cx<R> r1[2] = {P[0][1], Rr[0][1]};
-    const cx<R> c1d[2] = {cmul(C0[1], id), cmul(C1[1], id)};
     Acc<R> ar, ai;
     ar.init();
     ai.init();
-#pragma unroll
-    for (int path = 0; path < (1 << (N - 1)); ++path) {
-        // position x: 0, 1 = copies; x >= 2 = vertex v = x with Keldysh index a_v = bit (x-2) of path
-        cx<R> left[M], right[M], m[M][M];
-#pragma unroll
-        for (int x = 0; x < M; ++x) {
-            if (x < 2) {
-                left[x] = r1[x];
-                right[x] = c1d[x];
-            } else {
-                const int a = (path >> (x - 2)) & 1;
-                left[x] = nconj(sel<R>(a, P[1][x], Rr[1][x]));
-                right[x] = cmul(sel<R>(a, Rr[1][x], P[1][x]), id);
-            }
-        }
-#pragma unroll
-        for (int x = 0; x < M; ++x)
-#pragma unroll
-            for (int y = 0; y < M; ++y) {
-                if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
-                cx<R> base;
-                if (x == y) {
-                    base = x < 2 ? d : dv;
-                } else if (x < 2) {  // measurement row, vertex y
-                    base = sel<R>((path >> (y - 2)) & 1, Rr[0][y], P[0][y]);
-                } else if (y < 2) {  // vertex x, measurement column
-                    base = sel<R>((path >> (x - 2)) & 1, C1[x], C0[x]);
-                } else if (x < y) {  // upper: index of the column vertex
-                    base = sel<R>((path >> (y - 2)) & 1, Rr[x][y], P[x][y]);
-                } else {  // lower: index of the row vertex
-                    base = nconj(sel<R>((path >> (x - 2)) & 1, P[y][x], Rr[y][x]));
-                }
-                m[x][y] = cfms(base, left[x], right[y]);
-            }
-        cx<R> detD = dv;
-#pragma unroll
-        for (int p = 2; p < M - 1; ++p) {
-            cx<R> pv = m[p][p];
-            detD = cmul(detD, pv);
-            cx<R> iq = crcp(pv);
-#pragma unroll
-            for (int y = 0; y < M; ++y)
-                if (y < 2 || y > p) m[p][y] = cmul(m[p][y], iq);
-#pragma unroll
-            for (int x = 0; x < M; ++x) {
-                if (!(x < 2 || x > p)) continue;
-#pragma unroll
-                for (int y = 0; y < M; ++y) {
-                    if (!(y < 2 || y > p)) continue;
-                    if (x < 2 && y < 2 && x != y) continue;
-                    m[x][y] = cfms(m[x][y], m[x][p], m[p][y]);
-                }
-            }
-        }
-        cx<R> term;
-        if constexpr (M > 2) {
-            term = leaf_term(m[0][0], m[1][1], m[0][M - 1], m[M - 1][0], m[1][M - 1], m[M - 1][1], m[M - 1][M - 1],
-                             detD);
-        } else {  // order 1: vertex 1 was eliminated when the matrix was built
-            term = cmul(cmul(detD, detD), mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im));
-        }
-        if (__popc(path) & 1) term = mk<R>(-term.re, -term.im);
+    if constexpr (N == 1) {  // det M_up(a_1) = d dv - M(0,1) M(1,0), det M_down = dv
+        const cx<R> term = cmul(dv, csub(cmul(Rr[0][1], C1[1]), cmul(P[0][1], C0[1])));
         ar.add(term.re);
         ai.add(term.im);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const cx<R> m12 = sel<R>(s, Rr[1][2], P[1][2]), m21 = nconj(sel<R>(s, P[1][2], Rr[1][2]));
+            const cx<R> m02 = sel<R>(s, Rr[0][2], P[0][2]), m20 = sel<R>(s, C1[2], C0[2]);
+            const cx<R> del = cfms(cmul(dv, dv), m12, m21);
+            if constexpr (N == 2) {  // the root pair is the last pair
+                const cx<R> term =
+                    leaf_pair(d, d, P[0][1], m02, C0[1], m20, Rr[0][1], m02, C1[1], m20, dv, m12, m21, dv, mk<R>(1, 0));
+                ar.add(s ? -term.re : term.re);
+                ai.add(s ? -term.im : term.im);
+            } else {
+                const cx<R> id = crcp(del);
+                constexpr int M = N;  // copies + vertices 3..N at positions 2..N-1
+#pragma unroll
+                for (int path = 0; path < (1 << (N - 2)); ++path) {
+                    cx<R> l0[M], l1[M], w0[M], w1[M], m[M][M];
+#pragma unroll
+                    for (int x = 0; x < M; ++x) {
+                        cx<R> r0, r1;
+                        if (x < 2) {
+                            l0[x] = sel<R>(x, Rr[0][1], P[0][1]);  // M(0,1) with a_1 = x
+                            l1[x] = m02;
+                            r0 = sel<R>(x, C1[1], C0[1]);  // M(1,0) with a_1 = x
+                            r1 = m20;
+                        } else {
+                            const int v = x + 1, a = (path >> (x - 2)) & 1;
+                            l0[x] = nconj(sel<R>(a, P[1][v], Rr[1][v]));
+                            l1[x] = nconj(sel<R>(a, P[2][v], Rr[2][v]));
+                            r0 = sel<R>(a, Rr[1][v], P[1][v]);
+                            r1 = sel<R>(a, Rr[2][v], P[2][v]);
+                        }
+                        // B^-1 (r0; r1), B^-1 = (1 / delta) [[dv, -M12], [-M21, dv]]
+                        w0[x] = cmul(cfms(cmul(dv, r0), m12, r1), id);
+                        w1[x] = cmul(cfms(cmul(dv, r1), m21, r0), id);
+                    }
+#pragma unroll
+                    for (int x = 0; x < M; ++x)
+#pragma unroll
+                        for (int y = 0; y < M; ++y) {
+                            if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
+                            cx<R> base;
+                            if (x == y) {
+                                base = x < 2 ? d : dv;
+                            } else if (x < 2) {  // measurement row, vertex y + 1
+                                base = sel<R>((path >> (y - 2)) & 1, Rr[0][y + 1], P[0][y + 1]);
+                            } else if (y < 2) {  // vertex x + 1, measurement column
+                                base = sel<R>((path >> (x - 2)) & 1, C1[x + 1], C0[x + 1]);
+                            } else if (x < y) {  // upper: index of the column vertex
+                                base = sel<R>((path >> (y - 2)) & 1, Rr[x + 1][y + 1], P[x + 1][y + 1]);
+                            } else {  // lower: index of the row vertex
+                                base = nconj(sel<R>((path >> (x - 2)) & 1, P[y + 1][x + 1], Rr[y + 1][x + 1]));
+                            }
+                            m[x][y] = cfms(cfms(base, l0[x], w0[y]), l1[x], w1[y]);
+                        }
+                    cx<R> term;
+                    if constexpr (N == 3) {
+                        term = leaf_term(m[0][0], m[1][1], m[0][2], m[2][0], m[1][2], m[2][1], m[2][2], del);
+                    } else {
+                        static_assert(N == 4, "one point per lane serves orders 1..4");
+                        term = leaf_pair(m[0][0], m[1][1], m[0][2], m[0][3], m[2][0], m[3][0], m[1][2], m[1][3],
+                                         m[2][1], m[3][1], m[2][2], m[2][3], m[3][2], m[3][3], del);
+                    }
+                    if ((s + __popc(path)) & 1) term = cneg(term);
+                    ar.add(term.re);
+                    ai.add(term.im);
+                }
+            }
+        }
     }
     return mk<double>((double)ar.s + (double)ar.c, (double)ai.s + (double)ai.c);
 }
@@ -1655,6 +1761,8 @@ int launch_lead_table(Problem &pr, cudaStream_t s, double *zero) {
     if (e != cudaSuccess) return cuda_error(e, "lead table build");
     return QQMC_OK;
 }
+
+int tree_leaf_bits(int order) { return tree_shape(order).lbits; }
 
 size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
     size_t per = precision == QQMC_PREC_FP64 ? warp_smem_bytes<double>(n_max, tune.flat_min)

@@ -91,6 +91,9 @@ bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune);
 cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                         int precision, cudaStream_t s);
 constexpr int kLaneMaxOrder = 4;  // orders that may run one point per lane
+// Bits of the leaf index of an order's Keldysh tree (a_2, then two per
+// depth-first pair level); work units may fix a prefix of them.
+int tree_leaf_bits(int order);
 cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out, unsigned long long *d_counts,
                           cudaStream_t s);
 size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune);

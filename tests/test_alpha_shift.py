@@ -123,3 +123,146 @@ def test_integration_with_alpha_matches_oracle(Q, oracle, lane):
     finally:
         Q.qqmc_destroy_problem(pr)
         autotune.reset()
+
+
+# ------------------------------------------------- alpha at the occupation ---
+# alpha = Im g^<(0), the App. E choice that cancels the Hartree term, makes every vertex diagonal
+# of M_down zero.  At particle-hole symmetry (eps_d = 0, alpha = 1/2) M_down is moreover skew-
+# symmetric for every Keldysh index vector (g^>(tau) = conj g^<(tau)), so every odd leading minor
+# vanishes and det M_down = 0 at odd orders: c_n = 0 there, and both sides return rounding.
+# Bars per point: FP64 1e-12 sum_a |term_a| (the standard bar) plus 1e-14 times the summed
+# Hadamard bounds of both determinants, which bound the rounding of a determinant that vanishes
+# (n eps_64 < 1e-14 up to order 22); mixed precision 2^-20 (charge) or 2^-18 (current) of
+# sum_a |term_a| plus 2^-20 of the Hadamard sum (n eps_32 < 2^-20 up to order 12).
+
+OFFSETS = [0.0, 1e-6, -1e-6, 1e-3, -1e-3]
+
+
+def _check_point_bars(gpu, mixed, ref, scale, had, mixed_rel=2.0 ** -20):
+    assert np.all(np.isfinite(gpu)) and np.all(np.isfinite(mixed))
+    dev = np.abs(gpu - ref)
+    assert np.all(dev <= 1e-12 * scale + 1e-14 * had), np.max(dev / (scale + had))
+    dm = np.abs(mixed - ref)
+    assert np.all(dm <= mixed_rel * scale + 2.0 ** -20 * had), np.max(dm / (scale + had))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order,count", [(1, 64), (2, 64), (3, 48), (4, 32), (5, 24), (6, 16), (7, 12), (8, 8),
+                                         (9, 6), (10, 4), (12, 2)])
+def test_integrand_at_the_occupation_matches_oracle(Q, oracle, order, count):
+    from paper_2002_12372_gb300 import workloads as W
+    T = 10.0
+    gl, gg, g0, _ = W.synthetic_tables(500 + order, 4096, T)
+    u = W.ordered_times(600 + order, count, order, T)
+    for off in OFFSETS:
+        alpha = float(np.imag(g0)) + off
+        pr = Q.qqmc_create_problem_tables(Q.make_params(t_max=T, n_table=4096, alpha=alpha), gl, gg, g0)
+        try:
+            gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)
+            mixed = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_MIXED)
+        finally:
+            Q.qqmc_destroy_problem(pr)
+        ref, scale, had = oracle.integrand(order, u, T, (gl, gg, g0), T, return_abs=True, return_had=True,
+                                           alpha=alpha)
+        _check_point_bars(gpu, mixed, ref, scale, had)
+        if order == 1 and off == 0.0:  # the one-vertex det M_down is exactly zero
+            assert np.all(gpu == 0.0) and np.all(mixed == 0.0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order,count", [(1, 32), (2, 32), (3, 32), (4, 24), (5, 16), (6, 12), (7, 8), (8, 6),
+                                         (9, 4), (11, 2)])
+def test_integrand_at_particle_hole_symmetry_matches_oracle(Q, oracle, order, count):
+    """The wide-band dot at eps_d = 0 (tables from the oracle's closed form on both sides) with
+    alpha = <n> = 1/2 and next to it."""
+    from paper_2002_12372_gb300 import workloads as W
+    T, L = 10.0, 4096
+    gl, gg, g0 = oracle.gf_tables(1.0, 0.0, T, L)
+    u = W.ordered_times(700 + order, count, order, T)
+    for off in [0.0, 1e-6, -1e-3]:
+        alpha = float(np.imag(g0)) + off
+        pr = Q.qqmc_create_problem_tables(Q.make_params(t_max=T, n_table=L, alpha=alpha), gl, gg, g0)
+        try:
+            gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)
+            mixed = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_MIXED)
+        finally:
+            Q.qqmc_destroy_problem(pr)
+        ref, scale, had = oracle.integrand(order, u, T, (gl, gg, g0), T, return_abs=True, return_had=True,
+                                           alpha=alpha)
+        _check_point_bars(gpu, mixed, ref, scale, had)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order,count", [(1, 64), (2, 64), (3, 48), (5, 32), (7, 12), (10, 4)])
+def test_current_integrand_at_the_occupation_matches_oracle(Q, oracle, order, count):
+    from paper_2002_12372_gb300 import workloads as W
+    T, L = 10.0, 4096
+    gl, gg, g0, _ = W.synthetic_tables(800 + order, L, T)
+    cl, cg, c0 = W.synthetic_column_tables(1800 + order, L, T)
+    u = W.ordered_times(900 + order, count, order, T)
+    for off in OFFSETS:
+        alpha = float(np.imag(g0)) + off
+        pr = Q.qqmc_create_problem_tables(Q.make_params(t_max=T, n_table=L, alpha=alpha), gl, gg, g0)
+        try:
+            Q.qqmc_set_current_tables(pr, cl, cg, c0)
+            gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)
+            mixed = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_MIXED)
+        finally:
+            Q.qqmc_destroy_problem(pr)
+        ref, scale, had = oracle.integrand(order, u, T, (gl, gg, g0), T, return_abs=True, return_had=True,
+                                           alpha=alpha, col=(cl, cg, c0))
+        _check_point_bars(gpu, mixed, ref, scale, had, mixed_rel=2.0 ** -18)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("lane", [False, True])
+@pytest.mark.parametrize("off", [0.0, 1e-6, -1e-3])
+@pytest.mark.parametrize("current", [False, True])
+def test_integration_at_the_occupation_matches_oracle(Q, oracle, lane, off, current):
+    """Per-shift sums at alpha = Im g^<(0) and next to it, with the cooperative warp kernel and the
+    one-point-per-lane kernel (orders <= 4), for the charge and the current."""
+    from paper_2002_12372_gb300 import autotune
+    from paper_2002_12372_gb300 import workloads as W
+    T, K, L = 10.0, 3, 4096
+    gl, gg, g0, _ = W.synthetic_tables(81, L, T)
+    col = W.synthetic_column_tables(1081, L, T) if current else None
+    alpha = float(np.imag(g0)) + off
+    pr = Q.qqmc_create_problem_tables(Q.make_params(t_max=T, n_table=L, alpha=alpha), gl, gg, g0)
+    try:
+        if current:
+            Q.qqmc_set_current_tables(pr, *col)
+        for n in range(1, 5):
+            Q.qqmc_set_tuning(Q.QQMC_PREC_FP64, n, 2, 1 if lane else 2)
+        for n, N in [(1, 2049), (2, 1000), (3, 1000), (4, 777), (7, 200), (10, 64)]:
+            sw = W.shift_words(700 + n, K, n)
+            res, S = Q.qqmc_integrate(pr, n, N, K, Q.QQMC_PREC_FP64, sw)
+            S0, nin = oracle.estimate(n, N, sw, T, 1.0, (gl, gg, g0), T, alpha=alpha, col=col)
+            assert res.n_in_domain == int(nin.sum())
+            assert np.all(np.isfinite(S))
+            assert np.all(np.abs(S - S0) <= 1e-10 * np.abs(S0)), (n, S, S0)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+        autotune.reset()
+
+
+# -------------------------------------------------- the oracle's rounding scale ---
+
+def test_hadamard_scale_bounds_every_keldysh_term(oracle):
+    """Hadamard's inequality |det A| <= prod_rows ||row|| holds for each of the two determinants, so
+    the summed bounds dominate sum_a |term_a|; every bound is homogeneous of degree 2n + 1 in the
+    Green functions (n + 1 rows of M_up, n of M_down, one factor each)."""
+    from paper_2002_12372_gb300 import workloads as W
+    T = 10.0
+    gl, gg, g0, _ = W.synthetic_tables(5, 512, T)
+    for n in (1, 2, 3, 5):
+        u = W.ordered_times(40 + n, 16, n, T)
+        _, scale, had = oracle.integrand(n, u, T, (gl, gg, g0), T, return_abs=True, return_had=True, alpha=0.2)
+        assert np.all(had >= scale) and np.all(had > 0.0)
+        lam = 1.7
+        _, had2 = oracle.integrand(n, u, T, (lam * gl, lam * gg, lam * g0), T, return_had=True, alpha=lam * 0.2)
+        assert np.allclose(had2, lam ** (2 * n + 1) * had, rtol=1e-12)
+    # one vertex at alpha = Im g^<(0): M_down = (0), so both its bound and the term vanish
+    u = W.ordered_times(49, 8, 1, T)
+    c, scale, had = oracle.integrand(1, u, T, (gl, gg, g0), T, return_abs=True, return_had=True,
+                                     alpha=float(np.imag(g0)))
+    assert np.all(had == 0.0) and np.all(scale == 0.0) and np.all(c == 0.0)
