@@ -288,10 +288,9 @@ def run_ours(args, ws, rank, local, pg):
 
 
 # DRAM bytes (read + write) of the detsum launches of one default benchmark step (one launch per
-# tuned flat depth: two here), from a 1-pass ncu capture of this exact command
-# (profiles/detsum_*_plain-dot_n1-10.md); per step, like the achieved rate.
-# Set to None whenever the determinant kernel changes until it is captured again.
-MEASURED_LAUNCH_TRAFFIC = {"fp64": 2154752, "mixed": 1191936}
+# tuned flat depth), from a 1-pass ncu capture of this exact command; per step, like the achieved
+# rate.  None whenever the determinant kernel has changed since the capture.
+MEASURED_LAUNCH_TRAFFIC = {"fp64": None, "mixed": None}
 
 
 def _launch_traffic(args, slice_n):
@@ -581,21 +580,26 @@ def run_serving(args, local):
             "median_rel_err_at_nmax": statistics.median(rel_err) if rel_err else None}
 
 
-def cpu_oracle_sample(seconds_per_order: float = 1.5, orders=ORDERS, shift_seed: int = SEED):
+def cpu_oracle_sample(seconds_per_order: float = 1.5, orders=ORDERS, shift_seed: int = SEED, threads: int = 0):
     """Time the CPU oracle on a bounded sample of the workload (eps_d = 0, one shift,
-    first M points per order with M chosen so each order runs ~seconds_per_order)."""
+    first M points per order with M chosen so each order runs ~seconds_per_order).
+    Set-up that is not per-point work stays out of the timed calls: the direction
+    words are built once and passed in, and every order runs once untimed first.
+    threads = 0: every host core."""
     from oracle import oracle as O
 
     tabs = O.gf_tables(GAMMA, 0.0, T_MAX, L_TABLE)
     sw = O.shift_words(shift_seed, 1, max(orders))
-    threads = os.cpu_count() or 1
+    V = O.sobol_direction_numbers(max(orders))
+    threads = threads or os.cpu_count() or 1
     per_point = {}
     sample = {}
     for n in orders:
+        O.estimate(n, 32 * threads, sw, T_MAX, TAU, tabs, T_MAX, V=V, threads=threads, chunk=32)  # warm-up
         M = 64 * threads
         while True:
             t0 = time.perf_counter()
-            O.estimate(n, M, sw, T_MAX, TAU, tabs, T_MAX, threads=threads, chunk=max(1, M // (4 * threads)))
+            O.estimate(n, M, sw, T_MAX, TAU, tabs, T_MAX, V=V, threads=threads, chunk=max(1, M // (4 * threads)))
             dt = time.perf_counter() - t0
             if dt > 0.25 * seconds_per_order or M >= 2 ** 20:
                 break
@@ -605,6 +609,17 @@ def cpu_oracle_sample(seconds_per_order: float = 1.5, orders=ORDERS, shift_seed:
     # the workload has equal point counts per order: evals/s = n_orders / sum_n t_n
     value = len(orders) / sum(per_point.values())
     return value, threads, sample
+
+
+def cpu_baseline_entry(seconds_per_order: float = 1.5):
+    """The oracle on every host core (the reported value) and on one core."""
+    v, threads, sample = cpu_oracle_sample(seconds_per_order)
+    v1, _, sample1 = cpu_oracle_sample(seconds_per_order / 2, threads=1)
+    return {"value": v, "unit": "evals/s", "cores": threads, "kind": "oracle",
+            "single_core_value": v1,
+            "sample": "eps_d=0, 1 shift, first points per order " + ",".join(
+                "n%d:%d" % (n, m) for n, m in sample.items()) + "; one core: " + ",".join(
+                "n%d:%d" % (n, m) for n, m in sample1.items())}
 
 
 def run_reference(args, ws, rank, pg):
@@ -677,10 +692,7 @@ def main():
     out = run_ours(args, ws, rank, local, pg)
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
-            v, threads, sample = cpu_oracle_sample(1.5)
-            out["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": threads, "kind": "oracle",
-                                   "sample": "eps_d=0, 1 shift, first points per order " + ",".join(
-                                       "n%d:%d" % (n, m) for n, m in sample.items())}
+            out["cpu_baseline"] = cpu_baseline_entry(1.5)
         print(json.dumps(out), flush=True)
     if pg is not None:
         pg.destroy_process_group()

@@ -53,6 +53,7 @@ extern "C" {
 
 #define QQMC_OK 0
 #define QQMC_PENDING 1
+#define QQMC_RUNNING 2
 #define QQMC_E_INVAL (-1)     /* malformed argument */
 #define QQMC_E_RANGE (-2)     /* order outside 1..QQMC_MAX_ORDER */
 #define QQMC_E_NOMEM (-3)     /* device or host allocation failed */
@@ -61,6 +62,7 @@ extern "C" {
 #define QQMC_E_TIMEOUT (-6)   /* request or wait exceeded its limit */
 #define QQMC_E_CANCELLED (-7) /* request cancelled before completion */
 #define QQMC_E_NOTFOUND (-8)  /* unknown handle */
+#define QQMC_E_NONFINITE (-9) /* an integrand sum came out NaN or infinite (results still filled) */
 
 #define QQMC_MAX_ORDER 22
 #define QQMC_MAX_POINTS_LOG2 30 /* N <= 2^30 points per shifted sequence */
@@ -223,6 +225,8 @@ typedef struct qqmc_result {
                                   current: max_k |-4 Im S_k / N| (not a check) */
     uint64_t n_in_domain;      /* points with u_n > 0, summed over shifts */
     double device_ms;          /* device time of the launch that produced it */
+    uint64_t n_nonfinite;      /* work units whose partial sum was NaN or infinite (0 when valid);
+                                  any nonzero count makes the call return QQMC_E_NONFINITE */
 } qqmc_result;
 
 /*
@@ -276,6 +280,11 @@ int qqmc_plan_kernel_count(const qqmc_plan *plan);
  * kernel alone (events on the launch stream around it; 0 when the launch was a
  * graph replay) and the whole launch. */
 int qqmc_plan_timing(const qqmc_plan *plan, double *kernel_ms, double *total_ms);
+/* Execution span of the last launch on the device clock (%globaltimer, ns):
+ * the earliest start and the latest exit of any warp of its determinant
+ * launches.  Spans of plans launched on different streams can be compared to
+ * see whether their kernels ran at the same time.  Waits for the launch. */
+int qqmc_plan_device_span(const qqmc_plan *plan, uint64_t *start_ns, uint64_t *end_ns);
 
 /*
  * Partial sums of single chunks of the last launch (after qqmc_plan_results):
@@ -316,12 +325,18 @@ int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_ve
  *   d_sums: DEVICE [n_shifts][2] doubles, receives sum_i w_i c_n(u_i) per
  *           shift, NOT divided by N (Q_n^(k) = -2i d_sums[k] / N);
  *   d_counts: DEVICE [n_shifts] uint64 in-domain counts, or NULL;
- *   stream: cudaStream_t or NULL.  The call only enqueues work; the outputs
- *   are ready when the stream reaches that point.
+ *   stream: cudaStream_t or NULL.  The call only enqueues work (the item
+ *   descriptor travels as a kernel argument; no host buffer is read after the
+ *   call returns); the outputs are ready when the stream reaches that point.
+ *   NaN or infinite integrand values show up in d_sums; there is no
+ *   QQMC_E_NONFINITE here, since the call does not wait for the device.
+ * The current device must be the problem's (E_INVAL otherwise).
  * Limits (E_INVAL beyond): n_shifts * ceil(n_points / 32) <= 465792; the
- * whole Schur-tree stack in shared memory, so FP64 orders whose stack
- * exceeds a block's 227 KB (21 and 22 with the built-in shapes) are refused -- qqmc_integrate or the
- * mixed precision serve them.  No work-unit cut: one unit per chunk.
+ * whole Schur-tree stack in shared memory (every order up to
+ * QQMC_MAX_ORDER fits, one warp per block at the highest FP64 orders; a
+ * stack that did not fit would be refused).  No work-unit cut: one unit per
+ * chunk, so orders with few chunks, and those from the stack-policy order
+ * up, can run slower than in qqmc_integrate.
  * The first call on a device resolves the array's device address and uploads
  * the kernels' constant tables; make that first call before any stream
  * capture.  Every call shares the array and leaves its contents behind (the
@@ -407,6 +422,9 @@ typedef struct qqmc_series {
     double latency_ms;                 /* submit -> completion */
     double queue_ms;                   /* submit -> admission */
     uint64_t n_in_domain;
+    uint64_t batch;                    /* admission round that carried the request (1, 2, ...) */
+    uint64_t device_start_ns;          /* execution span of that round's kernels on the device */
+    uint64_t device_end_ns;            /*   clock (%globaltimer, ns); see qqmc_plan_device_span */
 } qqmc_series;
 
 int qqmc_server_create(const qqmc_server_opts *opts, qqmc_server **out);
@@ -415,6 +433,10 @@ int qqmc_submit(qqmc_server *s, const qqmc_request *r, uint64_t *handle);
 /* QQMC_PENDING, QQMC_OK (out filled; the handle is released) or an error code
  * (out->status set; the handle is released). */
 int qqmc_poll(qqmc_server *s, uint64_t handle, qqmc_series *out);
+/* Where a request stands, without releasing it: QQMC_PENDING (queued),
+ * QQMC_RUNNING (admitted: its round is on the device), or its final status
+ * (QQMC_OK or an error code) once done; E_NOTFOUND for an unknown handle. */
+int qqmc_request_state(qqmc_server *s, uint64_t handle);
 int qqmc_cancel(qqmc_server *s, uint64_t handle);
 /* Waits for in-flight work, fails pending requests with E_CANCELLED, frees all. */
 int qqmc_server_destroy(qqmc_server *s);

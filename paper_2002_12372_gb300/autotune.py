@@ -23,7 +23,7 @@ import time
 from . import qqmc as Q
 
 CANDIDATES = {
-    Q.QQMC_PREC_FP64: [(w, f) for w in (1, 2, 3, 4) for f in (2, 3, 5)],
+    Q.QQMC_PREC_FP64: [(w, f) for w in (1, 2, 3, 4) for f in (2, 3, 4, 5)],
     Q.QQMC_PREC_MIXED: [(w, f) for w in (2, 4, 6, 8) for f in (2, 3, 4, 5)],
 }
 # flat 1 = one point per lane (orders <= 4)
@@ -104,7 +104,9 @@ def save(table, path: str) -> None:
     if os.path.exists(path):
         with open(path) as f:
             data = json.load(f)
-    data[name] = {str(p): {str(n): list(v) for n, v in rows.items()} for p, rows in table.items()}
+    merged = data.setdefault(name, {})  # orders not tuned this time keep their rows
+    for p, rows in table.items():
+        merged.setdefault(str(p), {}).update({str(n): list(v) for n, v in rows.items()})
     with open(path, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
 

@@ -333,6 +333,7 @@ struct qqmc_plan {
     unsigned long long *d_counter = nullptr;
     double *d_out = nullptr;
     unsigned long long *d_counts = nullptr;
+    unsigned int *d_bad = nullptr;  // per shift: work units whose partial sum was not finite
     void *d_gstack = nullptr;       // FP64 tree stack in device memory (orders whose stack exceeds shared memory)
     long long gstack_warps = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ek0 = nullptr, ek1 = nullptr;
@@ -353,6 +354,7 @@ static void free_plan(qqmc_plan *pl) {
     cudaFree(pl->d_counter);
     cudaFree(pl->d_out);
     cudaFree(pl->d_counts);
+    cudaFree(pl->d_bad);
     cudaFree(pl->d_gstack);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
@@ -429,9 +431,11 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_shifts, sizeof(uint32_t) * shift_words_total);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_partials, sizeof(double) * 4 * chunk_total);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_inside, sizeof(unsigned int) * chunk_total);
-    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counter, (kMaxOrder + 2) * sizeof(unsigned long long));
+    // work counters (one per launch) and, after them, the execution span of the determinant launches
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_counter, (kMaxOrder + 4) * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_out, sizeof(double) * 2 * pl->total_shifts);
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_counts, sizeof(unsigned long long) * pl->total_shifts);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_bad, sizeof(unsigned int) * pl->total_shifts);
     if (e != cudaSuccess) {
         free_plan(pl);
         return set_error(QQMC_E_NOMEM, std::string("device allocation of the plan failed: ") + cudaGetErrorString(e));
@@ -557,9 +561,13 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     return QQMC_OK;
 }
 
+static unsigned long long *plan_span(const qqmc_plan *pl) { return pl->d_counter + kMaxOrder + 2; }
+
 static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
     const int ng = (int)pl->groups.size();
     cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, (ng + 1) * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan_span(pl), 0xff, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan_span(pl) + 1, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (timed && (e = cudaEventRecord(pl->ek0, s)) != cudaSuccess) return e;
     for (int gi = 0; gi < ng; ++gi) {
@@ -568,16 +576,17 @@ static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
         // a group sized without one gets none, and then runs the shared-memory stack or fails cleanly
         const long long w = g.gstack_warps;
         e = launch_detsum(pl->d_items + g.first, g.count, g.chunks, pl->d_counter + gi, g.n_max, pl->precision, g.tune,
-                          w > 0 ? pl->d_gstack : nullptr, w, s);
+                          w > 0 ? pl->d_gstack : nullptr, w, plan_span(pl), s);
         if (e != cudaSuccess) return e;
     }
     const int n_lane = (int)pl->items.size() - pl->n_warp;
     if (n_lane > 0) {
-        e = launch_lane(pl->d_items + pl->n_warp, n_lane, pl->chunks_lane, pl->d_counter + ng, pl->precision, s);
+        e = launch_lane(pl->d_items + pl->n_warp, n_lane, pl->chunks_lane, pl->d_counter + ng, pl->precision,
+                        plan_span(pl), s);
         if (e != cudaSuccess) return e;
     }
     if (timed && (e = cudaEventRecord(pl->ek1, s)) != cudaSuccess) return e;
-    return launch_reduce(pl->d_items, (int)pl->items.size(), pl->total_shifts, pl->d_out, pl->d_counts, s);
+    return launch_reduce(pl->d_items, (int)pl->items.size(), pl->total_shifts, pl->d_out, pl->d_counts, pl->d_bad, s);
 }
 
 extern "C" int qqmc_plan_launch(qqmc_plan *pl, void *stream, int use_graph) {
@@ -641,12 +650,12 @@ extern "C" int qqmc_plan_timing(const qqmc_plan *pl, double *kernel_ms, double *
     return QQMC_OK;
 }
 
-static void finish_result(const qqmc_item &it, const double *S, const unsigned long long *cnt, float ms,
-                          qqmc_result *r) {
+static void finish_result(const qqmc_item &it, const double *S, const unsigned long long *cnt,
+                          const unsigned int *bad, float ms, qqmc_result *r) {
     const int K = it.n_shifts;
     const double N = (double)it.n_points;
     double mean = 0.0, imax = 0.0;
-    uint64_t nin = 0;
+    uint64_t nin = 0, nbad = 0;
     std::vector<double> q(K);
     const bool current = it.problem->params.observable == QQMC_OBS_CURRENT;
     for (int k = 0; k < K; ++k) {
@@ -657,6 +666,7 @@ static void finish_result(const qqmc_item &it, const double *S, const unsigned l
         mean += q[k];
         imax = fabs(qi) > imax ? fabs(qi) : imax;
         nin += cnt[k];
+        nbad += bad[k];
     }
     mean /= K;
     double var = 0.0;
@@ -669,6 +679,7 @@ static void finish_result(const qqmc_item &it, const double *S, const unsigned l
     r->q_imag_absmax = imax;
     r->n_in_domain = nin;
     r->device_ms = ms;
+    r->n_nonfinite = nbad;
 }
 
 extern "C" int qqmc_plan_results(qqmc_plan *pl, qqmc_result *results, double *per_shift) {
@@ -680,10 +691,15 @@ extern "C" int qqmc_plan_results(qqmc_plan *pl, qqmc_result *results, double *pe
     cudaEventElapsedTime(&ms, pl->ev0, pl->ev1);
     std::vector<double> S(2 * (size_t)pl->total_shifts);
     std::vector<unsigned long long> cnt(pl->total_shifts);
+    std::vector<unsigned int> bad(pl->total_shifts);
     e = cudaMemcpy(S.data(), pl->d_out, sizeof(double) * S.size(), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
         e = cudaMemcpy(cnt.data(), pl->d_counts, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(bad.data(), pl->d_bad, sizeof(unsigned int) * bad.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "result download");
+    uint64_t nbad = 0;
+    int first_bad = -1;
     // per-shift outputs are in device order; caller offsets for per_shift
     const size_t n_items = pl->items.size();
     std::vector<size_t> user_off(n_items + 1, 0);
@@ -692,7 +708,11 @@ extern "C" int qqmc_plan_results(qqmc_plan *pl, qqmc_result *results, double *pe
     for (size_t q = 0; q < n_items; ++q) {
         const int i = pl->perm[q];
         const qqmc_item &it = pl->items[i];
-        if (results) finish_result(it, S.data() + 2 * g, cnt.data() + g, ms, &results[i]);
+        for (int k = 0; k < it.n_shifts; ++k) {
+            nbad += bad[g + k];
+            if (bad[g + k] && first_bad < 0) first_bad = i;
+        }
+        if (results) finish_result(it, S.data() + 2 * g, cnt.data() + g, bad.data() + g, ms, &results[i]);
         if (per_shift)
             for (int k = 0; k < it.n_shifts; ++k) {
                 per_shift[2 * (user_off[i] + k)] = S[2 * (g + k)] / (double)it.n_points;
@@ -700,6 +720,23 @@ extern "C" int qqmc_plan_results(qqmc_plan *pl, qqmc_result *results, double *pe
             }
         g += it.n_shifts;
     }
+    if (nbad)
+        return set_error(QQMC_E_NONFINITE, std::to_string(nbad) + " work unit(s) gave a NaN or infinite integrand sum "
+                                           "(first affected item " + std::to_string(first_bad) +
+                                           "); check the Green-function tables");
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_plan_device_span(const qqmc_plan *pl, uint64_t *start_ns, uint64_t *end_ns) {
+    if (!pl || !pl->launched || !start_ns || !end_ns)
+        return set_error(QQMC_E_INVAL, "qqmc_plan_device_span: plan not launched or NULL output");
+    cudaError_t e = cudaEventSynchronize(pl->ev1);
+    if (e != cudaSuccess) return cuda_error(e, "plan execution");
+    unsigned long long v[2];
+    e = cudaMemcpy(v, plan_span(pl), sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "span download");
+    *start_ns = v[0];
+    *end_ns = v[1];
     return QQMC_OK;
 }
 

@@ -1167,15 +1167,44 @@ __device__ __forceinline__ void point_gap(const ItemDev &I, int m, uint32_t y, d
     }
 }
 
+// The item owning global work unit c: the last item whose chunk_begin <= c
+// (items are laid out with ascending chunk_begin), by bisection.
+__device__ __forceinline__ int item_of(const ItemDev *__restrict__ items, int n_items, long long c) {
+    int lo = 0, hi = n_items;  // items[lo].chunk_begin <= c < items[hi].chunk_begin
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (items[mid].chunk_begin <= c) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Device clock (ns) for the execution span of a launch: span[0] = earliest warp
+// start, span[1] = latest warp exit, over every launch that shares the span.
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// A work unit's in-domain count carries this bit when its partial sum is not
+// finite (NaN or infinite: non-finite tables, or an overflow).
+constexpr unsigned kNonFinite = 0x80000000u;
+
+__device__ __forceinline__ unsigned unit_flag(double a, double b, double c, double d) {
+    return (isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d)) ? 0u : kNonFinite;
+}
+
 // ----------------------------------------------------------------------------
 // Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
 // ----------------------------------------------------------------------------
 template <class R, int RFMAX, bool GS>
 __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
-                              unsigned long long *counter, int n_max, int rf_min, cx<R> *gstack) {
+                              unsigned long long *counter, int n_max, int rf_min, cx<R> *gstack,
+                              unsigned long long *span) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    if (span && lane == 0) atomicMin(span, gtimer());
     cx<R> *gst = nullptr;
     if (GS) gst = gstack + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * gstack_entries<R>(n_max, rf_min);
     WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, rf_min, GS), n_max, rf_min, gst);
@@ -1185,9 +1214,7 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
         if (lane == 0) c = atomicAdd(counter, 1ull);
         c = __shfl_sync(FULL, c, 0);
         if ((long long)c >= total_chunks) break;
-        int it = 0;
-        while (it + 1 < n_items && items[it + 1].chunk_begin <= (long long)c) ++it;
-        const ItemDev &I = items[it];
+        const ItemDev &I = items[item_of(items, n_items, (long long)c)];
         const int n = I.order;
         const long long local = (long long)c - I.chunk_begin;
         const int k = (int)(local / I.chunks_per_shift);
@@ -1249,9 +1276,11 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             pp[1] = si;
             pp[2] = cr;
             pp[3] = ci;
-            I.inside[local] = sub == 0 ? __popc(mask) : 0u;  // a point counts once, in subtree 0
+            // a point counts once, in subtree 0
+            I.inside[local] = (sub == 0 ? __popc(mask) : 0u) | unit_flag(sr, si, cr, ci);
         }
     }
+    if (span && lane == 0) atomicMax(span + 1, gtimer());
 }
 
 // ----------------------------------------------------------------------------
@@ -1288,16 +1317,16 @@ __device__ __forceinline__ cx<double> lane_point(const ItemDev &I, int k, uint64
 
 template <class R>
 __global__ void __launch_bounds__(128) lane_kernel(const ItemDev *__restrict__ items, int n_items,
-                                                   long long total_chunks, unsigned long long *counter) {
+                                                   long long total_chunks, unsigned long long *counter,
+                                                   unsigned long long *span) {
     const int lane = threadIdx.x & 31;
+    if (span && lane == 0) atomicMin(span, gtimer());
     while (true) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(counter, 1ull);
         c = __shfl_sync(FULL, c, 0);
         if ((long long)c >= total_chunks) break;
-        int it = 0;
-        while (it + 1 < n_items && items[it + 1].chunk_begin <= (long long)c) ++it;
-        const ItemDev &I = items[it];
+        const ItemDev &I = items[item_of(items, n_items, (long long)c)];
         const long long local = (long long)c - I.chunk_begin;
         const int k = (int)(local / I.chunks_per_shift);
         const long long blk = local - (long long)k * I.chunks_per_shift;
@@ -1323,18 +1352,33 @@ __global__ void __launch_bounds__(128) lane_kernel(const ItemDev *__restrict__ i
             pp[1] = si;
             pp[2] = cr;
             pp[3] = ci;
-            I.inside[local] = __popc(mask);
+            I.inside[local] = __popc(mask) | unit_flag(sr, si, cr, ci);
         }
     }
+    if (span && lane == 0) atomicMax(span + 1, gtimer());
 }
 
 // Per shifted sequence: compensated sum of its chunk partials in a fixed order.
 // out[2*g], out[2*g+1] = sum_i w_i c_n(u_i) (complex, not divided by N);
-// counts[g] = in-domain points.  One block of 256 threads per sequence.
+// counts[g] = in-domain points; bad[g] (if bad is not null) = work units whose
+// partial sum was not finite.  One block of 256 threads per sequence: each
+// thread sums its strided share of the units with two-sum, then the block
+// combines the (sum, compensation) pairs in a fixed tree, also with two-sum.
+struct TwoSum {
+    double s, c;
+    __device__ __forceinline__ void add(double x) {
+        double t, e;
+        two_sum(s, x, t, e);
+        s = t;
+        c += e;
+    }
+};
+
 __global__ void reduce_kernel(const ItemDev *__restrict__ items, int n_items, double *out,
-                              unsigned long long *counts) {
+                              unsigned long long *counts, unsigned int *bad) {
     __shared__ double s_re[256], c_re[256], s_im[256], c_im[256];
     __shared__ unsigned long long cnt[256];
+    __shared__ unsigned int nbad[256];
     int g = blockIdx.x;
     int it = 0, base = 0;
     while (it < n_items && g >= base + items[it].n_shifts) {
@@ -1346,22 +1390,24 @@ __global__ void reduce_kernel(const ItemDev *__restrict__ items, int n_items, do
     const int k = g - base;
     const double *pp = I.partials + 4 * (size_t)k * I.chunks_per_shift;
     const unsigned int *ins = I.inside + (size_t)k * I.chunks_per_shift;
-    Acc<double> ar, ai;
-    ar.init();
-    ai.init();
+    TwoSum ar = {0.0, 0.0}, ai = {0.0, 0.0};
     unsigned long long cn = 0;
+    unsigned int nb = 0;
     for (int q = threadIdx.x; q < I.chunks_per_shift; q += blockDim.x) {
         ar.add(pp[4 * q]);
         ar.add(pp[4 * q + 2]);
         ai.add(pp[4 * q + 1]);
         ai.add(pp[4 * q + 3]);
-        cn += ins[q];
+        const unsigned int v = ins[q];
+        cn += v & ~kNonFinite;
+        nb += v >> 31;
     }
     s_re[threadIdx.x] = ar.s;
     c_re[threadIdx.x] = ar.c;
     s_im[threadIdx.x] = ai.s;
     c_im[threadIdx.x] = ai.c;
     cnt[threadIdx.x] = cn;
+    nbad[threadIdx.x] = nb;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
@@ -1373,6 +1419,7 @@ __global__ void reduce_kernel(const ItemDev *__restrict__ items, int n_items, do
             s_im[threadIdx.x] = t;
             c_im[threadIdx.x] = c_im[threadIdx.x] + c_im[threadIdx.x + o] + e;
             cnt[threadIdx.x] += cnt[threadIdx.x + o];
+            nbad[threadIdx.x] += nbad[threadIdx.x + o];
         }
         __syncthreads();
     }
@@ -1380,6 +1427,7 @@ __global__ void reduce_kernel(const ItemDev *__restrict__ items, int n_items, do
         out[2 * g] = s_re[0] + c_re[0];
         out[2 * g + 1] = s_im[0] + c_im[0];
         counts[g] = cnt[0];
+        if (bad) bad[g] = nbad[0];
     }
 }
 
@@ -1791,7 +1839,7 @@ static bool stack_in_global(int n_max, int rf_min) {
 template <class R, int F, bool GS>
 static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
-                                   long long gstack_warps, cudaStream_t s) {
+                                   long long gstack_warps, unsigned long long *span, cudaStream_t s) {
     // fewer warps per block when the shared memory of the requested shape does not fit
     const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min, GS);
     if (per_warp > kSmemMax) return cudaErrorInvalidConfiguration;
@@ -1815,19 +1863,20 @@ static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long lon
     }
     if (grid < 1) return cudaErrorInvalidConfiguration;
     detsum_kernel<R, F, GS><<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max,
-                                                                    rf_min, static_cast<cx<R> *>(gstack));
+                                                                    rf_min, static_cast<cx<R> *>(gstack), span);
     return cudaGetLastError();
 }
 
 template <class R, int F>
 static cudaError_t launch_detsum_f(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
-                                   long long gstack_warps, cudaStream_t s) {
+                                   long long gstack_warps, unsigned long long *span, cudaStream_t s) {
     // without a device-memory buffer (the allocation-free entry) the shared-memory stack serves where it fits
     if (stack_in_global<R>(n_max, rf_min) && (gstack || warp_smem_bytes<R>(n_max, rf_min) > kSmemMax))
         return launch_detsum_t<R, F, true>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack,
-                                           gstack_warps, s);
-    return launch_detsum_t<R, F, false>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, nullptr, 0, s);
+                                           gstack_warps, span, s);
+    return launch_detsum_t<R, F, false>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, nullptr, 0,
+                                        span, s);
 }
 
 static int clamp_rf_min(const Tuning &tune) {
@@ -1862,11 +1911,12 @@ long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size
 
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                           int n_max, int precision, const Tuning &tune, void *gstack, long long gstack_warps,
-                          cudaStream_t s) {
+                          unsigned long long *span, cudaStream_t s) {
     const int wpb = tune.warps_per_block;
     const int rf_min = clamp_rf_min(tune);
 #define QQMC_DETSUM(RT, F)                                                                                        \
-    launch_detsum_f<RT, F>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack, gstack_warps, s)
+    launch_detsum_f<RT, F>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack, gstack_warps, \
+                           span, s)
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
             case 2: return QQMC_DETSUM(double, 2);
@@ -1886,7 +1936,7 @@ cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_c
 
 template <class R>
 static cudaError_t launch_lane_t(const ItemDev *d_items, int n_items, long long total_chunks,
-                                 unsigned long long *d_counter, cudaStream_t s) {
+                                 unsigned long long *d_counter, unsigned long long *span, cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1897,20 +1947,30 @@ static cudaError_t launch_lane_t(const ItemDev *d_items, int n_items, long long 
     long long grid = (long long)sms * per_sm;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    lane_kernel<R><<<(unsigned)grid, 128, 0, s>>>(d_items, n_items, total_chunks, d_counter);
+    lane_kernel<R><<<(unsigned)grid, 128, 0, s>>>(d_items, n_items, total_chunks, d_counter, span);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
-                        int precision, cudaStream_t s) {
+                        int precision, unsigned long long *span, cudaStream_t s) {
     if (n_items < 1 || total_chunks < 1) return cudaSuccess;
-    return precision == QQMC_PREC_FP64 ? launch_lane_t<double>(d_items, n_items, total_chunks, d_counter, s)
-                                       : launch_lane_t<float>(d_items, n_items, total_chunks, d_counter, s);
+    return precision == QQMC_PREC_FP64 ? launch_lane_t<double>(d_items, n_items, total_chunks, d_counter, span, s)
+                                       : launch_lane_t<float>(d_items, n_items, total_chunks, d_counter, span, s);
 }
 
 cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out,
-                          unsigned long long *d_counts, cudaStream_t s) {
-    reduce_kernel<<<total_shifts, 256, 0, s>>>(d_items, n_items, d_out, d_counts);
+                          unsigned long long *d_counts, unsigned int *d_bad, cudaStream_t s) {
+    reduce_kernel<<<total_shifts, 256, 0, s>>>(d_items, n_items, d_out, d_counts, d_bad);
+    return cudaGetLastError();
+}
+
+__global__ void store_item_kernel(ItemDev item, ItemDev *dst, unsigned long long *counter) {
+    *dst = item;
+    *counter = 0ull;
+}
+
+cudaError_t launch_store_item(const ItemDev &item, ItemDev *d_item, unsigned long long *d_counter, cudaStream_t s) {
+    store_item_kernel<<<1, 1, 0, s>>>(item, d_item, d_counter);
     return cudaGetLastError();
 }
 

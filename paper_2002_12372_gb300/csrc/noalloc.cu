@@ -31,6 +31,9 @@ constexpr size_t kCountsOff = 512;                       // n_shifts x uint64 (u
 constexpr size_t kPartialsOff = kCountsOff + 1024 * 8;  // chunks x 4 doubles
 constexpr size_t kPerChunk = 4 * sizeof(double) + sizeof(unsigned int);
 constexpr size_t kMaxChunks = (kScratchBytes - kPartialsOff) / kPerChunk;
+static_assert(sizeof(ItemDev) <= kCounterOff - kItemOff, "the item descriptor overlaps the work counter");
+static_assert(kCounterOff % 8 == 0 && kCountsOff % 8 == 0 && kPartialsOff % 8 == 0,
+              "scratch areas must be 8-byte aligned");
 
 std::mutex g_mu;
 unsigned char *g_dev_ptr[64];  // device address of g_scratch, per device
@@ -76,6 +79,13 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
         return set_error(QQMC_E_INVAL,
                          "qqmc_integrate_noalloc: n_shifts * ceil(n_points / 32) exceeds the static scratch (" +
                              std::to_string(kMaxChunks) + " chunks of 32 points)");
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return cuda_error(de, "cudaGetDevice");
+    if (dev != P->device)
+        return set_error(QQMC_E_INVAL, "qqmc_integrate_noalloc: the problem's tables are on device " +
+                                           std::to_string(P->device) + " but device " + std::to_string(dev) +
+                                           " is current");
     unsigned char *base = nullptr;
     int rc = setup_device(&base);
     if (rc != QQMC_OK) return rc;
@@ -122,15 +132,17 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
     unsigned long long *d_counter = reinterpret_cast<unsigned long long *>(base + kCounterOff);
     unsigned long long *counts = d_counts ? d_counts : reinterpret_cast<unsigned long long *>(base + kCountsOff);
 
-    cudaError_t e = cudaMemcpyAsync(d_item, &it, sizeof(ItemDev), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
+    // The descriptor travels as a kernel argument (copied when the launch is enqueued), so
+    // the call reads no host memory after it returns and makes no pageable copy.
+    cudaError_t e = launch_store_item(it, d_item, d_counter, s);
     if (e == cudaSuccess) {
         if (it.flat == 1 && order <= kLaneMaxOrder)
-            e = launch_lane(d_item, 1, (long long)(cps * n_shifts), d_counter, precision, s);
+            e = launch_lane(d_item, 1, (long long)(cps * n_shifts), d_counter, precision, nullptr, s);
         else
-            e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, nullptr, 0, s);
+            e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, nullptr, 0,
+                              nullptr, s);
     }
-    if (e == cudaSuccess) e = launch_reduce(d_item, 1, n_shifts, d_sums, counts, s);
+    if (e == cudaSuccess) e = launch_reduce(d_item, 1, n_shifts, d_sums, counts, nullptr, s);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrate_noalloc");
     return QQMC_OK;
 }

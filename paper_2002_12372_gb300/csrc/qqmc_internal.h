@@ -80,23 +80,28 @@ void shift_words(uint64_t seed, int n_shifts, int n_dims, uint32_t *out);
 int upload_direction_numbers();
 int launch_gf_table(const Problem &pr, cudaStream_t s);
 int launch_lead_table(Problem &pr, cudaStream_t s, double *zero);
+// span (may be null): [earliest warp start, latest warp exit] of the launch in device-clock ns,
+// merged with atomicMin / atomicMax (the caller initialises it to [~0, 0]).
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                           int n_max, int precision, const Tuning &tune, void *gstack, long long gstack_warps,
-                          cudaStream_t s);
+                          unsigned long long *span, cudaStream_t s);
 // Warps (and bytes per warp) of device memory the determinant launch needs for
 // its tree stack; 0 when the stack fits in shared memory.
 long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp);
 void set_stack_policy(int precision, int min_order);
 bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune);
 cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
-                        int precision, cudaStream_t s);
+                        int precision, unsigned long long *span, cudaStream_t s);
 constexpr int kLaneMaxOrder = 4;  // orders that may run one point per lane
 // Bits of the leaf index of an order's Keldysh tree (a_2, then two per
 // depth-first pair level); work units may fix a prefix of them.
 int tree_leaf_bits(int order);
+// d_bad (may be null): per shift, the work units whose partial sum was not finite.
 cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out, unsigned long long *d_counts,
-                          cudaStream_t s);
+                          unsigned int *d_bad, cudaStream_t s);
 size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune);
+// One thread writes the item descriptor (a kernel argument) to d_item and zeroes the work counter.
+cudaError_t launch_store_item(const ItemDev &item, ItemDev *d_item, unsigned long long *d_counter, cudaStream_t s);
 cudaError_t launch_sobol(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, uint32_t *d_out,
                          const uint32_t *d_lat_z, int lat_m, cudaStream_t s);
 cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, double t, double tau,

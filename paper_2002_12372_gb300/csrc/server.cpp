@@ -42,6 +42,7 @@ struct Req {
 };
 
 struct Batch {
+    uint64_t id = 0;  // admission round
     std::vector<uint64_t> handles;
     std::vector<qqmc_problem *> problems;
     qqmc_plan *plan = nullptr;
@@ -68,6 +69,7 @@ struct qqmc_server {
     std::unordered_map<uint64_t, Req> reqs;
     std::vector<Batch> inflight;
     uint64_t next_handle = 1;
+    uint64_t next_batch = 1;
     uint64_t bytes_in_use = 0;
     bool stop = false;
     std::thread worker;
@@ -103,6 +105,8 @@ void qqmc_server::finish_batch(Batch &b) {
     }
     std::vector<qqmc_result> res(n_items);
     int rc = qqmc_plan_results(b.plan, res.data(), nullptr);
+    uint64_t t0 = 0, t1 = 0;
+    if (rc == QQMC_OK || rc == QQMC_E_NONFINITE) qqmc_plan_device_span(b.plan, &t0, &t1);
     Clock::time_point now = Clock::now();
     std::lock_guard<std::mutex> lk(mu);
     size_t off = 0;
@@ -113,11 +117,16 @@ void qqmc_server::finish_batch(Batch &b) {
             continue;
         }
         Req &R = it->second;
+        // a non-finite sum fails only the requests whose own items carry it
+        bool bad = false;
+        if (rc == QQMC_E_NONFINITE)
+            for (int n = 1; n <= nmax[q]; ++n) bad = bad || res[off + n - 1].n_nonfinite != 0;
+        const int rq = bad ? QQMC_E_NONFINITE : (rc == QQMC_E_NONFINITE ? QQMC_OK : rc);
         if (R.state == ADMITTED) {
-            if (rc != QQMC_OK) {
+            if (rq != QQMC_OK) {
                 R.state = FAILED;
-                R.status = rc;
-                R.out.status = rc;
+                R.status = rq;
+                R.out.status = rq;
             } else {
                 double U = R.r.U, Un = 1.0, sum = R.out.q[0];
                 for (int n = 1; n <= R.r.n_max; ++n) {
@@ -129,6 +138,9 @@ void qqmc_server::finish_batch(Batch &b) {
                     sum += x.q_mean * Un;
                 }
                 R.out.series_sum = sum;
+                R.out.batch = b.id;
+                R.out.device_start_ns = t0;
+                R.out.device_end_ns = t1;
                 R.out.latency_ms = std::chrono::duration<double, std::milli>(now - R.t_submit).count();
                 R.out.status = QQMC_OK;
                 R.state = DONE;
@@ -209,6 +221,7 @@ void qqmc_server::run() {
             std::vector<qqmc_request> rq;
             for (uint64_t h : admit) rq.push_back(reqs[h].r);
             Batch b;
+            b.id = next_batch++;
             b.handles = admit;
             for (uint64_t h : admit) b.bytes += reqs[h].bytes;
             lk.unlock();
@@ -326,6 +339,17 @@ extern "C" int qqmc_poll(qqmc_server *s, uint64_t handle, qqmc_series *out) {
     int st = R.status;
     s->reqs.erase(it);
     return st;
+}
+
+extern "C" int qqmc_request_state(qqmc_server *s, uint64_t handle) {
+    if (!s) return set_error(QQMC_E_INVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(handle);
+    if (it == s->reqs.end()) return set_error(QQMC_E_NOTFOUND, "unknown handle");
+    const Req &R = it->second;
+    if (R.state == PENDING) return QQMC_PENDING;
+    if (R.state == ADMITTED) return QQMC_RUNNING;
+    return R.status;
 }
 
 extern "C" int qqmc_cancel(qqmc_server *s, uint64_t handle) {

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libqqmc.so")
 
 QQMC_OK = 0
 QQMC_PENDING = 1
+QQMC_RUNNING = 2
 QQMC_E_INVAL = -1
 QQMC_E_RANGE = -2
 QQMC_E_NOMEM = -3
@@ -28,6 +29,7 @@ QQMC_E_BUSY = -5
 QQMC_E_TIMEOUT = -6
 QQMC_E_CANCELLED = -7
 QQMC_E_NOTFOUND = -8
+QQMC_E_NONFINITE = -9
 QQMC_MAX_ORDER = 22
 QQMC_PREC_FP64 = 0
 QQMC_PREC_MIXED = 1
@@ -43,7 +45,7 @@ EXPORTED = [
     "qqmc_submit", "qqmc_poll", "qqmc_cancel", "qqmc_server_destroy", "qqmc_last_error",
     "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola", "qqmc_set_projection",
     "qqmc_learn_projection", "qqmc_set_current_tables", "qqmc_problem_current_tables", "qqmc_set_lattice",
-    "qqmc_lattice_cbc", "qqmc_set_stack_policy",
+    "qqmc_lattice_cbc", "qqmc_set_stack_policy", "qqmc_plan_device_span", "qqmc_request_state",
 ]
 
 
@@ -57,7 +59,7 @@ class qqmc_params(ctypes.Structure):
 class qqmc_result(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("n_shifts", ctypes.c_int32), ("n_points", ctypes.c_uint64),
                 ("q_mean", ctypes.c_double), ("q_err", ctypes.c_double), ("q_imag_absmax", ctypes.c_double),
-                ("n_in_domain", ctypes.c_uint64), ("device_ms", ctypes.c_double)]
+                ("n_in_domain", ctypes.c_uint64), ("device_ms", ctypes.c_double), ("n_nonfinite", ctypes.c_uint64)]
 
 
 class qqmc_item(ctypes.Structure):
@@ -81,7 +83,8 @@ class qqmc_series(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("q", ctypes.c_double * (QQMC_MAX_ORDER + 1)), ("q_err", ctypes.c_double * (QQMC_MAX_ORDER + 1)),
                 ("series_sum", ctypes.c_double), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
-                ("n_in_domain", ctypes.c_uint64)]
+                ("n_in_domain", ctypes.c_uint64), ("batch", ctypes.c_uint64), ("device_start_ns", ctypes.c_uint64),
+                ("device_end_ns", ctypes.c_uint64)]
 
 
 _lib = None
@@ -135,6 +138,8 @@ def load(path: str = LIB_PATH):
         "qqmc_set_stack_policy": [ctypes.c_int, ctypes.c_int],
         "qqmc_lattice_cbc": [ctypes.c_int, ctypes.c_int, dp, u32p],
         "qqmc_problem_current_tables": [vp, dp, dp, dp],
+        "qqmc_plan_device_span": [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)],
+        "qqmc_request_state": [vp, ctypes.c_uint64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -283,11 +288,15 @@ class Plan:
         _check(load().qqmc_plan_launch(ctypes.c_void_p(self.handle), ctypes.c_void_p(stream or None),
                                        int(use_graph)), "qqmc_plan_launch")
 
-    def results(self):
+    def results(self, check: bool = True):
+        """[(qqmc_result, S_k per shift)] per item.  check=False returns the results of a
+        plan whose sums hit NaN or infinity (QQMC_E_NONFINITE) instead of raising; the
+        affected items carry n_nonfinite > 0."""
         res = (qqmc_result * self.n_items)()
         per = np.zeros(2 * sum(self.n_shifts))
-        _check(load().qqmc_plan_results(ctypes.c_void_p(self.handle), res, _ptr(per, ctypes.c_double)),
-               "qqmc_plan_results")
+        rc = load().qqmc_plan_results(ctypes.c_void_p(self.handle), res, _ptr(per, ctypes.c_double))
+        if check or rc != QQMC_E_NONFINITE:
+            _check(rc, "qqmc_plan_results")
         S = per.view(np.complex128)
         out, o = [], 0
         for i in range(self.n_items):
@@ -301,6 +310,13 @@ class Plan:
         _check(load().qqmc_plan_timing(ctypes.c_void_p(self.handle), ctypes.byref(k), ctypes.byref(a)),
                "qqmc_plan_timing")
         return k.value, a.value
+
+    def device_span(self):
+        """(start_ns, end_ns) of the last launch's determinant kernels on the device clock."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().qqmc_plan_device_span(ctypes.c_void_p(self.handle), ctypes.byref(a), ctypes.byref(b)),
+               "qqmc_plan_device_span")
+        return a.value, b.value
 
     def chunk_sums(self, item: int, shift: int, chunks) -> np.ndarray:
         """Complex per-chunk sums (sum + compensation) of the last launch."""
@@ -436,6 +452,11 @@ def qqmc_poll(server: int, handle: int):
     if rc == QQMC_PENDING:
         return rc, None
     return rc, out
+
+
+def qqmc_request_state(server: int, handle: int) -> int:
+    """QQMC_PENDING (queued), QQMC_RUNNING (admitted) or the final status; the handle stays."""
+    return load().qqmc_request_state(ctypes.c_void_p(server), handle)
 
 
 def qqmc_cancel(server: int, handle: int) -> int:

@@ -195,6 +195,22 @@ def test_single_level_flat_occupation_cancels_at_every_order(Q, W, oracle):
         Q.qqmc_destroy_problem(pr)
 
 
+def test_one_long_shift_reduces_like_the_oracle(Q, W, oracle):
+    """One shifted sequence of N = 2^20 points: 32768 chunk partials, 128 per thread of the
+    reduction block, summed with two-sum per thread and across the block; the per-shift sum
+    matches the oracle's (Neumaier per chunk, exactly rounded across chunks) to 1e-10."""
+    T, order, N = 10.0, 2, 2 ** 20
+    pr, tabs = _problem(Q, W, seed=17, T=T)
+    try:
+        sw = W.shift_words(19, 1, order)
+        res, S = Q.qqmc_integrate(pr, order, N, 1, Q.QQMC_PREC_FP64, sw)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    S0, nin = oracle.estimate(order, N, sw, T, 1.0, tabs, T)
+    assert res.n_in_domain == int(nin.sum())
+    assert np.all(np.abs(S - S0) <= 1e-10 * np.abs(S0)), (S, S0)
+
+
 @pytest.mark.parametrize("order,N", [(3, 4096), (6, 2048), (9, 512)])
 def test_integration_mixed_within_stated_bound_of_fp64(Q, W, oracle, order, N):
     """Mixed precision (FP32 tables and Schur updates, compensated FP32 leaf sums,

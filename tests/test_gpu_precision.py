@@ -1,0 +1,75 @@
+"""Precision pattern: the mixed path (FP32 tables, pair values, Schur updates
+and 2x2 block pivots; compensated FP32 leaf sums; FP64 point and shift sums)
+against the FP64 oracle on the same points.
+
+The bar per shifted sequence follows from the per-point bar of the mixed path,
+|c_mixed - c| <= 2^-20 sum_a |term_a|: summed with the point weights,
+|S_mixed - S| <= 2^-20 (1/N) sum_i w_i sum_a |term_a(u_i)|, both sums taken by
+the oracle at the warped points.
+
+``test_mixed_precision_table`` (opt-in: QQMC_PRECISION_TABLE=1) prints the
+per-order table of the precision configuration, orders 6..12 on the first 2^16
+Sobol' indices of two shifts; the default suite checks order 10 on 2^12.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2002_12372_gb300 import build as b
+    b.build()
+    from paper_2002_12372_gb300 import qqmc
+    qqmc.load()
+    return qqmc
+
+
+def _compare(Q, oracle, order, N, K, T=10.0, tau=1.0, L=4096):
+    """Mixed-path and oracle per-shift sums of the plain dot (eps_d = 0 tables from the
+    oracle's closed form on both sides); returns (S_mixed, S_oracle, bound, S_fp64)."""
+    from paper_2002_12372_gb300 import workloads as W
+    tabs = oracle.gf_tables(1.0, 0.0, T, L)
+    sw = W.shift_words(6000 + order, K, order)
+    pr = Q.qqmc_create_problem_tables(Q.make_params(t_max=T, tau=tau, n_table=L), *tabs)
+    try:
+        _, Sm = Q.qqmc_integrate(pr, order, N, K, Q.QQMC_PREC_MIXED, sw)
+        _, S64 = Q.qqmc_integrate(pr, order, N, K, Q.QQMC_PREC_FP64, sw)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+    V = oracle.sobol_direction_numbers(order)
+    S0, _ = oracle.estimate(order, N, sw, T, tau, tabs, T, V=V)
+    bound = np.zeros(K)
+    for k in range(K):
+        u, w, ins = oracle.warp(order, 0, N, V, sw[k], T, tau)
+        _, scale = oracle.integrand(order, u[ins], T, tabs, T, return_abs=True)
+        bound[k] = 2.0 ** -20 * np.sum(w[ins] * scale) / N
+    return Sm, S0, bound, S64
+
+
+def test_mixed_at_order_10_within_its_bound_of_the_oracle(Q, oracle):
+    Sm, S0, bound, S64 = _compare(Q, oracle, 10, 4096, 2)
+    assert np.all(np.abs(S64 - S0) <= 1e-10 * np.abs(S0))
+    assert np.all(np.abs(Sm - S0) <= bound), (np.abs(Sm - S0), bound)
+
+
+@pytest.mark.skipif(not os.environ.get("QQMC_PRECISION_TABLE"), reason="opt-in: minutes of oracle time")
+def test_mixed_precision_table(Q, oracle):
+    N, K = 2 ** 16, 2
+    print("\n| n | max_k |S_mixed - S_oracle| | bound | max_k |S_oracle| | dev / |S| | FP64 dev / |S| |")
+    print("|---|---|---|---|---|---|")
+    for n in range(6, 13):
+        Sm, S0, bound, S64 = _compare(Q, oracle, n, N, K)
+        dev = np.max(np.abs(Sm - S0))
+        rel = np.max(np.abs(Sm - S0) / np.abs(S0))
+        rel64 = np.max(np.abs(S64 - S0) / np.abs(S0))
+        print("| %d | %.3e | %.3e | %.3e | %.2e | %.2e |" % (n, dev, np.max(bound), np.max(np.abs(S0)), rel, rel64),
+              flush=True)
+        assert np.all(np.abs(Sm - S0) <= bound)
+        assert np.all(np.abs(S64 - S0) <= 1e-10 * np.abs(S0))
