@@ -143,6 +143,15 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def tree_shape(Q, pr, prec: int, n: int):
+    """(pair-block tree?, flat depth) that order n of problem pr runs with: the problem's
+    elimination order and that tree's tuned flat depth (one-point-per-lane orders resolve
+    all n - 1 vertices after the first per lane, with vertex pairs)."""
+    pairs = Q.qqmc_elimination(pr, prec) == Q.QQMC_ELIM_PAIRS
+    f = Q.qqmc_get_tuning(prec | (Q.QQMC_TUNE_PAIRS if pairs else 0), n)[1]
+    return (pairs or f < 2), (f if f >= 2 else n - 1)
+
+
 def workload_items(Q, problems, s: int, slice_n: int = SLICE):
     """Items of step s: every (eps_d, n) over Sobol' slice s (shift words from the seed)."""
     first = (s % (N_TOTAL // slice_n)) * slice_n
@@ -178,10 +187,13 @@ def run_ours(args, ws, rank, local, pg):
     n_plans = min(args.steps + args.warmup, N_TOTAL // slice_n)
     plans = [Q.Plan(workload_items(Q, problems, s, slice_n), prec) for s in range(n_plans)]
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
-    wpb, flat = Q.qqmc_get_tuning(prec, max(ORDERS))
-    # every item runs with its own order's tuned flat depth (one launch per shape group);
-    # one-point-per-lane orders (flat 1) resolve all their vertices per lane
-    flat_of = {n: (lambda f: f if f >= 2 else n - 1)(Q.qqmc_get_tuning(prec, n)[1]) for n in ORDERS}
+    # every item runs with its own order's tuned flat depth on its problem's Keldysh-sum tree
+    # (one launch per shape group); one-point-per-lane orders (flat 1) resolve all their
+    # vertices per lane with vertex pairs
+    shape_of = {(id(pr), n): tree_shape(Q, pr, prec, n) for pr in problems for n in ORDERS}
+    pairs0, flat = shape_of[(id(problems[0]), max(ORDERS))]
+    wpb = Q.qqmc_get_tuning(prec | (Q.QQMC_TUNE_PAIRS if pairs0 else 0), max(ORDERS))[0]
+    flat_of = {n: shape_of[(id(problems[0]), n)][1] for n in ORDERS}
 
     def step(s):
         p = plans[s % n_plans]
@@ -210,11 +222,13 @@ def run_ours(args, ws, rank, local, pg):
         km, _ = p.timing()
         step_ms.append(ev0.elapsed_time(ev1))
         kern_ms.append(km)
-        for r, _S in res:
+        items = workload_items(Q, problems, s, slice_n)
+        for (r, _S), it in zip(res, items):
+            pairs, f = shape_of[(id(it[0]), r.order)]
             pts += r.n_points * r.n_shifts
             pts_in += r.n_in_domain
             dets += r.n_in_domain * 2.0 ** r.order
-            flops += r.n_in_domain * perf.flops_per_point(r.order, flat_of[r.order])
+            flops += r.n_in_domain * perf.flops_per_point(r.order, f, pairs)
             naive += r.n_in_domain * perf.w_naive(r.order)
     torch.cuda.synchronize()
     _barrier(pg)
@@ -470,9 +484,8 @@ def run_orders(args, local):
     rows = {}
     rate = 0.7e12 if prec == Q.QQMC_PREC_FP64 else 15e12
     for n in range(args.orders_min, args.orders_max + 1):
-        f = Q.qqmc_get_tuning(prec, n)[1]
-        f = f if f >= 2 else n - 1
-        want = args.orders_seconds * rate / perf.flops_per_point(n, f) / 16
+        pairs, f = tree_shape(Q, pr, prec, n)
+        want = args.orders_seconds * rate / perf.flops_per_point(n, f, pairs) / 16
         N = int(2 ** max(6, min(22, math.floor(math.log2(max(want, 1.0))))))
         plan = Q.Plan([(pr, n, 16, N)], prec)
         plan.launch(stream.cuda_stream)
@@ -485,7 +498,8 @@ def run_orders(args, local):
         rows[n] = {"N": N, "shifts": 16, "kernel_ms": km, "evals_per_s": N * 16 / secs,
                    "in_domain_evals_per_s": r.n_in_domain / secs,
                    "keldysh_det_evals_per_s": r.n_in_domain * 2.0 ** n / secs,
-                   "tflops": r.n_in_domain * perf.flops_per_point(n, f) / secs / 1e12, "flat": f}
+                   "tflops": r.n_in_domain * perf.flops_per_point(n, f, pairs) / secs / 1e12, "flat": f,
+                   "tree": "pairs" if pairs else "single"}
     Q.qqmc_destroy_problem(pr)
     n_head = min(max(10, args.orders_min), args.orders_max)
     return {"metric": "per_order_integrand_evals_per_s", "value": rows[n_head]["evals_per_s"],

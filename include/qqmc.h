@@ -76,6 +76,23 @@ extern "C" {
 #define QQMC_PREC_MIXED 1 /* tables and Schur updates in FP32, leaf sums two-sum
                              compensated, point and shift sums in FP64 */
 
+/* Elimination order of the Keldysh sum (qqmc_set_elimination).  Every vertex
+ * diagonal of M_down is g^<(0) - i alpha (App. E), which is zero at the
+ * Hartree-cancelling alpha = Im g^<(0); at particle-hole symmetry every odd
+ * leading minor of M_down then vanishes too.
+ *   QQMC_ELIM_SINGLE  one vertex per tree level, 1x1 pivots (the fastest; its
+ *                     pivots are ratios of consecutive leading minors);
+ *   QQMC_ELIM_PAIRS   vertex pairs (1,2), (3,4), ... with 2x2 block pivots
+ *                     (the even leading minors) and a lone last vertex without
+ *                     a reciprocal: exact where the vertex diagonal vanishes,
+ *                     about 10 % (FP64) to 30 % (mixed) more work;
+ *   QQMC_ELIM_AUTO    (default) pairs when |g^<(0) - i alpha| is below 0.01
+ *                     (FP64) or 0.25 (mixed) of max(|g^<(0)|, |g^>(0)|), with
+ *                     g^>(0) = g^<(0) - i; the single-vertex tree otherwise. */
+#define QQMC_ELIM_AUTO 0
+#define QQMC_ELIM_PAIRS 1
+#define QQMC_ELIM_SINGLE 2
+
 /* Physical problem and warp (paper: App. E model, App. F exponential h). */
 typedef struct qqmc_params {
     double gamma;       /* tunnelling rate Gamma at the Fermi level (Lorentzian half-width), > 0 */
@@ -176,6 +193,13 @@ int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims, 
  * before creating plans.  Errors: E_INVAL.
  */
 int qqmc_set_stack_policy(int precision, int min_order);
+
+/* Elimination order of a problem's Keldysh sums (QQMC_ELIM_*, see above);
+ * applies to plans and calls made afterwards.  Errors: E_INVAL. */
+int qqmc_set_elimination(qqmc_problem *pr, int mode);
+/* The order a problem's sums use at the given precision: QQMC_ELIM_PAIRS or
+ * QQMC_ELIM_SINGLE (QQMC_ELIM_AUTO resolved), or a negative error code. */
+int qqmc_elimination(const qqmc_problem *pr, int precision);
 
 /*
  * Component-by-component construction of a generating vector for N = 2^log2_n
@@ -307,8 +331,12 @@ int qqmc_plan_chunk_sums(const qqmc_plan *plan, int item, int shift, const int64
  * the whole Keldysh sum of its own point).  Values <= 0 restore the built-in defaults.  Applies to
  * plans created afterwards; in a plan every item runs with its own order's
  * flat depth, and the items of one flat depth share a launch with the warps
- * per block of their highest order.
+ * per block of their highest order.  Each elimination order has its own table:
+ * precision | QQMC_TUNE_PAIRS addresses the pair-block tree's (its flat depth
+ * counts vertices resolved per lane as well; with vertex pairs a lane takes
+ * flat_vertices or one fewer).
  */
+#define QQMC_TUNE_PAIRS 16
 int qqmc_set_tuning(int precision, int order, int warps_per_block, int flat_vertices);
 int qqmc_get_tuning(int precision, int order, int *warps_per_block, int *flat_vertices);
 

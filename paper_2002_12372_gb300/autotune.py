@@ -9,9 +9,12 @@ the launch it will share.  The candidates
 are warps per block (points in flight per block) and vertices resolved per
 lane in the flat phase (a lane's Keldysh chunk: one of 2^flat choice paths of
 the last vertices).  The fastest shape is installed with ``qqmc_set_tuning``
-and the table can be stored as JSON keyed by the GPU name.
+and the table can be stored as JSON keyed by the GPU name.  Each Keldysh-sum
+tree has its own table: the single-vertex tree under the precision code (0, 1),
+the pair-block tree under precision | QQMC_TUNE_PAIRS (16, 17); the tuning
+problem is set to the tree being tuned.
 
-    python -m paper_2002_12372_gb300.autotune [--orders 1-12] [--out tuning.json]
+    python -m paper_2002_12372_gb300.autotune [--orders 1-12] [--tree single|pairs|both] [--out tuning.json]
 """
 from __future__ import annotations
 
@@ -33,6 +36,10 @@ LANE_CANDIDATES = {
 }
 
 
+def _precision(code: int) -> int:
+    return code & ~Q.QQMC_TUNE_PAIRS
+
+
 def _points_for(order: int, precision: int) -> int:
     # Large enough that the grid drains the way a full batch does (tens of
     # chunks per resident warp), small enough to time each shape in ~0.1 s.
@@ -40,8 +47,11 @@ def _points_for(order: int, precision: int) -> int:
     return max(2 ** 12, base >> max(0, order - 7))
 
 
-def time_shape(pr: int, order: int, precision: int, wpb: int, flat: int, reps: int = 2) -> float:
-    Q.qqmc_set_tuning(precision, order, wpb, flat)
+def time_shape(pr: int, order: int, code: int, wpb: int, flat: int, reps: int = 2) -> float:
+    """Kernel time of the batch 1..order with (wpb, flat) installed for `order` in table `code`."""
+    Q.qqmc_set_tuning(code, order, wpb, flat)
+    precision = _precision(code)
+    Q.qqmc_set_elimination(pr, Q.QQMC_ELIM_PAIRS if code & Q.QQMC_TUNE_PAIRS else Q.QQMC_ELIM_SINGLE)
     N = _points_for(order, precision)
     plan = Q.Plan([(pr, m, 16, N) for m in range(1, order + 1)], precision)
     try:
@@ -59,7 +69,8 @@ def time_shape(pr: int, order: int, precision: int, wpb: int, flat: int, reps: i
 
 
 def tune(orders=range(1, Q.QQMC_MAX_ORDER + 1), precisions=(Q.QQMC_PREC_FP64, Q.QQMC_PREC_MIXED), verbose=False):
-    """Returns {precision: {order: (wpb, flat, ms)}} and installs the winners."""
+    """Returns {table code: {order: (wpb, flat, ms)}} and installs the winners; a code is a
+    precision, or a precision | QQMC_TUNE_PAIRS for the pair-block tree."""
     pr = Q.qqmc_create_problem(Q.make_params(eps_d=0.0, t_max=10.0))
     table = {}
     try:
@@ -67,7 +78,7 @@ def tune(orders=range(1, Q.QQMC_MAX_ORDER + 1), precisions=(Q.QQMC_PREC_FP64, Q.
             table[prec] = {}
             for n in orders:
                 results = []
-                cands = CANDIDATES[prec] + (LANE_CANDIDATES[prec] if n <= 4 else [])
+                cands = CANDIDATES[_precision(prec)] + (LANE_CANDIDATES[_precision(prec)] if n <= 4 else [])
                 for wpb, flat in cands:
                     try:
                         ms = time_shape(pr, n, prec, wpb, flat)
@@ -93,8 +104,9 @@ def install(table) -> None:
 def reset() -> None:
     """Restore the built-in defaults for every (precision, order)."""
     for prec in (Q.QQMC_PREC_FP64, Q.QQMC_PREC_MIXED):
-        for n in range(1, Q.QQMC_MAX_ORDER + 1):
-            Q.qqmc_set_tuning(prec, n, 0, 0)
+        for tree in (0, Q.QQMC_TUNE_PAIRS):
+            for n in range(1, Q.QQMC_MAX_ORDER + 1):
+                Q.qqmc_set_tuning(prec | tree, n, 0, 0)
 
 
 def save(table, path: str) -> None:
@@ -128,10 +140,13 @@ def main():
     ap.add_argument("--orders", default="1-12")
     ap.add_argument("--out", default=None)
     ap.add_argument("--precision", choices=["fp64", "mixed", "both"], default="both")
+    ap.add_argument("--tree", choices=["single", "pairs", "both"], default="both")
     args = ap.parse_args()
     lo, hi = (int(x) for x in args.orders.split("-"))
     precs = {"fp64": (Q.QQMC_PREC_FP64,), "mixed": (Q.QQMC_PREC_MIXED,),
              "both": (Q.QQMC_PREC_FP64, Q.QQMC_PREC_MIXED)}[args.precision]
+    trees = {"single": (0,), "pairs": (Q.QQMC_TUNE_PAIRS,), "both": (0, Q.QQMC_TUNE_PAIRS)}[args.tree]
+    precs = tuple(p | t for t in trees for p in precs)
     from . import build
     build.build()
     t0 = time.time()

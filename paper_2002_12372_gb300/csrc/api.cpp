@@ -19,6 +19,7 @@ namespace qqmc {
 // ---------------------------------------------------------------- device init
 static std::mutex g_init_mu;
 static bool g_init_done[64];
+static cudaStream_t g_table_stream[64];
 
 static int ensure_device() {
     int dev = 0;
@@ -29,14 +30,27 @@ static int ensure_device() {
     if (g_init_done[dev]) return QQMC_OK;
     int rc = upload_direction_numbers();
     if (rc != QQMC_OK) return rc;
+    // Table builds get their own non-blocking stream at the highest priority, so that a problem
+    // created while long integrations run (a server admitting a new round) neither waits for
+    // them nor queues its kernel behind their pending blocks.
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g_table_stream[dev], cudaStreamNonBlocking, greatest);
+    if (e != cudaSuccess) return cuda_error(e, "table stream");
     g_init_done[dev] = true;
     return QQMC_OK;
 }
 
+static cudaStream_t table_stream() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev >= 0 && dev < 64 ? g_table_stream[dev] : nullptr;
+}
+
 // ---------------------------------------------------------------- tuning
 static std::mutex g_tune_mu;
-static Tuning g_tune[2][kMaxOrder + 1];
-static bool g_tune_set[2][kMaxOrder + 1];
+static Tuning g_tune[2][2][kMaxOrder + 1];  // [precision][pair tree][order]
+static bool g_tune_set[2][2][kMaxOrder + 1];
 
 static Tuning default_tuning(int precision, int order) {
     Tuning t;
@@ -51,11 +65,19 @@ static Tuning default_tuning(int precision, int order) {
     return t;
 }
 
-Tuning get_tuning(int precision, int order) {
+Tuning get_tuning(int precision, int order, bool pairs) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    int p = precision == QQMC_PREC_FP64 ? 0 : 1;
-    if (order >= 1 && order <= kMaxOrder && g_tune_set[p][order]) return g_tune[p][order];
+    const int p = precision == QQMC_PREC_FP64 ? 0 : 1, t = pairs ? 1 : 0;
+    if (order >= 1 && order <= kMaxOrder && g_tune_set[p][t][order]) return g_tune[p][t][order];
     return default_tuning(precision, order);
+}
+
+bool use_pairs(const Problem &P, int precision) {
+    if (P.elimination == QQMC_ELIM_PAIRS) return true;
+    if (P.elimination == QQMC_ELIM_SINGLE) return false;
+    const double dv = hypot(P.g0_re, P.g0_im - P.params.alpha);  // |g^<(0) - i alpha|
+    const double scale = fmax(hypot(P.g0_re, P.g0_im), hypot(P.g0_re, P.g0_im - 1.0));  // g^>(0) = g^<(0) - i
+    return dv < (precision == QQMC_PREC_FP64 ? 0.01 : 0.25) * scale;
 }
 
 }  // namespace qqmc
@@ -134,11 +156,12 @@ static int alloc_problem(const qqmc_params *p, qqmc_problem **out) {
 
 extern "C" int qqmc_create_problem(const qqmc_params *p, qqmc_problem **out) {
     qqmc_problem *pr = nullptr;
-    int rc = alloc_problem(p, &pr);
+    int rc = alloc_problem(p, &pr);  // validates p and initialises the device
     if (rc != QQMC_OK) return rc;
+    cudaStream_t ts = table_stream();
     if (p->half_bandwidth > 0.0) {  // semicircular leads: numerical tables, g^<(0) from the same quadrature
         double zero[4] = {0, 0, 0, 0};
-        rc = launch_lead_table(*pr, 0, zero);
+        rc = launch_lead_table(*pr, ts, zero);
         pr->g0_re = zero[0];
         pr->g0_im = zero[1];
         pr->c0_re = zero[2];
@@ -146,9 +169,9 @@ extern "C" int qqmc_create_problem(const qqmc_params *p, qqmc_problem **out) {
     } else {
         pr->g0_re = 0.0;
         pr->g0_im = 0.5 - atan(p->eps_d / p->gamma) / M_PI;
-        rc = launch_gf_table(*pr, 0);
+        rc = launch_gf_table(*pr, ts);
         if (rc == QQMC_OK) {
-            cudaError_t e = cudaStreamSynchronize(0);
+            cudaError_t e = cudaStreamSynchronize(ts);
             if (e != cudaSuccess) rc = cuda_error(e, "table build");
         }
     }
@@ -319,6 +342,7 @@ struct qqmc_plan {
         int first = 0, count = 0, n_max = 0;
         long long chunks = 0;
         Tuning tune{};
+        bool pairs = false;          // the pair-block tree (else the single-vertex tree)
         long long gstack_warps = 0;  // warps with a device-memory stack slice, fixed at creation
     };
     std::vector<Group> groups;
@@ -401,8 +425,11 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     // The cut depends on the item alone (batched and single runs agree bit for bit).
     constexpr long long kTargetUnits = 1 << 14;
     constexpr int kMinSubtreeLevels = 4;
+    // the Keldysh-sum tree of each item (the problem's elimination order at this precision)
+    std::vector<char> pv(n_items);
+    for (int i = 0; i < n_items; ++i) pv[i] = use_pairs(*items[i].problem, precision);
     auto lane_mode = [&](int i) {
-        return items[i].order <= kLaneMaxOrder && get_tuning(precision, items[i].order).flat == 1;
+        return items[i].order <= kLaneMaxOrder && get_tuning(precision, items[i].order, pv[i]).flat == 1;
     };
     std::vector<char> lmv(n_items);
     std::vector<int> pbits_of(n_items, 0), split_of(n_items, 0);
@@ -410,7 +437,7 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         const qqmc_item &it = items[i];
         lmv[i] = lane_mode(i);
         if (lmv[i]) continue;  // one point per lane: no cut
-        const int levels = tree_leaf_bits(it.order);  // bits of the tree's leaf index
+        const int levels = tree_leaf_bits(it.order, pv[i]);  // bits of the tree's leaf index
         const long long units = (long long)((it.n_points + kChunk - 1) / kChunk) * it.n_shifts;
         int pb = 0, sp = 0;
         while (pb < 5 && (units << pb) < kTargetUnits) ++pb;
@@ -440,24 +467,26 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
         free_plan(pl);
         return set_error(QQMC_E_NOMEM, std::string("device allocation of the plan failed: ") + cudaGetErrorString(e));
     }
-    // Device order: the warp-per-point items grouped by their order's tuned flat
-    // depth (groups holding higher orders first), then the one-point-per-lane
-    // items (orders <= 4 whose tuning asks for it); within a group highest order
-    // first, then more points first, so the longest items start early and the
-    // persistent grid drains evenly.  Each launch has its own chunk numbering.
+    // Device order: the warp-per-point items grouped by tree and their order's
+    // tuned flat depth (groups holding higher orders first), then the
+    // one-point-per-lane items (orders <= 4 whose tuning asks for it); within a
+    // group highest order first, then more points first, so the longest items
+    // start early and the persistent grid drains evenly.  Each launch has its own
+    // chunk numbering.
     auto flat_of = [&](int i) {
-        const int f = get_tuning(precision, items[i].order).flat;
+        const int f = get_tuning(precision, items[i].order, pv[i]).flat;
         return f < 2 ? 2 : f;
     };
-    int group_top[6] = {0, 0, 0, 0, 0, 0};  // highest order per flat depth 2..5
+    auto key_of = [&](int i) { return 6 * pv[i] + flat_of(i); };  // launch group: (tree, flat depth)
+    int group_top[12] = {};  // highest order per group
     for (int i = 0; i < n_items; ++i)
-        if (!lmv[i] && items[i].order > group_top[flat_of(i)]) group_top[flat_of(i)] = items[i].order;
+        if (!lmv[i] && items[i].order > group_top[key_of(i)]) group_top[key_of(i)] = items[i].order;
     pl->perm.resize(n_items);
     for (int i = 0; i < n_items; ++i) pl->perm[i] = i;
     std::stable_sort(pl->perm.begin(), pl->perm.end(), [&](int a, int b) {
         if (lmv[a] != lmv[b]) return !lmv[a];
         if (!lmv[a]) {
-            const int fa = flat_of(a), fb = flat_of(b);
+            const int fa = key_of(a), fb = key_of(b);
             if (group_top[fa] != group_top[fb]) return group_top[fa] > group_top[fb];
             if (fa != fb) return fa > fb;
         }
@@ -510,11 +539,13 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
             d.chunk_begin = cl;
             cl += (long long)cps * it.n_shifts;
         } else {
-            if (pl->groups.empty() || pl->groups.back().tune.flat != d.flat) {
+            if (pl->groups.empty() || pl->groups.back().tune.flat != d.flat ||
+                pl->groups.back().pairs != (pv[ci] != 0)) {
                 qqmc_plan::Group g;
                 g.first = q;
                 g.n_max = it.order;  // highest order first within a group
-                g.tune = get_tuning(precision, it.order);
+                g.pairs = pv[ci] != 0;
+                g.tune = get_tuning(precision, it.order, g.pairs);
                 g.tune.flat = g.tune.flat_min = d.flat;
                 pl->groups.push_back(g);
             }
@@ -534,7 +565,7 @@ extern "C" int qqmc_plan_create(const qqmc_item *items, int n_items, int precisi
     size_t gs_bytes = 0;
     for (auto &g : pl->groups) {
         size_t bpw = 0;
-        const long long w = detsum_gstack_warps(g.n_max, precision, g.tune, &bpw);
+        const long long w = detsum_gstack_warps(g.n_max, precision, g.tune, g.pairs, &bpw);
         g.gstack_warps = w;
         if ((size_t)w * bpw > gs_bytes) gs_bytes = (size_t)w * bpw;
         if (w > pl->gstack_warps) pl->gstack_warps = w;
@@ -576,7 +607,7 @@ static cudaError_t enqueue_plan(qqmc_plan *pl, cudaStream_t s, bool timed) {
         // a group sized without one gets none, and then runs the shared-memory stack or fails cleanly
         const long long w = g.gstack_warps;
         e = launch_detsum(pl->d_items + g.first, g.count, g.chunks, pl->d_counter + gi, g.n_max, pl->precision, g.tune,
-                          w > 0 ? pl->d_gstack : nullptr, w, plan_span(pl), s);
+                          g.pairs, w > 0 ? pl->d_gstack : nullptr, w, plan_span(pl), s);
         if (e != cudaSuccess) return e;
     }
     const int n_lane = (int)pl->items.size() - pl->n_warp;
@@ -792,32 +823,54 @@ extern "C" int qqmc_integrate(qqmc_problem *pr, int order, uint64_t n_points, in
     return rc;
 }
 
+// precision argument of the tuning calls: QQMC_PREC_* | optionally QQMC_TUNE_PAIRS
+static bool tuning_target(int arg, int *precision, int *tree) {
+    *precision = arg & ~QQMC_TUNE_PAIRS;
+    *tree = (arg & QQMC_TUNE_PAIRS) ? 1 : 0;
+    return *precision == QQMC_PREC_FP64 || *precision == QQMC_PREC_MIXED;
+}
+
 extern "C" int qqmc_set_tuning(int precision, int order, int warps_per_block, int flat_vertices) {
-    if ((precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED) || order < 1 || order > kMaxOrder)
+    int prec = 0, t = 0;
+    if (!tuning_target(precision, &prec, &t) || order < 1 || order > kMaxOrder)
         return set_error(QQMC_E_INVAL, "qqmc_set_tuning: bad precision or order");
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    int p = precision == QQMC_PREC_FP64 ? 0 : 1;
+    const int p = prec == QQMC_PREC_FP64 ? 0 : 1;
     if (warps_per_block <= 0 || flat_vertices <= 0) {
-        g_tune_set[p][order] = false;
+        g_tune_set[p][t][order] = false;
         return QQMC_OK;
     }
     if (warps_per_block > 16 || flat_vertices > 5)
         return set_error(QQMC_E_INVAL, "qqmc_set_tuning: warps_per_block in 1..16, flat_vertices in 1..5");
-    g_tune[p][order].warps_per_block = warps_per_block;
-    g_tune[p][order].flat = flat_vertices;
-    g_tune[p][order].flat_min = flat_vertices;
-    g_tune_set[p][order] = true;
+    g_tune[p][t][order].warps_per_block = warps_per_block;
+    g_tune[p][t][order].flat = flat_vertices;
+    g_tune[p][t][order].flat_min = flat_vertices;
+    g_tune_set[p][t][order] = true;
     return QQMC_OK;
 }
 
 extern "C" int qqmc_get_tuning(int precision, int order, int *wpb, int *flat) {
-    if ((precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED) || order < 1 || order > kMaxOrder || !wpb ||
-        !flat)
+    int prec = 0, t = 0;
+    if (!tuning_target(precision, &prec, &t) || order < 1 || order > kMaxOrder || !wpb || !flat)
         return set_error(QQMC_E_INVAL, "qqmc_get_tuning: bad arguments");
-    Tuning t = get_tuning(precision, order);
-    *wpb = t.warps_per_block;
-    *flat = t.flat;
+    Tuning tu = get_tuning(prec, order, t != 0);
+    *wpb = tu.warps_per_block;
+    *flat = tu.flat;
     return QQMC_OK;
+}
+
+extern "C" int qqmc_set_elimination(qqmc_problem *pr, int mode) {
+    if (!pr) return set_error(QQMC_E_INVAL, "qqmc_set_elimination: problem is NULL");
+    if (mode != QQMC_ELIM_AUTO && mode != QQMC_ELIM_PAIRS && mode != QQMC_ELIM_SINGLE)
+        return set_error(QQMC_E_INVAL, "qqmc_set_elimination: mode must be QQMC_ELIM_AUTO, _PAIRS or _SINGLE");
+    pr->elimination = mode;
+    return QQMC_OK;
+}
+
+extern "C" int qqmc_elimination(const qqmc_problem *pr, int precision) {
+    if (!pr || (precision != QQMC_PREC_FP64 && precision != QQMC_PREC_MIXED))
+        return set_error(QQMC_E_INVAL, "qqmc_elimination: NULL problem or bad precision");
+    return use_pairs(*pr, precision) ? QQMC_ELIM_PAIRS : QQMC_ELIM_SINGLE;
 }
 
 // ---------------------------------------------------------------- inspection
@@ -913,10 +966,11 @@ extern "C" int qqmc_integrand(const qqmc_problem *pr, int order, uint64_t count,
     it.alpha = pr->params.alpha;
     it.col = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col : nullptr;
     it.col32 = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col32 : nullptr;
-    Tuning tu = get_tuning(precision, order);
+    const bool pairs = use_pairs(*pr, precision);
+    Tuning tu = get_tuning(precision, order, pairs);
     if (tu.flat < 2) tu.flat = tu.flat_min = 2;  // the check kernel runs one warp per point
     it.flat = tu.flat;
-    if (e == cudaSuccess) e = launch_integrand(it, count, d_u.p, d_out.p, precision, tu, 0);
+    if (e == cudaSuccess) e = launch_integrand(it, count, d_u.p, d_out.p, precision, tu, pairs, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out, d_out.p, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrand");
     return QQMC_OK;
@@ -1018,10 +1072,11 @@ extern "C" int qqmc_learn_projection(qqmc_problem *pr, int order, uint64_t M, in
         it.alpha = pr->params.alpha;
         it.col = pr->params.observable == QQMC_OBS_CURRENT ? pr->d_col : nullptr;
         it.col32 = nullptr;
-        Tuning tu = get_tuning(QQMC_PREC_FP64, n);
+        const bool pairs = use_pairs(*pr, QQMC_PREC_FP64);
+        Tuning tu = get_tuning(QQMC_PREC_FP64, n, pairs);
         if (tu.flat < 2) tu.flat = tu.flat_min = 2;
         it.flat = tu.flat;
-        if (e == cudaSuccess) e = launch_integrand(it, nin, d_u, d_c, QQMC_PREC_FP64, tu, 0);
+        if (e == cudaSuccess) e = launch_integrand(it, nin, d_u, d_c, QQMC_PREC_FP64, tu, pairs, 0);
         if (e == cudaSuccess) e = cudaMemcpy(c.data(), d_c, sizeof(double) * c.size(), cudaMemcpyDeviceToHost);
         cudaFree(d_u);
         cudaFree(d_c);

@@ -227,6 +227,693 @@ __device__ __forceinline__ void interp_col(const typename TabT<R>::V *col, doubl
 }
 
 // ----------------------------------------------------------------------------
+// Complex helpers and the leaf formula shared by both Keldysh-sum trees.
+// ----------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ cx<R> sel(int bit, cx<R> one, cx<R> zero) {
+    return mk<R>(bit ? one.re : zero.re, bit ? one.im : zero.im);
+}
+template <class R>
+__device__ __forceinline__ cx<R> cneg(cx<R> a) {
+    return mk<R>(-a.re, -a.im);
+}
+template <class R>
+__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
+    return mk<R>(a.re - b.re, a.im - b.im);
+}
+// c + a * b
+template <class R>
+__device__ __forceinline__ cx<R> cfma(cx<R> c, cx<R> a, cx<R> b) {
+    return mk<R>(fmaR(a.re, b.re, fmaR(-a.im, b.im, c.re)), fmaR(a.re, b.im, fmaR(a.im, b.re, c.im)));
+}
+
+// Leaf term after a lone last vertex p: with pivot pv and the copies' entries,
+//   det' = det pv,   S_cc = m_cc - m_cp m_pc / pv   (c = copy 0, 1),
+//   det'^2 (S_00 - S_11) = det^2 pv (pv (m_00 - m_11) - (m_0p m_p0 - m_1p m_p1)):
+// no reciprocal, so a vanishing pivot (det M_down = 0) gives a zero term.
+template <class R>
+__device__ __forceinline__ cx<R> leaf_term(cx<R> m00, cx<R> m11, cx<R> m0p, cx<R> mp0, cx<R> m1p, cx<R> mp1, cx<R> pv,
+                                           cx<R> det) {
+    const cx<R> q = cfms(cmul(m0p, mp0), m1p, mp1);  // m0p mp0 - m1p mp1
+    const cx<R> r = cfms(q, pv, csub(m00, m11));      // q - pv (m00 - m11)
+    return cmul(cmul(det, det), cmul(pv, cneg(r)));
+}
+
+// Float-float or double-double style butterfly of the lane accumulators:
+// combines (s, c) pairs with two-sum in R, then returns s + c in double.
+template <class R>
+__device__ __forceinline__ void two_sum_r(R a, R b, R &s, R &e) {
+    s = a + b;
+    R z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+template <class R>
+__device__ __forceinline__ double warp_total(Acc<R> acc) {
+    R s = acc.s, c = acc.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        R s2 = __shfl_xor_sync(FULL, s, o);
+        R c2 = __shfl_xor_sync(FULL, c, o);
+        R t, e;
+        int lo = ((threadIdx.x & 31) & o) == 0;
+        if (lo) two_sum_r<R>(s, s2, t, e); else two_sum_r<R>(s2, s, t, e);
+        s = t;
+        c = lo ? (c + c2) + e : (c2 + c) + e;
+    }
+    return (double)s + (double)c;
+}
+
+// ----------------------------------------------------------------------------
+// Single-vertex Schur tree (the fast path): one vertex per tree level with
+// its 1x1 pivot.  Pivots are the ratios of consecutive leading minors of
+// M_down, the first being the vertex diagonal g^<(0) - i alpha itself; the
+// plans use this tree for problems whose vertex diagonal is well away from
+// zero and the pair-block tree (namespace pairs) otherwise.
+// ----------------------------------------------------------------------------
+namespace single {
+
+// ----------------------------------------------------------------------------
+// Per-warp shared-memory layout for the Keldysh sum.
+//
+// The depth-first tree stops when kTreeLeaf vertices remain (or earlier for
+// small n).  From there, B = Rleaf - RF levels are expanded breadth first
+// (2, 4, ... 2^B sibling matrices, all lanes cooperating), and each lane
+// resolves the last RF vertices of one node along one choice path in
+// registers: 2^B nodes x 2^RF paths = 2^Rleaf <= 32 lanes.
+// ----------------------------------------------------------------------------
+constexpr int kTreeLeaf = 5;
+
+template <class R>
+struct WarpSmem {
+    cx<R> *stack;   // tree levels, level l has (2 R_l + 2)^2 entries, R_l = n-1-l (shared memory)
+    cx<R> *gstack;  // split stack: the levels wider than gs_level in device memory, or null
+    cx<R> *wrow;    // scaled pivot row(s): <= max(2 n_max, 64) entries
+    cx<R> *P;       // vertex k's block at o_k = (k-1)(k+2)/2: P[o_k + j] = g^>(u_j - u_k), 0 <= j < k,
+                    // and P[o_k + k] = measurement-column entry (k, a_k = 1)
+    cx<R> *Rr;      // Rr[o_k + j] = g^<(u_j - u_k); Rr[o_k + k] = column entry (k, a_k = 0)
+    cx<R> *detD;    // per tree level, and (after the last) the sibling leaf's
+    cx<R> *sib;     // the second leaf of a sibling pair (2 kTreeLeaf + 2)^2 entries
+    cx<R> *lr;      // level 0: left and right factors of vertex 1 per block index (4 n_max)
+    cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
+    cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
+    cx<R> *bip;     // pivot reciprocal per child of the level being built (32)
+    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t); device memory with the split stack
+    int gs_level;   // split stack: levels with S > gs_level in device memory
+};
+
+
+// wrow, bdet and bip serve the general cooperative expansion: breadth-first
+// levels (flat depth below the tree leaf) and depth-first steps wider than a
+// warp (children of more than 32 rows, orders >= 18).
+__host__ __device__ inline bool needs_wide_buffers(int n_max, int RF) {
+    const int rl = n_max - 1 < kTreeLeaf ? n_max - 1 : kTreeLeaf;
+    return RF < rl || 2 * (n_max - 1) > 32;
+}
+
+__host__ __device__ inline size_t stack_entries(int n_max) {
+    size_t tot = 0;
+    int R0 = n_max - 1;
+    int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
+    for (int l = 0; l <= levels; ++l) {
+        size_t S = 2 * (size_t)(R0 - l) + 2;
+        tot += S * S;
+    }
+    return tot;
+}
+
+// With the split stack the tree levels wider than gs_level (the top levels,
+// built 1, 2, 4 ... times per point) live in device memory and the narrow, hot
+// bottom levels stay in shared memory.
+__host__ __device__ inline size_t stack_entries_split(int n_max, bool global_part, int gs_level) {
+    size_t tot = 0;
+    int R0 = n_max - 1;
+    int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
+    for (int l = 0; l <= levels; ++l) {
+        size_t S = 2 * (size_t)(R0 - l) + 2;
+        if (((int)S > gs_level) == global_part) tot += S * S;
+    }
+    return tot;
+}
+
+// entries of the breadth-first levels below a tree leaf of Rleaf vertices
+__host__ __device__ inline size_t bfs_entries(int Rleaf, int RF) {
+    size_t tot = 0;
+    int B = Rleaf > RF ? Rleaf - RF : 0;
+    for (int b = 1; b <= B; ++b) {
+        size_t S = 2 * (size_t)(Rleaf - b) + 2;
+        tot += ((size_t)1 << b) * S * S;
+    }
+    return tot;
+}
+
+__host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
+    size_t m = 0;
+    for (int Rl = 0; Rl <= kTreeLeaf && Rl <= n_max - 1; ++Rl) {
+        size_t e = bfs_entries(Rl, RF);
+        m = e > m ? e : m;
+    }
+    return m;
+}
+
+// The mixed-precision path builds sibling leaves in pairs (one depth-first step
+// for two leaves: its steps are latency-bound); the FP64 path, bound by its
+// FP64 pipe, gains nothing from it and keeps the shared memory for warps.
+template <class R>
+__host__ __device__ constexpr bool twin_leaves() { return sizeof(R) == 4; }
+
+// the sibling leaf buffer, used when the tree has depth-first levels
+template <class R>
+__host__ __device__ inline size_t sib_entries(int n_max) {
+    return twin_leaves<R>() && n_max - 1 > kTreeLeaf ? (size_t)(2 * kTreeLeaf + 2) * (2 * kTreeLeaf + 2) : 0;
+}
+
+// entries of the packed pair values with the measurement column (P and Rr:
+// blocks of k + 1 entries for the vertices k = 1 .. n_max)
+__host__ __device__ inline size_t pair_entries(int n_max) { return (size_t)n_max * (n_max + 3); }
+
+// Shared memory of one warp.  gs_level = 0: the whole tree stack and the point
+// times in shared memory.  gs_level > 0 (split stack): the levels wider than
+// gs_level and the point times in a per-warp slice of device memory.
+template <class R>
+__host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_level) {
+    size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
+    size_t c = (gs_level ? stack_entries_split(n_max, false, gs_level) : stack_entries(n_max)) + pair_entries(n_max) +
+               n_max + 1 + sib_entries<R>(n_max) + 4 * (size_t)n_max + bfs_max_entries(n_max, RF) + wide;
+    size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
+    if (!gs_level) bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
+    return (bytes + 127) & ~(size_t)127;
+}
+
+// Split-stack boundary: the widest levels go to device memory, two rows at a
+// time, until a warp's shared memory lets the SM hold the warps its bound pipe
+// needs (FP64: 6 warps keep GB300's two FP64 lanes per SM busy; mixed: 12).
+// Never the tree leaf (S = 12) or its parent (S = 14): the last depth-first
+// step and the breadth-first and flat phases work in shared memory only.
+template <class R>
+__host__ __device__ inline int gs_level_of(int n_max, int RF) {
+    const size_t budget = sizeof(R) == 8 ? 36 * 1024 : 18 * 1024;
+    int lev = 20;
+    while (lev > 2 * kTreeLeaf + 4 && warp_smem_bytes_at<R>(n_max, RF, lev) > budget) lev -= 2;
+    return lev;
+}
+
+// Shared memory of one warp; with the split stack (gs) the wide top levels of
+// the Schur tree live in a per-warp slice of device memory (FP64 orders >= 21,
+// whose whole stack exceeds the 227 KB a block can address, and the orders the
+// stack policy names).
+template <class R>
+__host__ __device__ inline size_t warp_smem_bytes(int n_max, int RF, bool gs = false) {
+    return warp_smem_bytes_at<R>(n_max, RF, gs ? gs_level_of<R>(n_max, RF) : 0);
+}
+
+// Device-memory slice of one warp with the split stack: the wide levels, one
+// spare entry, and the point times of the chunk.
+template <class R>
+__host__ __device__ inline size_t gstack_entries(int n_max, int RF) {
+    return stack_entries_split(n_max, true, gs_level_of<R>(n_max, RF)) + 1 +
+           (32 * (size_t)(n_max + 1) * sizeof(double) + sizeof(cx<R>) - 1) / sizeof(cx<R>);
+}
+
+template <class R>
+__device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack = nullptr) {
+    WarpSmem<R> w;
+    cx<R> *p = reinterpret_cast<cx<R> *>(base);
+    w.gstack = gstack;
+    w.gs_level = gstack ? gs_level_of<R>(n_max, RF) : 0;
+    w.stack = p;
+    p += gstack ? stack_entries_split(n_max, false, w.gs_level) : stack_entries(n_max);
+    const int npair = n_max * (n_max + 3) / 2;
+    w.P = p;
+    p += npair;
+    w.Rr = p;
+    p += npair;
+    w.detD = p;
+    p += n_max + 1;
+    w.sib = p;
+    p += sib_entries<R>(n_max);
+    w.lr = p;
+    p += 4 * n_max;
+    w.bfs = p;
+    p += bfs_max_entries(n_max, RF);
+    w.wrow = w.bdet = w.bip = nullptr;
+    if (needs_wide_buffers(n_max, RF)) {
+        w.wrow = p;
+        p += 2 * n_max > 64 ? 2 * n_max : 64;
+        w.bdet = p;
+        p += 64;
+        w.bip = p;
+        p += 32;
+    }
+    size_t off = (reinterpret_cast<unsigned char *>(p) - base + 15) & ~(size_t)15;
+    w.upt = gstack ? reinterpret_cast<double *>(gstack + stack_entries_split(n_max, true, w.gs_level) + 1)
+                   : reinterpret_cast<double *>(base + off);
+    return w;
+}
+
+// Flat phase: one lane resolves the F remaining vertices of node matrix E
+// (size S = 2F + 2) along the choice path `path` (bit q = Keldysh index of the
+// q-th remaining vertex).  The first elimination is fused with the gather;
+// the rest runs on an (F+1) x (F+1) register matrix whose rows and columns
+// are {copy a_1 = 0, copy a_1 = 1, remaining vertices}.
+template <class R, int F, int STRIDE = 1>
+__device__ __forceinline__ void flat_phase(const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &acc_re,
+                                           Acc<R> &acc_im) {
+    constexpr int S = 2 * F + 2;
+    if (F == 0) {
+        cx<R> dd = cmul(detD, detD);
+        cx<R> diff = mk<R>(E[0].re - E[(S + 1) * STRIDE].re, E[0].im - E[(S + 1) * STRIDE].im);
+        cx<R> term = cmul(dd, diff);
+        if (parity) term = mk<R>(-term.re, -term.im);
+        acc_re.add(term.re);
+        acc_im.add(term.im);
+        return;
+    }
+    constexpr int M = F + 1;  // after the first elimination: 2 copies + F-1 vertices
+    int idx[M];
+    idx[0] = 0;
+    idx[1] = 1;
+#pragma unroll
+    for (int q = 1; q < F; ++q) idx[q + 1] = 2 + 2 * q + ((path >> q) & 1);
+    const int p0 = 2 + (path & 1);
+    cx<R> piv = E[(p0 * S + p0) * STRIDE];
+    detD = cmul(detD, piv);
+    cx<R> ip = crcp(piv);
+    cx<R> m[M][M];
+    cx<R> prow[M];
+#pragma unroll
+    for (int y = 0; y < M; ++y) prow[y] = cmul(E[(p0 * S + idx[y]) * STRIDE], ip);
+#pragma unroll
+    for (int x = 0; x < M; ++x) {
+        cx<R> cf = E[(idx[x] * S + p0) * STRIDE];
+#pragma unroll
+        for (int y = 0; y < M; ++y) {
+            if (x < 2 && y < 2 && x != y) continue;  // copy cross terms are never used
+            m[x][y] = cfms(E[(idx[x] * S + idx[y]) * STRIDE], cf, prow[y]);
+        }
+    }
+#pragma unroll
+    for (int q = 1; q < F - 1; ++q) {
+        const int p = q + 1;
+        cx<R> pv = m[p][p];
+        detD = cmul(detD, pv);
+        cx<R> iq = crcp(pv);
+#pragma unroll
+        for (int y = 0; y < M; ++y)
+            if (y < 2 || y > p) m[p][y] = cmul(m[p][y], iq);
+#pragma unroll
+        for (int x = 0; x < M; ++x) {
+            if (!(x < 2 || x > p)) continue;
+#pragma unroll
+            for (int y = 0; y < M; ++y) {
+                if (!(y < 2 || y > p)) continue;
+                if (x < 2 && y < 2 && x != y) continue;
+                m[x][y] = cfms(m[x][y], m[x][p], m[p][y]);
+            }
+        }
+    }
+    cx<R> term;
+    if constexpr (F >= 2) {  // the last vertex is eliminated inside the leaf term
+        term = leaf_term(m[0][0], m[1][1], m[0][M - 1], m[M - 1][0], m[1][M - 1], m[M - 1][1], m[M - 1][M - 1], detD);
+    } else {  // F = 1: the gather step eliminated the only vertex
+        term = cmul(cmul(detD, detD), mk<R>(m[0][0].re - m[1][1].re, m[0][0].im - m[1][1].im));
+    }
+    parity ^= __popc(path) & 1;
+    if (parity) term = mk<R>(-term.re, -term.im);
+    acc_re.add(term.re);
+    acc_im.add(term.im);
+}
+
+template <class R, int RF>
+__device__ __forceinline__ void flat_dispatch(int Rf, const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &ar,
+                                              Acc<R> &ai) {
+    switch (Rf) {  // Rf <= RF
+        case 0: flat_phase<R, 0>(E, detD, parity, path, ar, ai); break;
+        case 1: flat_phase<R, 1>(E, detD, parity, path, ar, ai); break;
+        case 2: flat_phase<R, 2>(E, detD, parity, path, ar, ai); break;
+        case 3: if (RF >= 3) flat_phase<R, (RF >= 3 ? 3 : 0)>(E, detD, parity, path, ar, ai); break;
+        case 4: if (RF >= 4) flat_phase<R, (RF >= 4 ? 4 : 0)>(E, detD, parity, path, ar, ai); break;
+        default: if (RF >= 5) flat_phase<R, (RF >= 5 ? 5 : 0)>(E, detD, parity, path, ar, ai); break;
+    }
+}
+
+// One cooperative elimination: child(ren) of S x S parent matrices.  Child j
+// of the new level comes from parent j >> 1 with Keldysh index a = j & 1 on the
+// parent's first remaining vertex (pivot row/column 2 + a).  The new matrices
+// are (S-2) x (S-2), all children contiguous in `out`.
+template <class R>
+__device__ __forceinline__ void expand_level(const cx<R> *__restrict__ in, int S, int nchild, int first_a,
+                                             cx<R> *__restrict__ out, const cx<R> *detD_in, cx<R> *detD_out,
+                                             cx<R> *__restrict__ wrow, cx<R> *ip_buf, int lane) {
+    const int S2 = S - 2;
+    // child pivots: reciprocal and running det M_down
+    for (int j = lane; j < nchild; j += 32) {
+        const int a = nchild == 1 ? first_a : (j & 1);
+        const int pj = nchild == 1 ? 0 : (j >> 1);
+        const int pr = 2 + a;
+        cx<R> piv = in[(size_t)pj * S * S + pr * S + pr];
+        ip_buf[j] = crcp(piv);
+        detD_out[j] = cmul(detD_in[pj], piv);
+    }
+    __syncwarp();
+    // scaled pivot rows
+    for (int q = lane; q < nchild * S2; q += 32) {
+        const int j = q / S2, c2 = q - j * S2;
+        const int a = nchild == 1 ? first_a : (j & 1);
+        const int pj = nchild == 1 ? 0 : (j >> 1);
+        const int pr = 2 + a;
+        const int c = c2 < 2 ? c2 : c2 + 2;
+        wrow[q] = cmul(in[(size_t)pj * S * S + pr * S + c], ip_buf[j]);
+    }
+    __syncwarp();
+    // Only entries that are ever read are built: a choice path takes one copy of every vertex
+    // (and one measurement copy per determinant), so the entry joining row r2 to its row's
+    // other copy, column r2 ^ 1, is never used (1 / S2 of the updates).  lane -> (child j,
+    // row r2, used column cc of W = S2 - 1) stepped by 32 entries without divisions.
+    const int W = S2 - 1;
+    const int dr = 32 / W, dc = 32 - dr * W;
+    int r2 = lane / W, cc = lane - r2 * W, j = 0;
+    while (r2 >= S2) { r2 -= S2; ++j; }
+    const int total = nchild * S2 * W;
+    for (int e = lane; e < total; e += 32) {
+        const int c2 = cc < (r2 ^ 1) ? cc : cc + 1;
+        const int a = nchild == 1 ? first_a : (j & 1);
+        const int pj = nchild == 1 ? 0 : (j >> 1);
+        const int pr = 2 + a;
+        const int r = r2 < 2 ? r2 : r2 + 2;
+        const int c = c2 < 2 ? c2 : c2 + 2;
+        const cx<R> *P = in + (size_t)pj * S * S;
+        out[((size_t)j * S2 + r2) * S2 + c2] = cfms(P[r * S + c], P[r * S + pr], wrow[j * S2 + c2]);
+        cc += dc;
+        r2 += dr;
+        if (cc >= W) { cc -= W; ++r2; }
+        while (r2 >= S2) { r2 -= S2; ++j; }
+    }
+    __syncwarp();
+}
+
+// Single child (a depth-first step, S - 2 <= 32): each lane owns one column of
+// the child and a fixed row offset, so the scaled pivot-row entry of its
+// column stays in a register and the pivot-column entry of a row is a
+// broadcast load.  A step is latency-bound (a few hundred flops per warp), so
+// every load of the step is issued before the pivot's reciprocal is formed,
+// and the lane mapping needs no division.
+//
+// Children of 2T = 12, 14 or 16 rows (the deep, frequent steps): lanes 0-15
+// take the even rows, lanes 16-31 the odd rows, column c2 = lane & 15.
+template <class R, int T>
+__device__ __forceinline__ void expand_one_t(const cx<R> *__restrict__ in, int a, cx<R> *__restrict__ out,
+                                             const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    constexpr int S2 = 2 * T, S = S2 + 2;
+    const int pr = 2 + a;
+    const int c2 = lane & 15, rsub = lane >> 4;
+    const bool act = c2 < S2;
+    const int c = c2 < 2 ? c2 : c2 + 2;
+    const cx<R> piv = in[pr * S + pr];
+    cx<R> prc = mk<R>(0, 0), ev[T], cv[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) ev[t] = cv[t] = mk<R>(0, 0);
+    if (act) {
+        prc = in[pr * S + c];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int r2 = rsub + 2 * t;
+            const int r = r2 < 2 ? r2 : r2 + 2;
+            ev[t] = in[r * S + c];
+            cv[t] = in[r * S + pr];
+        }
+    }
+    const cx<R> ip = crcp(piv);
+    if (lane == 0) *detD_out = cmul(*detD_in, piv);
+    if (act) {
+        const cx<R> w = cmul(prc, ip);
+#pragma unroll
+        for (int t = 0; t < T; ++t) out[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv[t], w);
+    }
+    __syncwarp();
+}
+
+// Both children (a = 0 into out0, a = 1 into out1) of a parent of 2T + 2 rows:
+// the last depth-first step, whose two children are consecutive leaves.  The
+// parent entries are loaded once for both, and both pivots' latencies overlap.
+template <class R, int T>
+__device__ __forceinline__ void expand_both_t(const cx<R> *__restrict__ in, cx<R> *__restrict__ out0,
+                                              cx<R> *__restrict__ out1, const cx<R> *detD_in, cx<R> *detD_out0,
+                                              cx<R> *detD_out1, int lane) {
+    constexpr int S2 = 2 * T, S = S2 + 2;
+    const int c2 = lane & 15, rsub = lane >> 4;
+    const bool act = c2 < S2;
+    const int c = c2 < 2 ? c2 : c2 + 2;
+    const cx<R> piv0 = in[2 * S + 2], piv1 = in[3 * S + 3];
+    cx<R> prc0 = mk<R>(0, 0), prc1 = mk<R>(0, 0), ev[T], cv0[T], cv1[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) ev[t] = cv0[t] = cv1[t] = mk<R>(0, 0);
+    if (act) {
+        prc0 = in[2 * S + c];
+        prc1 = in[3 * S + c];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int r2 = rsub + 2 * t;
+            const int r = r2 < 2 ? r2 : r2 + 2;
+            ev[t] = in[r * S + c];
+            cv0[t] = in[r * S + 2];
+            cv1[t] = in[r * S + 3];
+        }
+    }
+    const cx<R> ip0 = crcp(piv0), ip1 = crcp(piv1);
+    if (lane == 0) *detD_out0 = cmul(*detD_in, piv0);
+    if (lane == 1) *detD_out1 = cmul(*detD_in, piv1);
+    if (act) {
+        const cx<R> w0 = cmul(prc0, ip0), w1 = cmul(prc1, ip1);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            out0[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv0[t], w0);
+            out1[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv1[t], w1);
+        }
+    }
+    __syncwarp();
+}
+
+// Wider children (S - 2 = 18 .. 32 rows, the rare top steps): lane = column,
+// rows in batches (eight in FP32, four in FP64) with the batch's loads issued first.
+template <class R>
+__device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
+                                                const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    constexpr int NB = sizeof(R) == 4 ? 8 : 4;  // rows per batch (FP64: register budget)
+    const int S2 = S - 2;
+    const int pr = 2 + a;
+    const cx<R> piv = in[pr * S + pr];
+    const cx<R> ip = crcp(piv);
+    if (lane == 0) *detD_out = cmul(*detD_in, piv);
+    if (lane < S2) {
+        const int c = lane < 2 ? lane : lane + 2;
+        const cx<R> w = cmul(in[pr * S + c], ip);
+        for (int r0 = 0; r0 < S2; r0 += NB) {
+            cx<R> ev[NB], cv[NB];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                const int r2 = r0 + t < S2 ? r0 + t : S2 - 1;  // a clamped duplicate of the last row
+                const int r = r2 < 2 ? r2 : r2 + 2;
+                ev[t] = in[r * S + c];
+                cv[t] = in[r * S + pr];
+            }
+#pragma unroll
+            for (int t = 0; t < NB; ++t)
+                if (r0 + t < S2) out[(r0 + t) * S2 + lane] = cfms(ev[t], cv[t], w);
+        }
+    }
+    __syncwarp();
+}
+
+template <class R>
+__device__ __forceinline__ void expand_one(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
+                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+    switch (S - 2) {
+        case 12: expand_one_t<R, 6>(in, a, out, detD_in, detD_out, lane); break;
+        case 14: expand_one_t<R, 7>(in, a, out, detD_in, detD_out, lane); break;
+        case 16: expand_one_t<R, 8>(in, a, out, detD_in, detD_out, lane); break;
+        default: expand_one_wide<R>(in, S, a, out, detD_in, detD_out, lane); break;
+    }
+}
+
+// Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
+// Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
+// i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
+// The depth-first walk covers the subtree `sub` of 2^split: the first `split`
+// tree levels follow the bits of sub (split <= levels); split = 0: whole tree.
+template <class R, int RFMAX, bool GS>
+__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+                                  const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
+                                  double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
+    // 1. pair interpolation, 0 <= j < k <= n
+    const int npairs = n * (n + 1) / 2;
+    for (int p = lane; p < npairs; p += 32) {
+        int k = (int)((1.0f + sqrtf(8.0f * p + 1.0f)) * 0.5f);
+        while (k * (k - 1) / 2 > p) --k;
+        while ((k + 1) * k / 2 <= p) ++k;
+        int j = p - k * (k - 1) / 2;
+        cx<R> gl, gg;
+        interp_pair<R>(tab, inv_h, s0, L, u[j] - u[k], gl, gg);
+        const int ok = p - j + k - 1;  // vertex k's block: (k-1)(k+2)/2
+        ws.P[ok + j] = gg;
+        ws.Rr[ok + j] = gl;
+        if (j == 0) {  // measurement column of vertex k: g^<(u_k - t), g^>(u_k - t) for the charge
+            cx<R> c0 = nconj(gl), c1 = nconj(gg);
+            if (col) interp_col<R>(col, inv_h, s0, L, u[k] - u[0], c0, c1);
+            ws.Rr[ok + k] = c0;
+            ws.P[ok + k] = c1;
+        }
+    }
+    __syncwarp();
+    // 2. level 0: vertex 1 eliminated (both a_1 kept in the two measurement copies).
+    // Built by 2x2 blocks: block row/column 0 = the measurement copies, block
+    // q >= 1 = vertex q+1 with its two Keldysh indices.  Within a block the
+    // entry is base(ai, aj) - left(ai) right(aj), with left = M(., vertex 1),
+    // right = M(vertex 1, .) / d.
+    const int R0 = n - 1;
+    const int S0 = 2 * R0 + 2;
+    // tree levels: offsets in shared memory, or (split stack) in device memory for the wide ones.
+    // Level l holds S_l^2 = 4 (R0 + 1 - l)^2 entries, so the offset of level l within its part is
+    // 4 (Q(R0 + 1 - l0) - Q(R0 + 1 - l)), Q(x) = x(x+1)(2x+1)/6, l0 = the part's first level.
+    const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
+    int lg = 0;  // levels [0, lg) in device memory: S_l > gs_level
+    if (GS) {
+        lg = R0 + 1 - ws.gs_level / 2;
+        lg = lg < 0 ? 0 : (lg > levels + 1 ? levels + 1 : lg);
+    }
+    auto sq_sum = [](int x) { return x * (x + 1) * (2 * x + 1) / 6; };
+    const int qtop = sq_sum(R0 + 1), qsplit = sq_sum(R0 + 1 - lg);
+    auto level = [&](int l) -> cx<R> * {
+        const int ql = sq_sum(R0 + 1 - l);
+        return (GS && l < lg) ? ws.gstack + 4 * (qtop - ql) : ws.stack + 4 * (qsplit - ql);
+    };
+    // the leaf and its parent are always in shared memory (gs_level >= 14)
+    auto level_smem = [&](int l) -> cx<R> * { return ws.stack + 4 * (qsplit - sq_sum(R0 + 1 - l)); };
+    const cx<R> id = crcp(dv);  // pivot of vertex 1
+    {
+        // Block row b's left factors M(., vertex 1) and block column b's right factors
+        // M(vertex 1, .) / d, once per block index: b = 0 the measurement copies (row entries
+        // r_1(a), column entries c_1(a) / d), b >= 1 vertex b + 1 (pair (1, b + 1)).
+        if (lane < n) {
+            cx<R> l0, l1, r0, r1;
+            if (lane == 0) {
+                l0 = ws.P[0];  // pair (0, 1)
+                l1 = ws.Rr[0];
+                r0 = cmul(ws.Rr[1], id);  // column entries of vertex 1
+                r1 = cmul(ws.P[1], id);
+            } else {
+                const int t = (lane * (lane + 3)) >> 1;  // vertex lane + 1's block
+                l0 = nconj(ws.Rr[t + 1]);
+                l1 = nconj(ws.P[t + 1]);
+                r0 = cmul(ws.P[t + 1], id);
+                r1 = cmul(ws.Rr[t + 1], id);
+            }
+            ws.lr[4 * lane] = l0;
+            ws.lr[4 * lane + 1] = l1;
+            ws.lr[4 * lane + 2] = r0;
+            ws.lr[4 * lane + 3] = r1;
+        }
+        __syncwarp();
+        // lane -> block (bx, by), stepped by 32 blocks without divisions; i = bx + 1 and
+        // j = by + 1 are the vertices, ti and tj the offsets of their packed blocks.  Within a
+        // block the entry is base(ai, aj) - left(ai) right(aj); base is the pair value of the
+        // later vertex's index: above the diagonal (row 0: the measurement row) it follows aj,
+        // below it (column 0: the measurement column, stored as is) it follows ai.
+        const int sq = 32 / n, sr = 32 - sq * n;
+        int bx = lane / n, by = lane - bx * n;
+        for (int bid = lane; bid < n * n; bid += 32) {
+            const int i = bx + 1, j = by + 1;
+            const int ti = (int)((unsigned)((i - 1) * (i + 2)) >> 1), tj = (int)((unsigned)((j - 1) * (j + 2)) >> 1);
+            const bool up = bx < by, diag = bx == by;
+            const int idx = up ? tj + (bx ? i : 0) : ti + (by ? j : i);
+            const cx<R> vP = ws.P[idx], vR = ws.Rr[idx];
+            const cx<R> left0 = ws.lr[4 * bx], left1 = ws.lr[4 * bx + 1];
+            const cx<R> right0 = ws.lr[4 * by + 2], right1 = ws.lr[4 * by + 3];
+            const R sg = (!up && by) ? R(-1) : R(1);  // lower entries of vertex pairs: -conj
+            const cx<R> lo0 = mk<R>(sg * vR.re, vR.im), lo1 = mk<R>(sg * vP.re, vP.im);
+            const cx<R> dd = bx == 0 ? d : dv;
+            const cx<R> b00 = diag ? dd : (up ? vP : lo0), b01 = diag ? dd : (up ? vR : lo0);
+            const cx<R> b10 = diag ? dd : (up ? vP : lo1), b11 = diag ? dd : (up ? vR : lo1);
+            cx<R> *o = level(0) + (2 * bx) * S0 + 2 * by;
+            o[0] = cfms(b00, left0, right0);
+            o[1] = cfms(b01, left0, right1);
+            o[S0] = cfms(b10, left1, right0);
+            o[S0 + 1] = cfms(b11, left1, right1);
+            by += sr;
+            bx += sq;
+            if (by >= n) {
+                by -= n;
+                ++bx;
+            }
+        }
+    }
+    if (lane == 0) ws.detD[0] = dv;
+    __syncwarp();
+    // 3. depth-first tree over a_2 .. a_{levels+1}
+    const int Rleaf = R0 - levels;
+    const int B = Rleaf > RF ? Rleaf - RF : 0;
+    const int Rf = Rleaf - B;
+    Acc<R> ar, ai;
+    ar.init();
+    ai.init();
+    const int nleaf = 1 << (levels - split);
+    const int node = lane >> Rf;
+    const int path = lane & ((1 << Rf) - 1);
+    const bool active = lane < (1 << Rleaf);
+    // With two or more leaves in the walk, leaves come in sibling pairs: the last depth-first step
+    // builds both (the second into ws.sib) and the pair is resolved one after the other.
+    const int twin = twin_leaves<R>() && levels - split >= 1 ? 1 : 0;
+    for (int bl = 0; bl < nleaf; bl += 1 + twin) {
+        const int b = (sub << (levels - split)) | bl;  // tree path: the subtree's fixed prefix, then bl
+        int from = (bl == 0) ? 0 : levels - (__ffs(b) - 1) - 1;
+        for (int l = from; l < levels - twin; ++l) {
+            const int a = (b >> (levels - 1 - l)) & 1;
+            const int S = 2 * (R0 - l) + 2;
+            if (S - 2 <= 32)
+                expand_one<R>(level(l), S, a, level(l + 1), ws.detD + l, ws.detD + l + 1, lane);
+            else
+                expand_level<R>(level(l), S, 1, a, level(l + 1), ws.detD + l, ws.detD + l + 1, ws.wrow, ws.bip,
+                                lane);
+        }
+        if (twin)  // the leaves' parent has 2 kTreeLeaf + 4 rows
+            expand_both_t<R, kTreeLeaf + 1>(level_smem(levels - 1), level_smem(levels), ws.sib,
+                                            ws.detD + levels - 1, ws.detD + levels, ws.detD + levels + 1, lane);
+#pragma unroll 1
+        for (int h = 0; h <= twin; ++h) {
+            const int tparity = __popc(b + h) & 1;
+            // 4. breadth-first expansion of B levels below the tree leaf
+            const cx<R> *E = h ? ws.sib : level_smem(levels);
+            int S = 2 * Rleaf + 2;
+            const cx<R> *ndet = ws.detD + levels + h;
+            cx<R> *dbuf = ws.bdet;
+            size_t bo = 0;
+            for (int lb = 0; lb < B; ++lb) {
+                const int nparent = 1 << lb;
+                cx<R> *out = ws.bfs + bo;
+                expand_level<R>(E, S, 2 * nparent, 0, out, ndet, dbuf, ws.wrow, ws.bip, lane);
+                bo += (size_t)(2 * nparent) * (S - 2) * (S - 2);
+                E = out;
+                S -= 2;
+                ndet = dbuf;
+                dbuf = (dbuf == ws.bdet) ? ws.bdet + 32 : ws.bdet;
+            }
+            // 5. per-lane flat phase on the last Rf vertices
+            if (active) {
+                const cx<R> *En = E + (size_t)node * S * S;
+                const int parity = tparity ^ (__popc(node) & 1);
+                flat_dispatch<R, RFMAX>(Rf, En, ndet[B > 0 ? node : 0], parity, path, ar, ai);
+            }
+            __syncwarp();
+        }
+    }
+    return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+}
+
+}  // namespace single
+
+namespace pairs {
+
+// ----------------------------------------------------------------------------
 // Pair-block Schur tree for the Keldysh sum.
 //
 // Every vertex diagonal of M_down is g^<(0) - i alpha.  With alpha at the
@@ -349,7 +1036,8 @@ template <class R>
 __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_level) {
     const LeafBufs lb = leaf_bufs(n_max, RF);
     size_t c = (gs_level ? stack_cap(n_max, 1, gs_level) : stack_cap(n_max, 0, 0)) + pair_entries(n_max) +
-               n_max + 2 + 8 * (size_t)n_max + lb.bfs + lb.wrow + lb.bip + 2 * lb.half;
+               n_max + 2 + 8 * (size_t)n_max + 20 * (size_t)tree_shape(n_max).dfl + lb.bfs + lb.wrow + lb.bip +
+               2 * lb.half;
     size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
     if (!gs_level) bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
     return (bytes + 127) & ~(size_t)127;
@@ -394,6 +1082,7 @@ struct WarpSmem {
     cx<R> *Rr;      // Rr[o_k + j] = g^<(u_j - u_k); Rr[o_k + k] = column entry (k, a_k = 0)
     cx<R> *detD;    // det M_down of the eliminated vertices per tree level (level 0: both roots when g = 1)
     cx<R> *lr;      // root: per block index L(., 0), L(., 1), B^-1 R(., 0), B^-1 R(., 1) (8 entries)
+    cx<R> *piv;     // per depth-first parent level: its four children's B^-1 and det B (node_pivots)
     cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
     cx<R> *wrow;    // general pair step: B^-1 (row p; row q) per child column
     cx<R> *bip;     // general pair step: B^-1 per child
@@ -421,6 +1110,8 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     p += n_max + 2;
     w.lr = p;
     p += 8 * n_max;
+    w.piv = p;
+    p += 20 * tree_shape(n_max).dfl;
     w.bfs = p;
     p += lb.bfs;
     w.wrow = p;
@@ -436,38 +1127,8 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     return w;
 }
 
-template <class R>
-__device__ __forceinline__ cx<R> sel(int bit, cx<R> one, cx<R> zero) {
-    return mk<R>(bit ? one.re : zero.re, bit ? one.im : zero.im);
-}
-template <class R>
-__device__ __forceinline__ cx<R> cneg(cx<R> a) {
-    return mk<R>(-a.re, -a.im);
-}
-template <class R>
-__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
-    return mk<R>(a.re - b.re, a.im - b.im);
-}
-// c + a * b
-template <class R>
-__device__ __forceinline__ cx<R> cfma(cx<R> c, cx<R> a, cx<R> b) {
-    return mk<R>(fmaR(a.re, b.re, fmaR(-a.im, b.im, c.re)), fmaR(a.re, b.im, fmaR(a.im, b.re, c.im)));
-}
-
 // packed offset of vertex k's block
 __device__ __forceinline__ int vblk(int k) { return (int)((unsigned)((k - 1) * (k + 2)) >> 1); }
-
-// Leaf term after a lone last vertex p: with pivot pv and the copies' entries,
-//   det' = det pv,   S_cc = m_cc - m_cp m_pc / pv   (c = copy 0, 1),
-//   det'^2 (S_00 - S_11) = det^2 pv (pv (m_00 - m_11) - (m_0p m_p0 - m_1p m_p1)):
-// no reciprocal, so a vanishing pivot (det M_down = 0) gives a zero term.
-template <class R>
-__device__ __forceinline__ cx<R> leaf_term(cx<R> m00, cx<R> m11, cx<R> m0p, cx<R> mp0, cx<R> m1p, cx<R> mp1, cx<R> pv,
-                                           cx<R> det) {
-    const cx<R> q = cfms(cmul(m0p, mp0), m1p, mp1);  // m0p mp0 - m1p mp1
-    const cx<R> r = cfms(q, pv, csub(m00, m11));      // q - pv (m00 - m11)
-    return cmul(cmul(det, det), cmul(pv, cneg(r)));
-}
 
 // Leaf term after the last vertex pair (p, q), also without a reciprocal:
 //   delta = det B,  x_c = (m_cp, m_cq) adj(B) (m_pc, m_qc)^T,
@@ -659,22 +1320,44 @@ __device__ void build_root(const WarpSmem<R> &ws, int n, int s, cx<R> d, cx<R> d
     __syncwarp();
 }
 
+// Pivot data of the four children of a node (S x S, vertex pair in rows 2-3 and
+// 4-5), once per node: child (a, b) has the block B = E[{p,q},{p,q}], p = 2 + a,
+// q = 4 + b, and pv[5 (2a + b) + 0..3] = B^-1 (row major), pv[5 (2a + b) + 4] =
+// det B.  Four lanes work; the depth-first steps to the node's children read it.
+template <class R>
+__device__ __forceinline__ void node_pivots(const cx<R> *__restrict__ E, int S, cx<R> *pv, int lane) {
+    if (lane < 4) {
+        const int p = 2 + (lane >> 1), q = 4 + (lane & 1);
+        const cx<R> bpp = E[p * S + p], bpq = E[p * S + q], bqp = E[q * S + p], bqq = E[q * S + q];
+        const cx<R> del = cfms(cmul(bpp, bqq), bpq, bqp);
+        const cx<R> id = crcp(del);
+        cx<R> *o = pv + 5 * lane;
+        o[0] = cmul(bqq, id);
+        o[1] = cneg(cmul(bpq, id));
+        o[2] = cneg(cmul(bqp, id));
+        o[3] = cmul(bpp, id);
+        o[4] = del;
+    }
+    __syncwarp();
+}
+
 // One child of a depth-first pair step: the vertices in rows 2-3 and 4-5 of
 // the S x S parent fixed to (a, b), pivot block B = E[{p,q},{p,q}] (p = 2 + a,
-// q = 4 + b); the (S - 4) x (S - 4) child keeps parent rows/columns 0, 1, 6, 7,
-// ...  Entry E_xy - E_xp W0_y - E_xq W1_y with (W0; W1) = B^-1 (E_p.; E_q.).
-// A step is latency-bound, so every load is issued before the pivot's
-// reciprocal.  Children of 2T = 12, 14 or 16 rows: lanes 0-15 take the even
-// rows, lanes 16-31 the odd rows, column c2 = lane & 15.
+// q = 4 + b) with B^-1 and det B in pv (node_pivots); the (S - 4) x (S - 4)
+// child keeps parent rows/columns 0, 1, 6, 7, ...  Entry E_xy - E_xp W0_y -
+// E_xq W1_y with (W0; W1) = B^-1 (E_p.; E_q.).  A step is latency-bound, so
+// every load is issued first.  Children of 2T = 12, 14 or 16 rows: lanes 0-15
+// take the even rows, lanes 16-31 the odd rows, column c2 = lane & 15.
 template <class R, int T>
-__device__ __forceinline__ void pair_one_t(const cx<R> *__restrict__ in, int a, int b, cx<R> *__restrict__ out,
-                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+__device__ __forceinline__ void pair_one_t(const cx<R> *__restrict__ in, int a, int b, const cx<R> *pv,
+                                           cx<R> *__restrict__ out, const cx<R> *detD_in, cx<R> *detD_out,
+                                           int lane) {
     constexpr int S2 = 2 * T, S = S2 + 4;
     const int p = 2 + a, q = 4 + b;
     const int c2 = lane & 15, rsub = lane >> 4;
     const bool act = c2 < S2;
     const int c = c2 < 2 ? c2 : c2 + 4;
-    const cx<R> bpp = in[p * S + p], bpq = in[p * S + q], bqp = in[q * S + p], bqq = in[q * S + q];
+    const cx<R> b00 = pv[0], b01 = pv[1], b10 = pv[2], b11 = pv[3];
     cx<R> epc = mk<R>(0, 0), eqc = mk<R>(0, 0), ev[T], ep[T], eq[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) ev[t] = ep[t] = eq[t] = mk<R>(0, 0);
@@ -690,12 +1373,10 @@ __device__ __forceinline__ void pair_one_t(const cx<R> *__restrict__ in, int a, 
             eq[t] = in[r * S + q];
         }
     }
-    const cx<R> del = cfms(cmul(bpp, bqq), bpq, bqp);
-    const cx<R> id = crcp(del);
-    if (lane == 0) *detD_out = cmul(*detD_in, del);
+    if (lane == 0) *detD_out = cmul(*detD_in, pv[4]);
     if (act) {
-        const cx<R> w0 = cmul(cfms(cmul(bqq, epc), bpq, eqc), id);
-        const cx<R> w1 = cmul(cfms(cmul(bpp, eqc), bqp, epc), id);
+        const cx<R> w0 = cfma(cmul(b00, epc), b01, eqc);
+        const cx<R> w1 = cfma(cmul(b10, epc), b11, eqc);
 #pragma unroll
         for (int t = 0; t < T; ++t) out[(rsub + 2 * t) * S2 + c2] = cfms(cfms(ev[t], ep[t], w0), eq[t], w1);
     }
@@ -705,21 +1386,18 @@ __device__ __forceinline__ void pair_one_t(const cx<R> *__restrict__ in, int a, 
 // Wider children (S - 4 = 18 .. 32 rows): lane = column, rows in batches
 // (eight in FP32, four in FP64) with the batch's loads issued first.
 template <class R>
-__device__ __forceinline__ void pair_one_wide(const cx<R> *__restrict__ in, int S, int a, int b,
+__device__ __forceinline__ void pair_one_wide(const cx<R> *__restrict__ in, int S, int a, int b, const cx<R> *pv,
                                               cx<R> *__restrict__ out, const cx<R> *detD_in, cx<R> *detD_out,
                                               int lane) {
     constexpr int NB = sizeof(R) == 4 ? 8 : 4;  // rows per batch (FP64: register budget)
     const int S2 = S - 4;
     const int p = 2 + a, q = 4 + b;
-    const cx<R> bpp = in[p * S + p], bpq = in[p * S + q], bqp = in[q * S + p], bqq = in[q * S + q];
-    const cx<R> del = cfms(cmul(bpp, bqq), bpq, bqp);
-    const cx<R> id = crcp(del);
-    if (lane == 0) *detD_out = cmul(*detD_in, del);
+    if (lane == 0) *detD_out = cmul(*detD_in, pv[4]);
     if (lane < S2) {
         const int c = lane < 2 ? lane : lane + 4;
         const cx<R> epc = in[p * S + c], eqc = in[q * S + c];
-        const cx<R> w0 = cmul(cfms(cmul(bqq, epc), bpq, eqc), id);
-        const cx<R> w1 = cmul(cfms(cmul(bpp, eqc), bqp, epc), id);
+        const cx<R> w0 = cfma(cmul(pv[0], epc), pv[1], eqc);
+        const cx<R> w1 = cfma(cmul(pv[2], epc), pv[3], eqc);
         for (int r0 = 0; r0 < S2; r0 += NB) {
             cx<R> ev[NB], ep[NB], eq[NB];
 #pragma unroll
@@ -745,10 +1423,15 @@ __device__ __forceinline__ void pair_one_wide(const cx<R> *__restrict__ in, int 
 // depth-first children wider than a warp.
 template <class R>
 __device__ void pair_level(const cx<R> *__restrict__ in, int S, int nchild, int a1, int b1, cx<R> *__restrict__ out,
-                           const cx<R> *detD_in, cx<R> *detD_out, cx<R> *__restrict__ wrow, cx<R> *binv, int lane) {
+                           const cx<R> *detD_in, cx<R> *detD_out, cx<R> *__restrict__ wrow, cx<R> *binv, int lane,
+                           const cx<R> *pv = nullptr) {
     const int S2 = S - 4;
+    if (pv) {  // one child whose pivot data the node already holds
+        if (lane < 4) binv[lane] = pv[lane];
+        if (lane == 0) detD_out[0] = cmul(detD_in[0], pv[4]);
+    }
     // pivot blocks: B^-1 and the running det M_down per child
-    for (int j = lane; j < nchild; j += 32) {
+    for (int j = lane; j < (pv ? 0 : nchild); j += 32) {
         const int a = nchild == 1 ? a1 : (j >> 1) & 1, b = nchild == 1 ? b1 : j & 1;
         const int pj = nchild == 1 ? 0 : j >> 2;
         const cx<R> *E = in + (size_t)pj * S * S;
@@ -813,18 +1496,20 @@ __device__ void pair_level(const cx<R> *__restrict__ in, int S, int nchild, int 
 }
 
 // One depth-first pair step from an S x S parent.
+// pv: the parent's pivot data for this child (node_pivots).
 template <class R>
-__device__ __forceinline__ void pair_step(const WarpSmem<R> &ws, const cx<R> *in, int S, int a, int b, cx<R> *out,
-                                          const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+__device__ __forceinline__ void pair_step(const WarpSmem<R> &ws, const cx<R> *in, int S, int a, int b,
+                                          const cx<R> *pv, cx<R> *out, const cx<R> *detD_in, cx<R> *detD_out,
+                                          int lane) {
     switch (S - 4) {
-        case 12: pair_one_t<R, 6>(in, a, b, out, detD_in, detD_out, lane); break;
-        case 14: pair_one_t<R, 7>(in, a, b, out, detD_in, detD_out, lane); break;
-        case 16: pair_one_t<R, 8>(in, a, b, out, detD_in, detD_out, lane); break;
+        case 12: pair_one_t<R, 6>(in, a, b, pv, out, detD_in, detD_out, lane); break;
+        case 14: pair_one_t<R, 7>(in, a, b, pv, out, detD_in, detD_out, lane); break;
+        case 16: pair_one_t<R, 8>(in, a, b, pv, out, detD_in, detD_out, lane); break;
         default:
             if (S - 4 <= 32)
-                pair_one_wide<R>(in, S, a, b, out, detD_in, detD_out, lane);
+                pair_one_wide<R>(in, S, a, b, pv, out, detD_in, detD_out, lane);
             else
-                pair_level<R>(in, S, 1, a, b, out, detD_in, detD_out, ws.wrow, ws.bip, lane);
+                pair_level<R>(in, S, 1, a, b, out, detD_in, detD_out, ws.wrow, ws.bip, lane, pv);
             break;
     }
 }
@@ -858,31 +1543,6 @@ __device__ __forceinline__ void leaf_group(const WarpSmem<R> &ws, const cx<R> *E
         ai.add(term.im);
     }
     __syncwarp();
-}
-
-// Float-float or double-double style butterfly of the lane accumulators:
-// combines (s, c) pairs with two-sum in R, then returns s + c in double.
-template <class R>
-__device__ __forceinline__ void two_sum_r(R a, R b, R &s, R &e) {
-    s = a + b;
-    R z = s - a;
-    e = (a - (s - z)) + (b - z);
-}
-
-template <class R>
-__device__ __forceinline__ double warp_total(Acc<R> acc) {
-    R s = acc.s, c = acc.c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        R s2 = __shfl_xor_sync(FULL, s, o);
-        R c2 = __shfl_xor_sync(FULL, c, o);
-        R t, e;
-        int lo = ((threadIdx.x & 31) & o) == 0;
-        if (lo) two_sum_r<R>(s, s2, t, e); else two_sum_r<R>(s2, s, t, e);
-        s = t;
-        c = lo ? (c + c2) + e : (c2 + c) + e;
-    }
-    return (double)s + (double)c;
 }
 
 // Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
@@ -954,37 +1614,92 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
             for (int j = dev ? 0 : lg; j < l; ++j) off += level_entries(ts, j);
             return (dev ? ws.gstack : ws.stack) + off;
         };
-        if (ts.g) {
-            cx<R> *root = level(0);
-            build_root<R>(ws, n, 0, d, dv, root, ws.detD, lane);
-            build_root<R>(ws, n, 1, d, dv, root + Sr * Sr, ws.detD + 1, lane);
-            leaf_group<R, RFMAX>(ws, root, ws.detD, 1, ts.Rleaf, B, F, 0, ar, ai, lane);
-        } else {
-            const int free_bits = ts.lbits - split;
-            const int nleaf = 1 << free_bits;
-            for (int bl = 0; bl < nleaf; ++bl) {
-                const int b = (sub << free_bits) | bl;  // leaf index: the subtree's fixed prefix, then bl
-                int from = 0;
-                if (bl) {  // rebuild from the level of the highest index bit that changed
-                    const int pos = __ffs(b) - 1;
-                    from = pos == ts.lbits - 1 ? 0 : (ts.lbits - pos) >> 1;
-                }
-                for (int l = from; l <= ts.dfl; ++l) {
-                    if (l == 0) {
-                        build_root<R>(ws, n, (b >> (ts.lbits - 1)) & 1, d, dv, level(0), ws.detD, lane);
-                    } else {
-                        const int a = (b >> (ts.lbits - 2 * l)) & 1, c = (b >> (ts.lbits - 2 * l - 1)) & 1;
-                        pair_step<R>(ws, level(l - 1), Sr - 4 * (l - 1), a, c, level(l), ws.detD + l - 1,
-                                     ws.detD + l, lane);
-                    }
-                }
-                leaf_group<R, RFMAX>(ws, level(ts.dfl), ws.detD + ts.dfl, 0, ts.Rleaf, B, F, __popc(b) & 1, ar, ai,
-                                     lane);
+        // Depth-first walk over the leaves (one leaf group, both roots, when g = 1).  Each code
+        // path below has one call site, which keeps the inlined kernel small.
+        const int free_bits = ts.g ? 0 : ts.lbits - split;
+        const int nleaf = 1 << free_bits;
+        for (int bl = 0; bl < nleaf; ++bl) {
+            const int b = (sub << free_bits) | bl;  // leaf index: the subtree's fixed prefix, then bl
+            int from = 0;
+            if (bl) {  // rebuild from the level of the highest index bit that changed
+                const int pos = __ffs(b) - 1;
+                from = pos == ts.lbits - 1 ? 0 : (ts.lbits - pos) >> 1;
             }
+            for (int l = from; l <= ts.dfl; ++l) {
+                cx<R> *E = level(l);
+                const int S = Sr - 4 * l;
+                if (l == 0) {
+                    for (int r = 0; r <= ts.g; ++r)  // a_2 = the top leaf-index bit, or both roots
+                        build_root<R>(ws, n, ts.g ? r : (b >> (ts.lbits - 1)) & 1, d, dv, E + r * Sr * Sr,
+                                      ws.detD + r, lane);
+                } else {
+                    const int a = (b >> (ts.lbits - 2 * l)) & 1, c = (b >> (ts.lbits - 2 * l - 1)) & 1;
+                    pair_step<R>(ws, level(l - 1), S + 4, a, c, ws.piv + 20 * (l - 1) + 5 * (2 * a + c), E,
+                                 ws.detD + l - 1, ws.detD + l, lane);
+                }
+                if (l < ts.dfl) node_pivots<R>(E, S, ws.piv + 20 * l, lane);
+            }
+            leaf_group<R, RFMAX>(ws, level(ts.dfl), ws.detD + ts.dfl, ts.g, ts.Rleaf, B, F,
+                                 ts.g ? 0 : __popc(b) & 1, ar, ai, lane);
         }
     }
     return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
 }
+
+
+}  // namespace pairs
+
+// The two trees behind one interface for the determinant kernels.
+struct SingleTree {
+    template <class R>
+    using Smem = single::WarpSmem<R>;
+    template <class R>
+    __host__ __device__ static size_t smem_bytes(int n_max, int RF, bool gs) {
+        return single::warp_smem_bytes<R>(n_max, RF, gs);
+    }
+    template <class R>
+    __host__ __device__ static size_t gstack_entries(int n_max, int RF) {
+        return single::gstack_entries<R>(n_max, RF);
+    }
+    template <class R>
+    __device__ static Smem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack) {
+        return single::carve<R>(base, n_max, RF, gstack);
+    }
+    template <class R, int RFMAX, bool GS>
+    __device__ static cx<double> sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+                                     const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
+                                     double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
+        return single::keldysh_sum<R, RFMAX, GS>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
+                                                 split);
+    }
+    // depth-first levels above the tree leaf (5 vertices), one bit of the leaf index each
+    static int leaf_bits(int n) { return n - 1 > single::kTreeLeaf ? n - 1 - single::kTreeLeaf : 0; }
+};
+
+struct PairTree {
+    template <class R>
+    using Smem = pairs::WarpSmem<R>;
+    template <class R>
+    __host__ __device__ static size_t smem_bytes(int n_max, int RF, bool gs) {
+        return pairs::warp_smem_bytes<R>(n_max, RF, gs);
+    }
+    template <class R>
+    __host__ __device__ static size_t gstack_entries(int n_max, int RF) {
+        return pairs::gstack_entries<R>(n_max, RF);
+    }
+    template <class R>
+    __device__ static Smem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack) {
+        return pairs::carve<R>(base, n_max, RF, gstack);
+    }
+    template <class R, int RFMAX, bool GS>
+    __device__ static cx<double> sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+                                     const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
+                                     double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
+        return pairs::keldysh_sum<R, RFMAX, GS>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
+                                                split);
+    }
+    static int leaf_bits(int n) { return pairs::tree_shape(n).lbits; }
+};
 
 // One point per lane (small orders), registers only: the lane interpolates its
 // own pairs, and for each a_2 and every choice path of vertices 3..N builds the
@@ -1028,7 +1743,7 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
             const cx<R> del = cfms(cmul(dv, dv), m12, m21);
             if constexpr (N == 2) {  // the root pair is the last pair
                 const cx<R> term =
-                    leaf_pair(d, d, P[0][1], m02, C0[1], m20, Rr[0][1], m02, C1[1], m20, dv, m12, m21, dv, mk<R>(1, 0));
+                    pairs::leaf_pair(d, d, P[0][1], m02, C0[1], m20, Rr[0][1], m02, C1[1], m20, dv, m12, m21, dv, mk<R>(1, 0));
                 ar.add(s ? -term.re : term.re);
                 ai.add(s ? -term.im : term.im);
             } else {
@@ -1080,7 +1795,7 @@ __device__ __forceinline__ cx<double> lane_keldysh_sum(const double *u, cx<R> d,
                         term = leaf_term(m[0][0], m[1][1], m[0][2], m[2][0], m[1][2], m[2][1], m[2][2], del);
                     } else {
                         static_assert(N == 4, "one point per lane serves orders 1..4");
-                        term = leaf_pair(m[0][0], m[1][1], m[0][2], m[0][3], m[2][0], m[3][0], m[1][2], m[1][3],
+                        term = pairs::leaf_pair(m[0][0], m[1][1], m[0][2], m[0][3], m[2][0], m[3][0], m[1][2], m[1][3],
                                          m[2][1], m[3][1], m[2][2], m[2][3], m[3][2], m[3][3], del);
                     }
                     if ((s + __popc(path)) & 1) term = cneg(term);
@@ -1197,7 +1912,7 @@ __device__ __forceinline__ unsigned unit_flag(double a, double b, double c, doub
 // ----------------------------------------------------------------------------
 // Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
 // ----------------------------------------------------------------------------
-template <class R, int RFMAX, bool GS>
+template <class Tree, class R, int RFMAX, bool GS>
 __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
                               unsigned long long *counter, int n_max, int rf_min, cx<R> *gstack,
                               unsigned long long *span) {
@@ -1206,8 +1921,11 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
     const int warp = threadIdx.x >> 5;
     if (span && lane == 0) atomicMin(span, gtimer());
     cx<R> *gst = nullptr;
-    if (GS) gst = gstack + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * gstack_entries<R>(n_max, rf_min);
-    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, rf_min, GS), n_max, rf_min, gst);
+    if (GS)
+        gst = gstack +
+              ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * Tree::template gstack_entries<R>(n_max, rf_min);
+    const auto ws = Tree::template carve<R>(
+        smem_raw + (size_t)warp * Tree::template smem_bytes<R>(n_max, rf_min, GS), n_max, rf_min, gst);
     const int NU = n_max + 1;
     while (true) {
         unsigned long long c = 0;
@@ -1259,8 +1977,9 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
             // every warp-per-point item of a launch shares the launch's flat depth
-            cx<double> s = keldysh_sum<R, RFMAX, GS>(ws, ws.upt + src * NU, n, n_max, d, dv, tab, item_col<R>(I), inv_h,
-                                                     s0, I.L, RFMAX, lane, sub, I.split);
+            cx<double> s = Tree::template sum<R, RFMAX, GS>(ws, ws.upt + src * NU, n, n_max, d, dv, tab,
+                                                            item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sub,
+                                                            I.split);
             if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
@@ -1460,15 +2179,16 @@ __global__ void warp_kernel(int order, uint64_t first, uint64_t count, const uin
 
 // One warp per caller point.
 // One warp per caller point, grid-stride over the points.
-template <class R, int RF, bool GS>
+template <class Tree, class R, int RF, bool GS>
 __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, double *out, int n_max, cx<R> *gstack) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint64_t wid = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
     cx<R> *gst = nullptr;
-    if (GS) gst = gstack + wid * gstack_entries<R>(n_max, RF);
-    WarpSmem<R> ws = carve<R>(smem_raw + (size_t)warp * warp_smem_bytes<R>(n_max, RF, GS), n_max, RF, gst);
+    if (GS) gst = gstack + wid * Tree::template gstack_entries<R>(n_max, RF);
+    const auto ws = Tree::template carve<R>(smem_raw + (size_t)warp * Tree::template smem_bytes<R>(n_max, RF, GS),
+                                            n_max, RF, gst);
     const int n = I.order;
     const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
     const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
@@ -1476,8 +2196,8 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     for (uint64_t q = wid; q < count; q += (uint64_t)gridDim.x * (blockDim.x >> 5)) {
         if (lane <= n) ws.upt[lane] = lane == 0 ? I.t : u[q * n + lane - 1];
         __syncwarp();
-        cx<double> s = keldysh_sum<R, RF, GS>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I), inv_h,
-                                          I.T * inv_h, I.L, RF, lane);
+        cx<double> s = Tree::template sum<R, RF, GS>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I),
+                                                     inv_h, I.T * inv_h, I.L, RF, lane);
         if (lane == 0) {
             cx<double> cval = times_i_pow(s, n);
             out[2 * q] = cval.re;
@@ -1723,6 +2443,17 @@ int upload_direction_numbers() {
     return QQMC_OK;
 }
 
+// Every kernel of the library prefers the largest shared-memory carveout, the
+// one the determinant kernels need: an SM runs blocks of different kernels side
+// by side only while they agree on its L1 / shared-memory split, so small
+// kernels (table builds, one-point-per-lane items, reductions) of another
+// launch can start next to running determinant blocks instead of waiting for
+// the SM to drain.
+template <class K>
+static void prefer_shared(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
 int launch_gf_table(const Problem &pr, cudaStream_t s) {
     const qqmc_params &p = pr.params;
     double wm = fmin(p.eps_d, 0.0) - 3.0 * p.gamma;
@@ -1731,6 +2462,7 @@ int launch_gf_table(const Problem &pr, cudaStream_t s) {
     int warps = pr.L / 2;
     int threads = 128;
     int blocks = (warps * 32 + threads - 1) / threads;
+    prefer_shared(gf_table_kernel);
     gf_table_kernel<<<blocks, threads, 0, s>>>(pr.d_table, pr.d_table32, pr.L, p.t_max, pr.h, p.eps_d, p.gamma,
                                                panels);
     cudaError_t e = cudaGetLastError();
@@ -1786,11 +2518,14 @@ int launch_lead_table(Problem &pr, cudaStream_t s, double *zero) {
         return set_error(QQMC_E_INVAL, "half_bandwidth x t_max too large for the lead-table quadrature");
     double *d_w = nullptr, *d_zero = nullptr;
     dbl4 *d_s00 = nullptr, *d_s01 = nullptr;
-    cudaError_t e = cudaMalloc(&d_w, nq * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&d_s00, nq * sizeof(dbl4));
-    if (e == cudaSuccess) e = cudaMalloc(&d_s01, nq * sizeof(dbl4));
-    if (e == cudaSuccess) e = cudaMalloc(&d_zero, 4 * sizeof(double));
+    // stream-ordered temporaries: no device-wide synchronisation with other streams' work
+    cudaError_t e = cudaMallocAsync(&d_w, nq * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_s00, nq * sizeof(dbl4), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_s01, nq * sizeof(dbl4), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_zero, 4 * sizeof(double), s);
     if (e == cudaSuccess) {
+        prefer_shared(lead_spectrum_kernel);
+        prefer_shared(lead_table_kernel);
         lead_spectrum_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(q, (int)nq, d_w, d_s00, d_s01);
         e = cudaGetLastError();
     }
@@ -1801,28 +2536,23 @@ int launch_lead_table(Problem &pr, cudaStream_t s, double *zero) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(zero, d_zero, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d_w);
-    cudaFree(d_s00);
-    cudaFree(d_s01);
-    cudaFree(d_zero);
+    if (d_w) cudaFreeAsync(d_w, s);
+    if (d_s00) cudaFreeAsync(d_s00, s);
+    if (d_s01) cudaFreeAsync(d_s01, s);
+    if (d_zero) cudaFreeAsync(d_zero, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return cuda_error(e, "lead table build");
     return QQMC_OK;
 }
 
-int tree_leaf_bits(int order) { return tree_shape(order).lbits; }
-
-size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune) {
-    size_t per = precision == QQMC_PREC_FP64 ? warp_smem_bytes<double>(n_max, tune.flat_min)
-                                             : warp_smem_bytes<float>(n_max, tune.flat_min);
-    return per * tune.warps_per_block;
-}
+int tree_leaf_bits(int order, bool pairs) { return pairs ? PairTree::leaf_bits(order) : SingleTree::leaf_bits(order); }
 
 // The tree stack is split (wide top levels in device memory) where it does not
 // fit in shared memory, and from the order set by qqmc_set_stack_policy
-// (default: from order 11 in both precisions, measured fastest on GB300): a large
-// shared-memory stack limits the warps per SM, while the wide levels are built
-// only a few times per point.
+// (default: from order 11 in both precisions, measured fastest on GB300 with the
+// single-vertex tree): a large shared-memory stack limits the warps per SM, while
+// the wide levels are built only a few times per point.
 constexpr int kGsDefault[2] = {11, 11};
 static std::atomic<int> g_gs_min_order[2] = {{kGsDefault[0]}, {kGsDefault[1]}};  // read by plans on any thread
 
@@ -1831,27 +2561,29 @@ void set_stack_policy(int precision, int min_order) {
     g_gs_min_order[p].store(min_order <= 0 ? kGsDefault[p] : min_order);
 }
 
-template <class R>
+template <class Tree, class R>
 static bool stack_in_global(int n_max, int rf_min) {
-    return warp_smem_bytes<R>(n_max, rf_min) > kSmemMax || n_max >= g_gs_min_order[sizeof(R) == 8 ? 0 : 1].load();
+    return Tree::template smem_bytes<R>(n_max, rf_min, false) > kSmemMax ||
+           n_max >= g_gs_min_order[sizeof(R) == 8 ? 0 : 1].load();
 }
 
-template <class R, int F, bool GS>
+template <class Tree, class R, int F, bool GS>
 static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
                                    long long gstack_warps, unsigned long long *span, cudaStream_t s) {
     // fewer warps per block when the shared memory of the requested shape does not fit
-    const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min, GS);
+    const size_t per_warp = Tree::template smem_bytes<R>(n_max, rf_min, GS);
     if (per_warp > kSmemMax) return cudaErrorInvalidConfiguration;
     while (wpb > 1 && per_warp * wpb > kSmemMax) --wpb;
     size_t smem = per_warp * wpb;
-    cudaError_t e =
-        cudaFuncSetAttribute(detsum_kernel<R, F, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = detsum_kernel<Tree, R, F, GS>;
+    prefer_shared(kern);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, detsum_kernel<R, F, GS>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long want = (total_chunks + wpb - 1) / wpb;
@@ -1862,61 +2594,75 @@ static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long lon
         if (grid > gstack_warps / wpb) grid = gstack_warps / wpb;
     }
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    detsum_kernel<R, F, GS><<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max,
-                                                                    rf_min, static_cast<cx<R> *>(gstack), span);
+    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(d_items, n_items, total_chunks, d_counter, n_max, rf_min,
+                                                static_cast<cx<R> *>(gstack), span);
     return cudaGetLastError();
 }
 
-template <class R, int F>
+template <class Tree, class R, int F>
 static cudaError_t launch_detsum_f(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
                                    long long gstack_warps, unsigned long long *span, cudaStream_t s) {
     // without a device-memory buffer (the allocation-free entry) the shared-memory stack serves where it fits
-    if (stack_in_global<R>(n_max, rf_min) && (gstack || warp_smem_bytes<R>(n_max, rf_min) > kSmemMax))
-        return launch_detsum_t<R, F, true>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack,
-                                           gstack_warps, span, s);
-    return launch_detsum_t<R, F, false>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, nullptr, 0,
-                                        span, s);
+    if (stack_in_global<Tree, R>(n_max, rf_min) &&
+        (gstack || Tree::template smem_bytes<R>(n_max, rf_min, false) > kSmemMax))
+        return launch_detsum_t<Tree, R, F, true>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min,
+                                                 gstack, gstack_warps, span, s);
+    return launch_detsum_t<Tree, R, F, false>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min,
+                                              nullptr, 0, span, s);
 }
 
 static int clamp_rf_min(const Tuning &tune) {
     return tune.flat_min < 2 ? 2 : (tune.flat_min > tune.flat ? tune.flat : tune.flat_min);
 }
 
-template <class R>
+template <class Tree, class R>
 static long long gstack_warps_t(int n_max, int rf_min, size_t *bytes_per_warp) {
     *bytes_per_warp = 0;
-    if (!stack_in_global<R>(n_max, rf_min)) return 0;
+    if (!stack_in_global<Tree, R>(n_max, rf_min)) return 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t per_warp = warp_smem_bytes<R>(n_max, rf_min, true);
+    const size_t per_warp = Tree::template smem_bytes<R>(n_max, rf_min, true);
     long long per_sm = (long long)(kSmemMax / per_warp);  // resident warps, bound by shared memory
     if (per_sm > 64) per_sm = 64;                          // and by the SM's warp slots
-    *bytes_per_warp = gstack_entries<R>(n_max, rf_min) * sizeof(cx<R>);
+    *bytes_per_warp = Tree::template gstack_entries<R>(n_max, rf_min) * sizeof(cx<R>);
     return (long long)sms * (per_sm < 1 ? 1 : per_sm);
 }
 
-bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune) {
-    const int rf_min = clamp_rf_min(tune);
-    return precision == QQMC_PREC_FP64 ? warp_smem_bytes<double>(n_max, rf_min) <= kSmemMax
-                                       : warp_smem_bytes<float>(n_max, rf_min) <= kSmemMax;
+template <class Tree>
+static bool stack_fits_t(int n_max, int precision, int rf_min) {
+    return precision == QQMC_PREC_FP64 ? Tree::template smem_bytes<double>(n_max, rf_min, false) <= kSmemMax
+                                       : Tree::template smem_bytes<float>(n_max, rf_min, false) <= kSmemMax;
 }
 
-long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp) {
+bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune, bool pairs) {
     const int rf_min = clamp_rf_min(tune);
-    return precision == QQMC_PREC_FP64 ? gstack_warps_t<double>(n_max, rf_min, bytes_per_warp)
-                                       : gstack_warps_t<float>(n_max, rf_min, bytes_per_warp);
+    return pairs ? stack_fits_t<PairTree>(n_max, precision, rf_min) : stack_fits_t<SingleTree>(n_max, precision, rf_min);
 }
 
-cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
-                          int n_max, int precision, const Tuning &tune, void *gstack, long long gstack_warps,
-                          unsigned long long *span, cudaStream_t s) {
+template <class Tree>
+static long long gstack_warps_p(int n_max, int precision, int rf_min, size_t *bytes_per_warp) {
+    return precision == QQMC_PREC_FP64 ? gstack_warps_t<Tree, double>(n_max, rf_min, bytes_per_warp)
+                                       : gstack_warps_t<Tree, float>(n_max, rf_min, bytes_per_warp);
+}
+
+long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, bool pairs, size_t *bytes_per_warp) {
+    const int rf_min = clamp_rf_min(tune);
+    return pairs ? gstack_warps_p<PairTree>(n_max, precision, rf_min, bytes_per_warp)
+                 : gstack_warps_p<SingleTree>(n_max, precision, rf_min, bytes_per_warp);
+}
+
+template <class Tree>
+static cudaError_t launch_detsum_tree(const ItemDev *d_items, int n_items, long long total_chunks,
+                                      unsigned long long *d_counter, int n_max, int precision, const Tuning &tune,
+                                      void *gstack, long long gstack_warps, unsigned long long *span,
+                                      cudaStream_t s) {
     const int wpb = tune.warps_per_block;
     const int rf_min = clamp_rf_min(tune);
-#define QQMC_DETSUM(RT, F)                                                                                        \
-    launch_detsum_f<RT, F>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack, gstack_warps, \
-                           span, s)
+#define QQMC_DETSUM(RT, F)                                                                                         \
+    launch_detsum_f<Tree, RT, F>(d_items, n_items, total_chunks, d_counter, n_max, wpb, rf_min, gstack,          \
+                                 gstack_warps, span, s)
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
             case 2: return QQMC_DETSUM(double, 2);
@@ -1934,6 +2680,15 @@ cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_c
 #undef QQMC_DETSUM
 }
 
+cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
+                          int n_max, int precision, const Tuning &tune, bool pairs, void *gstack,
+                          long long gstack_warps, unsigned long long *span, cudaStream_t s) {
+    return pairs ? launch_detsum_tree<PairTree>(d_items, n_items, total_chunks, d_counter, n_max, precision, tune,
+                                                gstack, gstack_warps, span, s)
+                 : launch_detsum_tree<SingleTree>(d_items, n_items, total_chunks, d_counter, n_max, precision, tune,
+                                                  gstack, gstack_warps, span, s);
+}
+
 template <class R>
 static cudaError_t launch_lane_t(const ItemDev *d_items, int n_items, long long total_chunks,
                                  unsigned long long *d_counter, unsigned long long *span, cudaStream_t s) {
@@ -1947,6 +2702,7 @@ static cudaError_t launch_lane_t(const ItemDev *d_items, int n_items, long long 
     long long grid = (long long)sms * per_sm;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
+    prefer_shared(lane_kernel<R>);
     lane_kernel<R><<<(unsigned)grid, 128, 0, s>>>(d_items, n_items, total_chunks, d_counter, span);
     return cudaGetLastError();
 }
@@ -1960,6 +2716,7 @@ cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chu
 
 cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out,
                           unsigned long long *d_counts, unsigned int *d_bad, cudaStream_t s) {
+    prefer_shared(reduce_kernel);
     reduce_kernel<<<total_shifts, 256, 0, s>>>(d_items, n_items, d_out, d_counts, d_bad);
     return cudaGetLastError();
 }
@@ -1970,6 +2727,7 @@ __global__ void store_item_kernel(ItemDev item, ItemDev *dst, unsigned long long
 }
 
 cudaError_t launch_store_item(const ItemDev &item, ItemDev *d_item, unsigned long long *d_counter, cudaStream_t s) {
+    prefer_shared(store_item_kernel);
     store_item_kernel<<<1, 1, 0, s>>>(item, d_item, d_counter);
     return cudaGetLastError();
 }
@@ -1991,24 +2749,25 @@ cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_
     return cudaGetLastError();
 }
 
-template <class R, int F, bool GS>
+template <class Tree, class R, int F, bool GS>
 static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
                                       cudaStream_t s) {
-    const size_t per_warp = warp_smem_bytes<R>(item.order, F, GS);
+    const size_t per_warp = Tree::template smem_bytes<R>(item.order, F, GS);
     if (per_warp > kSmemMax) return cudaErrorInvalidConfiguration;
     const int wpb = per_warp * 2 <= kSmemMax ? 2 : 1;
     size_t smem = per_warp * wpb;
-    cudaError_t e =
-        cudaFuncSetAttribute(integrand_kernel<R, F, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = integrand_kernel<Tree, R, F, GS>;
+    prefer_shared(kern);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     uint64_t blocks = (count + wpb - 1) / wpb;
     cx<R> *gstack = nullptr;
     if (GS) {  // check path: a bounded number of warps, each with its own slice of device memory
         if (blocks > 304) blocks = 304;
-        e = cudaMalloc(&gstack, blocks * wpb * gstack_entries<R>(item.order, F) * sizeof(cx<R>));
+        e = cudaMalloc(&gstack, blocks * wpb * Tree::template gstack_entries<R>(item.order, F) * sizeof(cx<R>));
         if (e != cudaSuccess) return e;
     }
-    integrand_kernel<R, F, GS><<<(unsigned)blocks, wpb * 32, smem, s>>>(item, count, d_u, d_out, item.order, gstack);
+    kern<<<(unsigned)blocks, wpb * 32, smem, s>>>(item, count, d_u, d_out, item.order, gstack);
     e = cudaGetLastError();
     if (GS) {
         cudaError_t e2 = cudaStreamSynchronize(s);
@@ -2018,30 +2777,37 @@ static cudaError_t launch_integrand_t(const ItemDev &item, uint64_t count, const
     return e;
 }
 
-template <class R, int F>
+template <class Tree, class R, int F>
 static cudaError_t launch_integrand_f(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
                                       cudaStream_t s) {
-    if (stack_in_global<R>(item.order, F)) return launch_integrand_t<R, F, true>(item, count, d_u, d_out, s);
-    return launch_integrand_t<R, F, false>(item, count, d_u, d_out, s);
+    if (stack_in_global<Tree, R>(item.order, F)) return launch_integrand_t<Tree, R, F, true>(item, count, d_u, d_out, s);
+    return launch_integrand_t<Tree, R, F, false>(item, count, d_u, d_out, s);
 }
 
-cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
-                             const Tuning &tune, cudaStream_t s) {
-    if (count == 0) return cudaSuccess;
+template <class Tree>
+static cudaError_t launch_integrand_tree(const ItemDev &item, uint64_t count, const double *d_u, double *d_out,
+                                         int precision, const Tuning &tune, cudaStream_t s) {
     if (precision == QQMC_PREC_FP64) {
         switch (tune.flat) {
-            case 2: return launch_integrand_f<double, 2>(item, count, d_u, d_out, s);
-            case 3: return launch_integrand_f<double, 3>(item, count, d_u, d_out, s);
-            case 4: return launch_integrand_f<double, 4>(item, count, d_u, d_out, s);
-            default: return launch_integrand_f<double, 5>(item, count, d_u, d_out, s);
+            case 2: return launch_integrand_f<Tree, double, 2>(item, count, d_u, d_out, s);
+            case 3: return launch_integrand_f<Tree, double, 3>(item, count, d_u, d_out, s);
+            case 4: return launch_integrand_f<Tree, double, 4>(item, count, d_u, d_out, s);
+            default: return launch_integrand_f<Tree, double, 5>(item, count, d_u, d_out, s);
         }
     }
     switch (tune.flat) {
-        case 2: return launch_integrand_f<float, 2>(item, count, d_u, d_out, s);
-        case 3: return launch_integrand_f<float, 3>(item, count, d_u, d_out, s);
-        case 4: return launch_integrand_f<float, 4>(item, count, d_u, d_out, s);
-        default: return launch_integrand_f<float, 5>(item, count, d_u, d_out, s);
+        case 2: return launch_integrand_f<Tree, float, 2>(item, count, d_u, d_out, s);
+        case 3: return launch_integrand_f<Tree, float, 3>(item, count, d_u, d_out, s);
+        case 4: return launch_integrand_f<Tree, float, 4>(item, count, d_u, d_out, s);
+        default: return launch_integrand_f<Tree, float, 5>(item, count, d_u, d_out, s);
     }
+}
+
+cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
+                             const Tuning &tune, bool pairs, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    return pairs ? launch_integrand_tree<PairTree>(item, count, d_u, d_out, precision, tune, s)
+                 : launch_integrand_tree<SingleTree>(item, count, d_u, d_out, precision, tune, s);
 }
 
 }  // namespace qqmc

@@ -119,11 +119,12 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
         return set_error(QQMC_E_INVAL, "points outside the problem's lattice (order > its dimension or index >= N)");
     it.proj = P->d_proj[order];
     it.proj_cells = P->proj_cells[order];
-    Tuning tu = get_tuning(precision, order);
+    const bool pairs = use_pairs(*P, precision);
+    Tuning tu = get_tuning(precision, order, pairs);
     it.flat = tu.flat;
     if (it.flat < 2 && order > 4) it.flat = 2;
     if (tu.flat < 2) tu.flat = tu.flat_min = 2;
-    if (!(it.flat == 1 && order <= kLaneMaxOrder) && !detsum_stack_fits_shared(order, precision, tu))
+    if (!(it.flat == 1 && order <= kLaneMaxOrder) && !detsum_stack_fits_shared(order, precision, tu, pairs))
         return set_error(QQMC_E_INVAL,
                          "qqmc_integrate_noalloc: this order's FP64 tree stack needs device memory; use the mixed "
                          "precision or qqmc_integrate");
@@ -139,8 +140,8 @@ extern "C" int qqmc_integrate_noalloc(const qqmc_problem *pr, int order, uint64_
         if (it.flat == 1 && order <= kLaneMaxOrder)
             e = launch_lane(d_item, 1, (long long)(cps * n_shifts), d_counter, precision, nullptr, s);
         else
-            e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, nullptr, 0,
-                              nullptr, s);
+            e = launch_detsum(d_item, 1, (long long)(cps * n_shifts), d_counter, order, precision, tu, pairs, nullptr,
+                              0, nullptr, s);
     }
     if (e == cudaSuccess) e = launch_reduce(d_item, 1, n_shifts, d_sums, counts, nullptr, s);
     if (e != cudaSuccess) return cuda_error(e, "qqmc_integrate_noalloc");

@@ -34,7 +34,14 @@ struct Problem {
     uint32_t *d_lat_z = nullptr;
     int lat_m = 0;       // log2 N, plus 64 when the baker's transform follows the shift
     int lat_dims = 0;
+    int elimination = QQMC_ELIM_AUTO;  // Keldysh-sum tree: QQMC_ELIM_* (qqmc_set_elimination)
 };
+
+// Whether a problem's Keldysh sums run on the pair-block tree (else the
+// single-vertex tree), for the given precision: QQMC_ELIM_AUTO picks pairs when
+// the vertex diagonal dv = g^<(0) - i alpha is small against the scale of the
+// Green function at tau = 0, max(|g^<(0)|, |g^>(0)|) with g^>(0) = g^<(0) - i.
+bool use_pairs(const Problem &P, int precision);
 
 // One item as the device sees it.
 struct ItemDev {
@@ -82,24 +89,25 @@ int launch_gf_table(const Problem &pr, cudaStream_t s);
 int launch_lead_table(Problem &pr, cudaStream_t s, double *zero);
 // span (may be null): [earliest warp start, latest warp exit] of the launch in device-clock ns,
 // merged with atomicMin / atomicMax (the caller initialises it to [~0, 0]).
+// pairs: the pair-block tree, else the single-vertex tree (every item of a launch uses one tree).
 cudaError_t launch_detsum(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
-                          int n_max, int precision, const Tuning &tune, void *gstack, long long gstack_warps,
-                          unsigned long long *span, cudaStream_t s);
+                          int n_max, int precision, const Tuning &tune, bool pairs, void *gstack,
+                          long long gstack_warps, unsigned long long *span, cudaStream_t s);
 // Warps (and bytes per warp) of device memory the determinant launch needs for
 // its tree stack; 0 when the stack fits in shared memory.
-long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, size_t *bytes_per_warp);
+long long detsum_gstack_warps(int n_max, int precision, const Tuning &tune, bool pairs, size_t *bytes_per_warp);
 void set_stack_policy(int precision, int min_order);
-bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune);
+bool detsum_stack_fits_shared(int n_max, int precision, const Tuning &tune, bool pairs);
 cudaError_t launch_lane(const ItemDev *d_items, int n_items, long long total_chunks, unsigned long long *d_counter,
                         int precision, unsigned long long *span, cudaStream_t s);
 constexpr int kLaneMaxOrder = 4;  // orders that may run one point per lane
-// Bits of the leaf index of an order's Keldysh tree (a_2, then two per
-// depth-first pair level); work units may fix a prefix of them.
-int tree_leaf_bits(int order);
+// Bits of the leaf index of an order's Keldysh tree (single-vertex tree: one
+// per depth-first level; pair tree: a_2, then two per depth-first pair level);
+// work units may fix a prefix of them.
+int tree_leaf_bits(int order, bool pairs);
 // d_bad (may be null): per shift, the work units whose partial sum was not finite.
 cudaError_t launch_reduce(const ItemDev *d_items, int n_items, int total_shifts, double *d_out, unsigned long long *d_counts,
                           unsigned int *d_bad, cudaStream_t s);
-size_t detsum_smem_bytes(int n_max, int precision, const Tuning &tune);
 // One thread writes the item descriptor (a kernel argument) to d_item and zeroes the work counter.
 cudaError_t launch_store_item(const ItemDev &item, ItemDev *d_item, unsigned long long *d_counter, cudaStream_t s);
 cudaError_t launch_sobol(int order, uint64_t first, uint64_t count, const uint32_t *d_shift, uint32_t *d_out,
@@ -108,8 +116,9 @@ cudaError_t launch_warp(int order, uint64_t first, uint64_t count, const uint32_
                         double *d_u, double *d_w, int32_t *d_inside, const uint32_t *d_lat_z, int lat_m,
                         cudaStream_t s);
 cudaError_t launch_integrand(const ItemDev &item, uint64_t count, const double *d_u, double *d_out, int precision,
-                             const Tuning &tune, cudaStream_t s);
-Tuning get_tuning(int precision, int order);
+                             const Tuning &tune, bool pairs, cudaStream_t s);
+// Launch shape of an order's determinant kernel, per precision and tree.
+Tuning get_tuning(int precision, int order, bool pairs);
 bool valid_params(const qqmc_params *p, std::string &why);
 double order0_value(const Problem &pr);
 

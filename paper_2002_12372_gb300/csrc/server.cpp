@@ -7,7 +7,8 @@
 // the newly admitted requests into ONE batched plan (all their orders share a
 // persistent kernel launch) on its own stream; rounds overlap on the device:
 // a request that arrives while earlier batches run is admitted as soon as
-// memory frees up and its kernel starts as SMs drain.  Completed batches are
+// memory frees up and its kernels start as SMs drain (rounds with less work on
+// higher-priority streams, see round_priority).  Completed batches are
 // detected with events, their results finalised per request, and their memory
 // returned to the budget.
 #include <math.h>
@@ -51,6 +52,21 @@ struct Batch {
     uint64_t bytes = 0;
 };
 
+// Stream priority of an admission round: the less work (Keldysh determinants,
+// N K 2^n summed over the round's items), the higher the priority, so that a
+// short round's blocks are dispatched as a long round's persistent blocks retire,
+// ahead of that round's remaining kernels, instead of queueing behind all of them.
+int round_priority(const std::vector<qqmc_request> &rq) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+    double work = 1.0;
+    for (const auto &r : rq)
+        for (int n = 1; n <= r.n_max; ++n) work += (double)r.n_points * r.n_shifts * ldexp(1.0, n);
+    double x = (log2(work) - 20.0) / 10.0;  // 2^20 determinants and less: greatest; 2^30 and more: least
+    x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+    return greatest + (int)lround(x * (least - greatest));
+}
+
 uint64_t request_bytes(const qqmc_request &r) {
     uint64_t b = (uint64_t)(r.params.n_table / 2 + 1) * (32 + 16);
     uint64_t cps = (r.n_points + kChunk - 1) / kChunk;
@@ -68,6 +84,10 @@ struct qqmc_server {
     std::deque<uint64_t> queue;
     std::unordered_map<uint64_t, Req> reqs;
     std::vector<Batch> inflight;
+    // Finished rounds whose plans and problems wait to be freed: cudaFree waits for the whole
+    // device, so it runs only when no round is in flight (or at shutdown).
+    std::vector<Batch> retired;
+    void free_retired();
     uint64_t next_handle = 1;
     uint64_t next_batch = 1;
     uint64_t bytes_in_use = 0;
@@ -153,6 +173,14 @@ void qqmc_server::finish_batch(Batch &b) {
     cv.notify_all();
 }
 
+void qqmc_server::free_retired() {
+    for (Batch &b : retired) {
+        qqmc_plan_destroy(b.plan);
+        for (auto *p : b.problems) qqmc_destroy_problem(p);
+    }
+    retired.clear();
+}
+
 void qqmc_server::run() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
@@ -175,10 +203,16 @@ void qqmc_server::run() {
             } else {
                 finish_batch(b);
             }
-            qqmc_plan_destroy(b.plan);
-            for (auto *p : b.problems) qqmc_destroy_problem(p);
             cudaEventDestroy(b.done);
             cudaStreamDestroy(b.stream);
+            b.done = nullptr;
+            b.stream = nullptr;
+            lk.lock();
+            retired.push_back(b);
+        }
+        if (inflight.empty() && !retired.empty()) {
+            lk.unlock();
+            free_retired();
             lk.lock();
         }
         // 2. timeouts of queued requests
@@ -242,7 +276,8 @@ void qqmc_server::run() {
                 }
             }
             if (rc == QQMC_OK) rc = qqmc_plan_create(its.data(), (int)its.size(), opts.precision, &b.plan);
-            if (rc == QQMC_OK && cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess)
+            if (rc == QQMC_OK && cudaStreamCreateWithPriority(&b.stream, cudaStreamNonBlocking,
+                                                              round_priority(rq)) != cudaSuccess)
                 rc = set_error(QQMC_E_CUDA, "stream create");
             if (rc == QQMC_OK && cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess)
                 rc = set_error(QQMC_E_CUDA, "event create");
@@ -273,7 +308,12 @@ void qqmc_server::run() {
             cv.notify_all();
             continue;
         }
-        if (stop && inflight.empty()) break;
+        if (stop && inflight.empty()) {
+            lk.unlock();
+            free_retired();
+            lk.lock();
+            break;
+        }
         if (inflight.empty())
             cv.wait_for(lk, std::chrono::milliseconds(50));
         else

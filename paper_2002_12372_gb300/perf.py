@@ -1,12 +1,14 @@
 """Work accounting for the roofline of the determinant kernel.
 
-``flops_per_point(n, F)`` counts the real floating-point operations the
-kernel executes for one in-domain point of order n (complex FMA c -/+ a*b = 8,
-complex product = 6, complex reciprocal = 6, the accumulation of a leaf term =
-8), following the kernel's loops exactly: the root (vertices 1 and 2
-eliminated with their 2x2 pivot block, once per a_2), the depth-first tree of
-vertex pairs, the breadth-first pair levels below each leaf and the per-lane
-flat phase over the last F vertices.  ``w_naive`` is the cost of the plain form
+``flops_per_point(n, F, pairs)`` counts the real floating-point operations
+the kernel executes for one in-domain point of order n (complex FMA c -/+ a*b
+= 8, complex product = 6, complex reciprocal = 6, the accumulation of a leaf
+term = 8), following the kernel's loops exactly, for either Keldysh-sum tree:
+the single-vertex tree (level 0 with vertex 1 eliminated, a depth-first tree
+over a_2.., breadth-first levels below each leaf, the per-lane flat phase over
+the last F vertices) or the pair-block tree (a root per a_2 with vertices 1
+and 2 eliminated by their 2x2 pivot block, a depth-first tree of vertex pairs,
+breadth-first pair levels, the per-lane flat phase).  ``w_naive`` is the cost of the plain form
 (one LU per Keldysh configuration of M_up and of M_down), for an
 algorithm-independent "effective" rate.
 
@@ -72,19 +74,22 @@ def _root(n: int) -> float:
     return PIVOT + nb * 4 * (CMUL + CFMS + CMUL) + (2 * nb + 4 * (nb * nb - nb)) * 2 * CFMS
 
 
+NODE_PIVOTS = 4 * (PIVOT + 4 * CMUL)  # B^-1 and det B of a node's four children, once per node
+W_BINV = 2 * (CMUL + CFMA)  # (W0; W1) = B^-1 (e_p; e_q) for one column from a stored B^-1
+
+
 def _child_lanecol(S2: int) -> float:
-    """Depth-first pair step, one child of S2 rows (every entry formed)."""
-    return PIVOT + CMUL + S2 * W_COL + S2 * S2 * 2 * CFMS
+    """Depth-first pair step, one child of S2 rows (every entry formed), pivot data stored."""
+    return CMUL + S2 * W_BINV + S2 * S2 * 2 * CFMS
 
 
-def _child_general(S2: int) -> float:
-    """General pair step, per child: pivot, scaled pivot rows, the used entries."""
-    return PIVOT + 4 * CMUL + CMUL + S2 * 2 * (CMUL + CFMA) + S2 * (S2 - 1) * 2 * CFMS
+def _child_general(S2: int, stored_pivot: bool = False) -> float:
+    """General pair step, per child: pivot (unless stored), scaled pivot rows, the used entries."""
+    return (0 if stored_pivot else PIVOT + 4 * CMUL) + CMUL + S2 * W_BINV + S2 * (S2 - 1) * 2 * CFMS
 
 
-def flops_per_point(n: int, RF: int = 2) -> float:
-    """Real flops per in-domain point of order n with tuned flat depth RF, following
-    the pair-block tree: root (vertices 1, 2) per a_2, depth-first pair levels, then
+def _flops_pairs(n: int, RF: int) -> float:
+    """Pair-block tree: root (vertices 1, 2) per a_2, depth-first pair levels, then
     per leaf group the breadth-first pair levels and the per-lane flat phase."""
     fl = (n * (n + 1) // 2) * 12  # pair interpolation: 2 complex lerps + position arithmetic
     if n == 1:
@@ -95,8 +100,8 @@ def flops_per_point(n: int, RF: int = 2) -> float:
     fl += 2 * _root(n)
     for l in range(1, dfl + 1):  # level l is built 2 * 4^(l-1) * 4 times per point
         S2 = 2 * (Rr - 2 * l) + 2
-        per = _child_lanecol(S2) if S2 <= 32 else _child_general(S2)
-        fl += 2 * 4 ** l * per
+        per = _child_lanecol(S2) if S2 <= 32 else _child_general(S2, stored_pivot=True)
+        fl += 2 * 4 ** (l - 1) * (NODE_PIVOTS + 4 * per)
     B = _bfs_levels(Rleaf, RF)
     F = Rleaf - 2 * B
     nodes = 2 if g else 1
@@ -107,6 +112,60 @@ def flops_per_point(n: int, RF: int = 2) -> float:
     leaf += (nodes << F) * (_flat_term(F) + ACC)
     groups = 1 if g else 2 * 4 ** dfl
     return fl + groups * leaf
+
+
+TREE_LEAF = 5
+
+
+def _flat_lane_single(Rf: int) -> float:
+    """One lane resolving Rf vertices of a node along one choice path."""
+    if Rf == 0:
+        return 2 * CMUL + 2 + ACC
+    M = Rf + 1
+    fl = CRCP + CMUL + M * CMUL + (M * M - 2) * CFMS
+    for q in range(1, Rf):
+        p = q + 1
+        rows = 2 + (M - 1 - p)
+        fl += CRCP + CMUL + rows * CMUL + (rows * rows - 2) * CFMS
+    return fl + 2 * CMUL + 2 + ACC
+
+
+def _flops_single(n: int, RF: int) -> float:
+    """Single-vertex tree: level 0 (vertex 1 eliminated), the depth-first tree over a_2..,
+    the breadth-first levels below each leaf and the per-lane flat phase."""
+    R0 = n - 1
+    S0 = 2 * n
+    fl = 0.0
+    # pair interpolation: 2 complex lerps + position arithmetic
+    fl += (n * (n + 1) // 2) * 12
+    # level 0: one cfms per entry, the right factors M(1, .) / d once per block index
+    # (2 cmul each), one reciprocal
+    fl += S0 * S0 * CFMS + 2 * n * CMUL + CRCP
+    levels = R0 - TREE_LEAF if R0 > TREE_LEAF else 0
+    Rleaf = R0 - levels
+    # depth-first tree: level l -> l+1 computed 2^(l+1) times in the walk; children wider
+    # than a warp (S2 > 32) take the general step, which skips the never-read entries that
+    # join a row to its other copy (S2 of the S2^2)
+    for l in range(levels):
+        S2 = 2 * (R0 - l)
+        upd = S2 * (S2 - 1) if S2 > 32 else S2 * S2
+        fl += 2 ** (l + 1) * (S2 * CMUL + upd * CFMS + CRCP + CMUL)
+    # below each tree leaf: breadth-first levels (the general step, S2 (S2 - 1) updates),
+    # then the per-lane flat phase
+    B = Rleaf - RF if Rleaf > RF else 0
+    Rf = Rleaf - B
+    leaf = 0.0
+    for lb in range(B):
+        S2 = 2 * (Rleaf - lb)
+        leaf += 2 ** (lb + 1) * (CRCP + CMUL + S2 * CMUL + S2 * (S2 - 1) * CFMS)
+    leaf += 2 ** Rleaf * _flat_lane_single(Rf)
+    return fl + 2 ** levels * leaf
+
+
+def flops_per_point(n: int, RF: int = 2, pairs: bool = False) -> float:
+    """Real flops per in-domain point of order n with tuned flat depth RF, on the
+    single-vertex tree or (pairs) the pair-block tree."""
+    return _flops_pairs(n, RF) if pairs else _flops_single(n, RF)
 
 
 def w_naive(n: int) -> float:

@@ -33,6 +33,10 @@ QQMC_E_NONFINITE = -9
 QQMC_MAX_ORDER = 22
 QQMC_PREC_FP64 = 0
 QQMC_PREC_MIXED = 1
+QQMC_TUNE_PAIRS = 16
+QQMC_ELIM_AUTO = 0
+QQMC_ELIM_PAIRS = 1
+QQMC_ELIM_SINGLE = 2
 QQMC_OBS_CHARGE = 0
 QQMC_OBS_CURRENT = 1
 
@@ -46,6 +50,7 @@ EXPORTED = [
     "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola", "qqmc_set_projection",
     "qqmc_learn_projection", "qqmc_set_current_tables", "qqmc_problem_current_tables", "qqmc_set_lattice",
     "qqmc_lattice_cbc", "qqmc_set_stack_policy", "qqmc_plan_device_span", "qqmc_request_state",
+    "qqmc_set_elimination", "qqmc_elimination",
 ]
 
 
@@ -140,6 +145,8 @@ def load(path: str = LIB_PATH):
         "qqmc_problem_current_tables": [vp, dp, dp, dp],
         "qqmc_plan_device_span": [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)],
         "qqmc_request_state": [vp, ctypes.c_uint64],
+        "qqmc_set_elimination": [vp, ctypes.c_int],
+        "qqmc_elimination": [vp, ctypes.c_int],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -352,6 +359,18 @@ def qqmc_integrate_noalloc(pr: int, order: int, n_points: int, n_shifts: int, pr
                                          ctypes.c_void_p(d_shift_words), ctypes.c_void_p(d_sums),
                                          ctypes.c_void_p(d_counts or None), ctypes.c_void_p(stream or None)),
            "qqmc_integrate_noalloc")
+
+
+def qqmc_set_elimination(pr: int, mode: int) -> None:
+    """QQMC_ELIM_AUTO (default), QQMC_ELIM_PAIRS or QQMC_ELIM_SINGLE for this problem's Keldysh sums."""
+    _check(load().qqmc_set_elimination(ctypes.c_void_p(pr), mode), "qqmc_set_elimination")
+
+
+def qqmc_elimination(pr: int, precision: int) -> int:
+    """The elimination order the problem's sums use at this precision (QQMC_ELIM_PAIRS or _SINGLE)."""
+    rc = load().qqmc_elimination(ctypes.c_void_p(pr), precision)
+    _check(rc if rc < 0 else 0, "qqmc_elimination")
+    return rc
 
 
 def qqmc_set_tuning(precision: int, order: int, warps_per_block: int, flat_vertices: int) -> None:

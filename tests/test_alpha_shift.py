@@ -245,6 +245,59 @@ def test_integration_at_the_occupation_matches_oracle(Q, oracle, lane, off, curr
         autotune.reset()
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("ph", [False, True])
+@pytest.mark.parametrize("order,count", [(3, 32), (4, 24), (5, 16), (7, 8), (9, 4)])
+def test_single_vertex_tree_at_the_auto_threshold(Q, oracle, ph, order, count):
+    """QQMC_ELIM_AUTO keeps the single-vertex tree while |g^<(0) - i alpha| is at least 0.01
+    (FP64) or 0.25 (mixed) of max(|g^<(0)|, |g^>(0)|).  Just above those thresholds, where its
+    first pivot (and at particle-hole symmetry every odd pivot) is that small, it still holds the
+    bars: synthetic tables, and the wide-band dot at eps_d = 0."""
+    from paper_2002_12372_gb300 import workloads as W
+    T, L = 10.0, 4096
+    if ph:
+        gl, gg, g0 = oracle.gf_tables(1.0, 0.0, T, L)
+    else:
+        gl, gg, g0, _ = W.synthetic_tables(950 + order, L, T)
+    u = W.ordered_times(960 + order, count, order, T)
+    scale = max(abs(g0), abs(g0 - 1j))
+    for prec, frac, rel in [(Q.QQMC_PREC_FP64, 0.01, 1e-12), (Q.QQMC_PREC_MIXED, 0.25, 2.0 ** -20)]:
+        alpha = float(np.imag(g0)) + 1.02 * frac * scale
+        pr = Q.qqmc_create_problem_tables(Q.make_params(t_max=T, n_table=L, alpha=alpha), gl, gg, g0)
+        try:
+            assert Q.qqmc_elimination(pr, prec) == Q.QQMC_ELIM_SINGLE
+            got = Q.qqmc_integrand(pr, order, u, prec)
+        finally:
+            Q.qqmc_destroy_problem(pr)
+        ref, sc, had = oracle.integrand(order, u, T, (gl, gg, g0), T, return_abs=True, return_had=True,
+                                        alpha=alpha)
+        floor = 1e-14 if prec == Q.QQMC_PREC_FP64 else 2.0 ** -20
+        dev = np.abs(got - ref)
+        assert np.all(np.isfinite(got))
+        assert np.all(dev <= rel * sc + floor * had), (prec, np.max(dev / sc))
+
+
+@pytest.mark.gpu
+def test_auto_elimination_picks_pairs_near_the_occupation(Q):
+    """The auto rule itself: pairs within the thresholds, single vertices outside them."""
+    from paper_2002_12372_gb300 import workloads as W
+    gl, gg, g0, _ = W.synthetic_tables(5, 256, 10.0)
+    scale = max(abs(g0), abs(g0 - 1j))
+    for prec, frac in [(Q.QQMC_PREC_FP64, 0.01), (Q.QQMC_PREC_MIXED, 0.25)]:
+        for off, want in [(0.0, Q.QQMC_ELIM_PAIRS), (0.98 * frac * scale, Q.QQMC_ELIM_PAIRS),
+                          (-0.98 * frac * scale, Q.QQMC_ELIM_PAIRS), (1.02 * frac * scale, Q.QQMC_ELIM_SINGLE)]:
+            pr = Q.qqmc_create_problem_tables(
+                Q.make_params(t_max=10.0, n_table=256, alpha=float(np.imag(g0)) + off), gl, gg, g0)
+            try:
+                assert Q.qqmc_elimination(pr, prec) == want, (prec, off)
+                Q.qqmc_set_elimination(pr, Q.QQMC_ELIM_SINGLE)
+                assert Q.qqmc_elimination(pr, prec) == Q.QQMC_ELIM_SINGLE
+                Q.qqmc_set_elimination(pr, Q.QQMC_ELIM_PAIRS)
+                assert Q.qqmc_elimination(pr, prec) == Q.QQMC_ELIM_PAIRS
+            finally:
+                Q.qqmc_destroy_problem(pr)
+
+
 # -------------------------------------------------- the oracle's rounding scale ---
 
 def test_hadamard_scale_bounds_every_keldysh_term(oracle):

@@ -35,10 +35,16 @@ def W():
     return workloads
 
 
-def _problem(Q, W, seed=7, T=10.0, L=4096, tau=1.0):
+def _problem(Q, W, seed=7, T=10.0, L=4096, tau=1.0, elim=0):
+    """elim: the Keldysh-sum tree (QQMC_ELIM_AUTO = 0, _PAIRS = 1, _SINGLE = 2)."""
     gl, gg, g0, _ = W.synthetic_tables(seed, L, T)
     p = Q.make_params(t_max=T, tau=tau, n_table=L)
-    return Q.qqmc_create_problem_tables(p, gl, gg, g0), (gl, gg, g0)
+    pr = Q.qqmc_create_problem_tables(p, gl, gg, g0)
+    Q.qqmc_set_elimination(pr, elim)
+    return pr, (gl, gg, g0)
+
+
+TREES = [1, 2]  # both Keldysh-sum trees: vertex pairs, single vertices
 
 
 # ------------------------------------------------------------------ points ---
@@ -70,10 +76,11 @@ def test_warp_points_match_oracle(Q, W, oracle, order, tau, t):
 
 # -------------------------------------------------------------- integrand ---
 
+@pytest.mark.parametrize("elim", TREES)
 @pytest.mark.parametrize("order,count", [(1, 64), (2, 64), (3, 64), (5, 48), (6, 32), (8, 16), (10, 6), (12, 2)])
-def test_integrand_fp64_matches_oracle(Q, W, oracle, order, count):
+def test_integrand_fp64_matches_oracle(Q, W, oracle, order, count, elim):
     T = 10.0
-    pr, tabs = _problem(Q, W, seed=100 + order, T=T)
+    pr, tabs = _problem(Q, W, seed=100 + order, T=T, elim=elim)
     try:
         u = W.ordered_times(200 + order, count, order, T)
         gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_FP64)
@@ -83,11 +90,12 @@ def test_integrand_fp64_matches_oracle(Q, W, oracle, order, count):
     assert np.all(np.abs(gpu - ref) <= 1e-12 * scale), np.max(np.abs(gpu - ref) / scale)
 
 
+@pytest.mark.parametrize("elim", TREES)
 @pytest.mark.parametrize("order,count", [(2, 64), (5, 32), (8, 12), (10, 6)])
-def test_integrand_mixed_within_fp32_bound(Q, W, oracle, order, count):
+def test_integrand_mixed_within_fp32_bound(Q, W, oracle, order, count, elim):
     """FP32 Schur updates: deviation bounded by 2^-20 (~1e-6) of the Keldysh-sum scale."""
     T = 10.0
-    pr, tabs = _problem(Q, W, seed=300 + order, T=T)
+    pr, tabs = _problem(Q, W, seed=300 + order, T=T, elim=elim)
     try:
         u = W.ordered_times(400 + order, count, order, T)
         gpu = Q.qqmc_integrand(pr, order, u, Q.QQMC_PREC_MIXED)
@@ -99,11 +107,12 @@ def test_integrand_mixed_within_fp32_bound(Q, W, oracle, order, count):
 
 # ------------------------------------------------------------- integration ---
 
+@pytest.mark.parametrize("elim", TREES)
 @pytest.mark.parametrize("order,N,K", [(1, 4096, 4), (2, 1000, 3), (3, 2049, 3), (4, 4096, 2), (6, 517, 2),
                                        (8, 97, 2), (1, 1, 1), (2, 31, 2), (3, 33, 2)])
-def test_integration_fp64_matches_oracle(Q, W, oracle, order, N, K):
+def test_integration_fp64_matches_oracle(Q, W, oracle, order, N, K, elim):
     T = 10.0
-    pr, tabs = _problem(Q, W, seed=order, T=T)
+    pr, tabs = _problem(Q, W, seed=order, T=T, elim=elim)
     sw = W.shift_words(1000 + order, K, order)
     try:
         res, S = Q.qqmc_integrate(pr, order, N, K, Q.QQMC_PREC_FP64, sw)
