@@ -289,8 +289,9 @@ def run_ours(args, ws, rank, local, pg):
                      "traffic": _launch_traffic(args, slice_n),
                      "kernel": "detsum_kernel<%s,flat> (one launch per tuned flat depth)" % (
                          "double" if args.precision == "fp64" else "float"),
-                     "peak_source": "derived: 152 SMs x %d %s FMA lanes x 2 flops x 2070 MHz" % (
-                         perf.FP64_LANES if args.precision == "fp64" else perf.FP32_LANES, args.precision),
+                     "peak_source": "measured: %s FMA throughput of the register-resident microbenchmark "
+                                    "(qqmc_fma_peak, bench.py --config peaks) at 2070 MHz; %.4g TFLOP/s derived "
+                                    "from unit counts" % (args.precision, perf.derived_tflops(args.precision)),
                      "kernel_ms_per_step": k_s * 1e3 / args.steps},
         "clocks": clk,
     }
@@ -304,7 +305,7 @@ def run_ours(args, ws, rank, local, pg):
 # DRAM bytes (read + write) of the detsum launches of one default benchmark step (one launch per
 # tuned flat depth), from a 1-pass ncu capture of this exact command; per step, like the achieved
 # rate.  None whenever the determinant kernel has changed since the capture.
-MEASURED_LAUNCH_TRAFFIC = {"fp64": None, "mixed": None}
+MEASURED_LAUNCH_TRAFFIC = {"fp64": 2940000, "mixed": 1660000}
 
 
 def _launch_traffic(args, slice_n):
@@ -464,6 +465,31 @@ def run_current(args, local):
                        "precision": args.precision, "l2": "flushed (256 MiB write) between timed steps"},
             "table_build_s": table_s, "I_0": -4.0 * c0.real,
             "per_order": {r.order: {"I": r.q_mean, "err": r.q_err, "in_domain": r.n_in_domain} for r, _ in res}}
+
+
+def run_peaks(args, local):
+    """Measured FMA throughput of the FP64 and FP32 pipes (the roofline denominators of the
+    determinant kernels), with the SM clocks sampled while it runs."""
+    Q = _setup(args, local)
+    from paper_2002_12372_gb300 import perf
+    clocks = Clocks(local)
+    clocks.start()
+    runs = {"fp64": [], "fp32": []}
+    for _ in range(max(1, args.steps)):
+        runs["fp64"].append(Q.qqmc_fma_peak(Q.QQMC_PREC_FP64, 1.0))
+        runs["fp32"].append(Q.qqmc_fma_peak(Q.QQMC_PREC_MIXED, 1.0))
+    clk = clocks.stop()
+    out = {k: {"best_tflops": max(v), "runs": v} for k, v in runs.items()}
+    mhz = clk.get("sm_mhz")
+    for k in ("fp64", "fp32"):
+        derived = perf.derived_tflops("fp64" if k == "fp64" else "mixed", mhz or perf.SM_MAX_MHZ)
+        out[k]["derived_tflops_at_sampled_clock"] = derived
+        out[k]["fraction_of_derived"] = out[k]["best_tflops"] / derived
+    return {"metric": "fma_peak_tflops", "value": out["fp64"]["best_tflops"], "unit": "TFLOP/s (FP64 FMA)",
+            "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": True, "dtype": "f64",
+            "data": "register-resident FMA chains", "config": {"workload": "qqmc_fma_peak: 8 independent FMA chains "
+                                                                         "per thread, 64 warps per SM, ~1 s each"},
+            "peaks": out, "clocks": clk}
 
 
 def run_orders(args, local):
@@ -673,7 +699,8 @@ def main():
                     help="autotuner table (JSON keyed by GPU name); built-in defaults when absent")
     ap.add_argument("--slice-log2", type=int, default=16,
                     help="Sobol' indices per shift in one step (16: the benchmark batch; smaller for profiling)")
-    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving", "current", "lattice", "orders"],
+    ap.add_argument("--config", choices=["plain", "batched", "precision", "serving", "current", "lattice", "orders",
+                                         "peaks"],
                     default="plain",
                     help="plain: the benchmark workload; the others print their own study line")
     ap.add_argument("--precision-log2", type=int, default=22)
@@ -694,7 +721,7 @@ def main():
     if args.config != "plain":
         local = int(os.environ.get("LOCAL_RANK", "0"))
         fn = {"batched": run_batched, "precision": run_precision, "serving": run_serving,
-              "current": run_current, "lattice": run_lattice, "orders": run_orders}[args.config]
+              "current": run_current, "lattice": run_lattice, "orders": run_orders, "peaks": run_peaks}[args.config]
         print(json.dumps(fn(args, local)), flush=True)
         return
     ws, rank, local, pg = _dist()

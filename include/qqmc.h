@@ -469,6 +469,17 @@ int qqmc_cancel(qqmc_server *s, uint64_t handle);
 /* Waits for in-flight work, fails pending requests with E_CANCELLED, frees all. */
 int qqmc_server_destroy(qqmc_server *s);
 
+/*
+ * Measured FMA throughput of the CUDA cores (the paper has no counterpart; it
+ * is the denominator of the determinant kernels' roofline, which are bound by
+ * the FP64 or FP32 FMA pipes).  A register-resident kernel runs independent
+ * multiply-add chains on every resident warp of every SM; *tflops receives
+ * 2 x FMAs / second of the last launch, each launch lasting about
+ * seconds / 4 (0 < seconds <= 60).  precision: QQMC_PREC_FP64 (DFMA) or
+ * QQMC_PREC_MIXED (FFMA).  Blocking.  Errors: E_INVAL, E_CUDA.
+ */
+int qqmc_fma_peak(int precision, double seconds, double *tflops);
+
 /* Copy the calling thread's last error message (NUL-terminated, truncated). */
 int qqmc_last_error(char *buf, size_t len);
 

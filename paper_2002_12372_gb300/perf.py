@@ -14,8 +14,10 @@ algorithm-independent "effective" rate.
 
 Peaks of the GB300 CUDA cores (the path is not a dense contraction and does
 not use tensor cores): 152 SMs at up to 2070 MHz; per SM and clock 128 FP32
-FMA lanes and 2 FP64 FMA lanes (the FP64 rate measured by an FMA-chain
-microbenchmark on this part, 1.20 TFLOP/s at ~1.97 GHz, fixes the latter).
+FMA lanes and 2 FP64 FMA lanes.  The roofline divides by the FMA throughput
+measured on this part with the library's own register-resident microbenchmark
+(qqmc_fma_peak): 1.2558 TFLOP/s FP64 (99.8 % of the unit-count figure) and
+77.32 TFLOP/s FP32 (96 %).
 """
 from __future__ import annotations
 
@@ -25,9 +27,21 @@ FP32_LANES = 128
 FP64_LANES = 2
 
 
-def peak_tflops(precision: str, mhz: float = SM_MAX_MHZ) -> float:
+# Measured FMA throughput on GB300 (qqmc_fma_peak: register-resident FMA chains on 64 warps per SM,
+# best of three ~1 s runs, SM clock 2070 MHz throughout, no throttle reason), from
+#   python bench.py --config peaks --steps 3
+MEASURED_TFLOPS = {"fp64": 1.2558, "mixed": 77.32}
+
+
+def derived_tflops(precision: str, mhz: float = SM_MAX_MHZ) -> float:
+    """Unit count x clock: SMs x FMA lanes x 2 flops x clock."""
     lanes = FP64_LANES if precision == "fp64" else FP32_LANES
     return SMS * lanes * 2.0 * mhz * 1e6 / 1e12
+
+
+def peak_tflops(precision: str) -> float:
+    """The roofline denominator: the measured FMA throughput of the pipe that bounds the kernel."""
+    return MEASURED_TFLOPS["fp64" if precision == "fp64" else "mixed"]
 
 
 CFMS, CMUL, CRCP, ACC = 8, 6, 6, 8

@@ -50,7 +50,7 @@ EXPORTED = [
     "qqmc_integrate_noalloc", "qqmc_plan_chunk_sums", "qqmc_resum_parabola", "qqmc_set_projection",
     "qqmc_learn_projection", "qqmc_set_current_tables", "qqmc_problem_current_tables", "qqmc_set_lattice",
     "qqmc_lattice_cbc", "qqmc_set_stack_policy", "qqmc_plan_device_span", "qqmc_request_state",
-    "qqmc_set_elimination", "qqmc_elimination",
+    "qqmc_set_elimination", "qqmc_elimination", "qqmc_fma_peak",
 ]
 
 
@@ -147,6 +147,7 @@ def load(path: str = LIB_PATH):
         "qqmc_request_state": [vp, ctypes.c_uint64],
         "qqmc_set_elimination": [vp, ctypes.c_int],
         "qqmc_elimination": [vp, ctypes.c_int],
+        "qqmc_fma_peak": [ctypes.c_int, ctypes.c_double, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -371,6 +372,13 @@ def qqmc_elimination(pr: int, precision: int) -> int:
     rc = load().qqmc_elimination(ctypes.c_void_p(pr), precision)
     _check(rc if rc < 0 else 0, "qqmc_elimination")
     return rc
+
+
+def qqmc_fma_peak(precision: int, seconds: float = 1.0) -> float:
+    """Measured FMA throughput (TFLOP/s, 2 flops per FMA) of the FP64 or FP32 pipes."""
+    t = ctypes.c_double()
+    _check(load().qqmc_fma_peak(precision, seconds, ctypes.byref(t)), "qqmc_fma_peak")
+    return t.value
 
 
 def qqmc_set_tuning(precision: int, order: int, warps_per_block: int, flat_vertices: int) -> None:
