@@ -644,6 +644,17 @@ def learn_projection(n: int, M: int, seed: int, t: float, tau: float, tables, T:
     if ins.any():
         c = integrand(n, u[ins], t, tables, T)
         vals[ins] = w[ins] * np.abs(c) / M
+    return projection_cdf(x, vals, n_bins, lam, floor_frac, cells)
+
+
+def projection_cdf(x: np.ndarray, vals: np.ndarray, n_bins: int = 100, lam: float = 0.05,
+                   floor_frac: float = 1e-3, cells: int = 1024) -> np.ndarray:
+    """The projection step of the learned warp (App. F) for samples x [M, n] in [0, 1)^n with
+    values vals [M]: per dimension d, the histogram of vals over n_bins equal bins of x_d
+    (centres (l + 1/2) / n_bins), smoothed by the Gaussian kernel exp(-(z - w_l)^2 / lam^2)
+    normalised over the bin centres, evaluated at the centres z of `cells` equal cells, floored
+    at floor_frac x its maximum; returns the cumulative sums [n, cells + 1], 0 .. 1."""
+    n = x.shape[1]
     centers = (np.arange(n_bins) + 0.5) / n_bins
     z = (np.arange(cells) + 0.5) / cells
     K = np.exp(-((z[:, None] - centers[None, :]) ** 2) / lam ** 2)

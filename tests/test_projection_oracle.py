@@ -48,3 +48,28 @@ def test_learned_table_lowers_the_error_bar_and_keeps_the_mean(oracle):
         oracle.q_from_sums(oracle.estimate_proj(n, N, sh, T, 1.0, cdf, tabs, T)[0]).real)
     assert e1 < e0
     assert abs(m1 - m0) < 4 * np.hypot(e0, e1)
+
+
+@pytest.mark.parametrize("lam", [0.05, 0.1])
+def test_projection_of_a_separable_density_is_its_smoothed_marginal(oracle, lam):
+    """Samples on Sobol' points with the separable value g(x_1) g(x_2), g(x) = 1 + a cos(2 pi x):
+    the projection onto x_d is g (the other factor integrates to 1), and smoothing with the
+    kernel exp(-d^2 / lam^2) attenuates the cosine by exp(-pi^2 lam^2), so away from the edges
+    the learned CDF is z + a exp(-pi^2 lam^2) sin(2 pi z) / (2 pi) up to a constant offset.
+    A wrong kernel width, a half-bin shift of the centres or a dropped factor fails this."""
+    M, a = 2 ** 16, 0.8
+    V = oracle.sobol_direction_numbers(2)
+    x = oracle.sobol_points(2, 0, M, V).astype(np.float64) * 2.0 ** -32
+    g = lambda v: 1.0 + a * np.cos(2 * np.pi * v)
+    vals = g(x[:, 0]) * g(x[:, 1]) / M
+    cdf = oracle.projection_cdf(x, vals, n_bins=100, lam=lam, floor_frac=1e-3, cells=1024)
+    z = np.arange(1025) / 1024.0
+    want = z + a * np.exp(-(np.pi * lam) ** 2) * np.sin(2 * np.pi * z) / (2 * np.pi)
+    inner = (z > 3 * lam) & (z < 1 - 3 * lam)
+    for d in range(2):
+        dev = cdf[d, inner] - want[inner]
+        assert np.max(np.abs(dev - np.mean(dev))) < 1e-3, (d, np.max(np.abs(dev - np.mean(dev))))
+    # a plainly wrong width is detected at the same bar
+    wrong = z + a * np.exp(-(np.pi * 2 * lam) ** 2) * np.sin(2 * np.pi * z) / (2 * np.pi)
+    dev = cdf[0, inner] - wrong[inner]
+    assert np.max(np.abs(dev - np.mean(dev))) > 1e-3

@@ -58,3 +58,34 @@ def test_library_resummation_rejects_bad_arguments(Q):
         Q.qqmc_resum_parabola([1.0, 2.0], 1.0, 2.0)   # p must be negative
     with pytest.raises(Q.QQMCError):
         Q.qqmc_resum_parabola([0.0, 2.0], -1.0, 2.0, invert=True)
+
+
+def _atanh_sq_coeffs(N):
+    """c_m of atanh(sqrt W)^2 = sum_m c_m W^m from the Cauchy product of atanh x = sum_k x^(2k+1)/(2k+1):
+    c_m = sum_{j+k=m-1} 1 / ((2j+1)(2k+1))  (1, 2/3, 23/45, 44/105, ...)."""
+    return [0.0] + [sum(1.0 / ((2 * j + 1) * (2 * (m - 1 - j) + 1)) for j in range(m)) for m in range(1, N + 1)]
+
+
+@pytest.mark.parametrize("p,U", [(-1.0, 0.7), (-2.5, 3.0)])
+def test_oracle_parabola_map_expansion(oracle, p, U):
+    """F(U) = U re-expanded in W is U(W) = |p| atanh(sqrt W)^2 truncated at the input order: its
+    value at W(U) = tanh(sqrt(U/|p|))^2 is |p| sum_{m<=N} c_m W^m, and F(U) = U^2 gives the square
+    of that series, truncated."""
+    N = 8
+    c = np.array(_atanh_sq_coeffs(N)) * abs(p)
+    assert c[1] == pytest.approx(abs(p)) and c[2] == pytest.approx(2 * abs(p) / 3)
+    assert c[3] == pytest.approx(23 * abs(p) / 45) and c[4] == pytest.approx(44 * abs(p) / 105)
+    W = math.tanh(math.sqrt(U / abs(p))) ** 2
+    a1 = [0.0, 1.0] + [0.0] * (N - 1)
+    assert oracle.resum_parabola(a1, p, U) == pytest.approx(np.polynomial.polynomial.polyval(W, c), rel=1e-12)
+    a2 = [0.0, 0.0, 1.0] + [0.0] * (N - 2)
+    sq = np.polynomial.polynomial.polymul(c, c)[: N + 1]
+    assert oracle.resum_parabola(a2, p, U) == pytest.approx(np.polynomial.polynomial.polyval(W, sq), rel=1e-12)
+
+
+def test_oracle_parabola_map_inverts_the_transform(oracle):
+    """U(W(U)) = U: the resummed series of F(U) = U converges to U as the order grows (W < 1)."""
+    p, U = -1.0, 2.0
+    errs = [abs(oracle.resum_parabola([0.0, 1.0] + [0.0] * (N - 1), p, U) - U) for N in (4, 8, 16, 24)]
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:]))
+    assert errs[-1] < 0.02 * U
