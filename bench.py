@@ -364,6 +364,35 @@ def run_batched(args, local):
         sep += p1.timing()[1]
         p1.close()
     plan.close()
+    # where batching pays: many items that each leave most of the GPU idle (a served sweep's small
+    # requests): 3 dots x orders 4..10 x 2^12 points x 16 shifts, one batched launch against one
+    # plan per item
+    probs = [Q.qqmc_create_problem(Q.make_params(GAMMA, e, T_MAX, TAU, L_TABLE, SEED)) for e in EPS]
+    small = [(p, n, 16, 2 ** 12) for p in probs for n in range(4, 11)]
+    bplan = Q.Plan(small, prec)
+    for _ in range(2):
+        bplan.launch(stream.cuda_stream, use_graph=True)
+        bplan.results()
+    sm = []
+    for _ in range(max(1, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bplan.launch(stream.cuda_stream, use_graph=True)
+        e1.record(stream)
+        bplan.results()
+        sm.append(e0.elapsed_time(e1))
+    bplan.close()
+    small_sep = 0.0
+    for it in small:
+        p1 = Q.Plan([it], prec)
+        p1.launch(stream.cuda_stream)
+        p1.results()
+        p1.launch(stream.cuda_stream)
+        p1.results()
+        small_sep += p1.timing()[1]
+        p1.close()
+    for p in probs:
+        Q.qqmc_destroy_problem(p)
     Q.qqmc_destroy_problem(pr)
     t = statistics.median(ms) / 1e3
     return {"metric": "batched_integrand_evals_per_s", "value": pts / t, "unit": "evals/s", "n_gpus": 1,
@@ -372,6 +401,8 @@ def run_batched(args, local):
             "config": {"workload": "one persistent launch (CUDA graph) over orders 2..12, N_n = 2^max(14,24-n), "
                                    "16 shifts, Gamma=1, eps_d=0, t=10, tau=1, L=4096", "precision": args.precision},
             "keldysh_det_evals_per_s": dets / t, "separate_launches_ms": sep, "batched_ms": t * 1e3,
+            "small_items": {"items": len(small), "batched_ms": statistics.median(sm), "separate_launches_ms": small_sep,
+                            "workload": "3 dots (eps_d -1, 0, 1) x orders 4..10 x 2^12 points x 16 shifts"},
             "per_order": {r.order: {"q": r.q_mean, "err": r.q_err, "in_domain": r.n_in_domain} for r, _ in res}}
 
 
