@@ -228,7 +228,7 @@ def run_ours(args, ws, rank, local, pg):
             pts += r.n_points * r.n_shifts
             pts_in += r.n_in_domain
             dets += r.n_in_domain * 2.0 ** r.order
-            flops += r.n_in_domain * perf.flops_per_point(r.order, f, pairs)
+            flops += r.n_in_domain * perf.flops_per_point(r.order, f, pairs, args.precision)
             naive += r.n_in_domain * perf.w_naive(r.order)
     torch.cuda.synchronize()
     _barrier(pg)
@@ -450,7 +450,9 @@ def run_precision(args, local):
 
 def run_current(args, local):
     """Current I_n through the dot with semicircular leads under bias (the paper's finite-bias current
-    calculations): one plan over orders 1..10 with 2^log2 points x 10 shifts each."""
+    calculations): one plan over orders 1..10 with 2^log2 points x 10 shifts each, alpha at the
+    occupation of the tables' level, Im g^<(0) (the shift that cancels the Hartree term)."""
+    import numpy as np
     import torch
 
     from paper_2002_12372_gb300 import workloads as W
@@ -459,12 +461,19 @@ def run_current(args, local):
     c = W.CurrentConfig()
     prec = Q.QQMC_PREC_FP64 if args.precision == "fp64" else Q.QQMC_PREC_MIXED
     L = args.current_table
-    p = Q.make_params(c.gamma, c.E_d, c.t_max, c.tau, L, SEED, alpha=c.alpha, observable=Q.QQMC_OBS_CURRENT,
-                      half_bandwidth=c.half_bandwidth, bias=c.bias)
+
+    def params(alpha):
+        return Q.make_params(c.gamma, c.E_d, c.t_max, c.tau, L, SEED, alpha=alpha, observable=Q.QQMC_OBS_CURRENT,
+                             half_bandwidth=c.half_bandwidth, bias=c.bias)
+
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
-    pr = Q.qqmc_create_problem(p)
+    pr0 = Q.qqmc_create_problem(params(0.0))
     table_s = time.perf_counter() - t0
+    alpha = float(np.imag(Q.qqmc_problem_tables(pr0, L)[2]))  # the tables do not depend on alpha
+    Q.qqmc_destroy_problem(pr0)
+    pr = Q.qqmc_create_problem(params(alpha))
+    tree = "pairs" if Q.qqmc_elimination(pr, prec) == Q.QQMC_ELIM_PAIRS else "single"
     N = 2 ** args.current_log2
     plan = Q.Plan([(pr, n, c.n_shifts, N) for n in c.orders], prec)
     for _ in range(args.warmup):
@@ -489,10 +498,11 @@ def run_current(args, local):
     return {"metric": "current_integrand_evals_per_s", "value": pts / t, "unit": "evals/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": "current, semicircular leads D=%g, Gamma=%g, E_d=%g, alpha=%g, V=%g, t=%g, "
-                                   "tau=%g, L=%d, orders %d..%d, N=2^%d x %d shifts, one CUDA-graph launch"
-                                   % (c.half_bandwidth, c.gamma, c.E_d, c.alpha, c.bias, c.t_max, c.tau, L,
+            "config": {"workload": "current, semicircular leads D=%g, Gamma=%g, E_d=%g, alpha=Im g<(0)=%.6f, V=%g, "
+                                   "t=%g, tau=%g, L=%d, orders %d..%d, N=2^%d x %d shifts, one CUDA-graph launch"
+                                   % (c.half_bandwidth, c.gamma, c.E_d, alpha, c.bias, c.t_max, c.tau, L,
                                       c.orders[0], c.orders[-1], args.current_log2, c.n_shifts),
+                       "tree": tree,
                        "precision": args.precision, "l2": "flushed (256 MiB write) between timed steps"},
             "table_build_s": table_s, "I_0": -4.0 * c0.real,
             "per_order": {r.order: {"I": r.q_mean, "err": r.q_err, "in_domain": r.n_in_domain} for r, _ in res}}
@@ -542,7 +552,7 @@ def run_orders(args, local):
     rate = 0.7e12 if prec == Q.QQMC_PREC_FP64 else 15e12
     for n in range(args.orders_min, args.orders_max + 1):
         pairs, f = tree_shape(Q, pr, prec, n)
-        want = args.orders_seconds * rate / perf.flops_per_point(n, f, pairs) / 16
+        want = args.orders_seconds * rate / perf.flops_per_point(n, f, pairs, args.precision) / 16
         N = int(2 ** max(6, min(22, math.floor(math.log2(max(want, 1.0))))))
         plan = Q.Plan([(pr, n, 16, N)], prec)
         plan.launch(stream.cuda_stream)
@@ -555,7 +565,8 @@ def run_orders(args, local):
         rows[n] = {"N": N, "shifts": 16, "kernel_ms": km, "evals_per_s": N * 16 / secs,
                    "in_domain_evals_per_s": r.n_in_domain / secs,
                    "keldysh_det_evals_per_s": r.n_in_domain * 2.0 ** n / secs,
-                   "tflops": r.n_in_domain * perf.flops_per_point(n, f, pairs) / secs / 1e12, "flat": f,
+                   "tflops": r.n_in_domain * perf.flops_per_point(n, f, pairs, args.precision) / secs / 1e12,
+                   "flat": f,
                    "tree": "pairs" if pairs else "single"}
     Q.qqmc_destroy_problem(pr)
     n_head = min(max(10, args.orders_min), args.orders_max)

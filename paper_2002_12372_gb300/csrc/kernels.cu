@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "qqmc_internal.h"
 
@@ -557,6 +558,73 @@ __device__ __forceinline__ void flat_dispatch(int Rf, const cx<R> *E, cx<R> detD
     }
 }
 
+// Flat phase for the two choice paths that differ only in the last vertex:
+// `path` holds the Keldysh indices of the first F - 1 remaining vertices and
+// the lane carries both rows and columns of the last one (register indices F
+// and F + 1) through the first F - 1 eliminations, then closes each path with
+// its own leaf term.  Per path this shares all but the leaf, about a third of
+// flat_phase's flops and loads at F = 5; the entries joining the two copies
+// of the last vertex are never used and never built.  The terms equal
+// flat_phase's for the same paths, operation for operation.
+template <class R, int F>
+__device__ __forceinline__ void flat_pair(const cx<R> *E, cx<R> detD, int parity, int path, Acc<R> &acc_re,
+                                          Acc<R> &acc_im) {
+    static_assert(F >= 2, "the paired flat phase needs a vertex before the last");
+    constexpr int S = 2 * F + 2;
+    constexpr int M = F + 2;  // 2 copies, vertices 1 .. F-2, both indices of vertex F-1
+    auto used = [](int x, int y) { return x == y || !((x < 2 && y < 2) || (x >= F && y >= F)); };
+    int idx[M];
+    idx[0] = 0;
+    idx[1] = 1;
+#pragma unroll
+    for (int q = 1; q < F - 1; ++q) idx[q + 1] = 2 + 2 * q + ((path >> q) & 1);
+    idx[F] = 2 * F;
+    idx[F + 1] = 2 * F + 1;
+    const int p0 = 2 + (path & 1);
+    cx<R> piv = E[p0 * S + p0];
+    detD = cmul(detD, piv);
+    cx<R> ip = crcp(piv);
+    cx<R> m[M][M];
+    cx<R> prow[M];
+#pragma unroll
+    for (int y = 0; y < M; ++y) prow[y] = cmul(E[p0 * S + idx[y]], ip);
+#pragma unroll
+    for (int x = 0; x < M; ++x) {
+        cx<R> cf = E[idx[x] * S + p0];
+#pragma unroll
+        for (int y = 0; y < M; ++y)
+            if (used(x, y)) m[x][y] = cfms(E[idx[x] * S + idx[y]], cf, prow[y]);
+    }
+#pragma unroll
+    for (int q = 1; q < F - 1; ++q) {
+        const int p = q + 1;
+        cx<R> pv = m[p][p];
+        detD = cmul(detD, pv);
+        cx<R> iq = crcp(pv);
+#pragma unroll
+        for (int y = 0; y < M; ++y)
+            if (y < 2 || y > p) m[p][y] = cmul(m[p][y], iq);
+#pragma unroll
+        for (int x = 0; x < M; ++x) {
+            if (!(x < 2 || x > p)) continue;
+#pragma unroll
+            for (int y = 0; y < M; ++y) {
+                if (!(y < 2 || y > p) || !used(x, y)) continue;
+                m[x][y] = cfms(m[x][y], m[x][p], m[p][y]);
+            }
+        }
+    }
+    parity ^= __popc(path) & 1;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int L = F + c;
+        cx<R> term = leaf_term(m[0][0], m[1][1], m[0][L], m[L][0], m[1][L], m[L][1], m[L][L], detD);
+        if (parity ^ c) term = mk<R>(-term.re, -term.im);
+        acc_re.add(term.re);
+        acc_im.add(term.im);
+    }
+}
+
 // One cooperative elimination: child(ren) of S x S parent matrices.  Child j
 // of the new level comes from parent j >> 1 with Keldysh index a = j & 1 on the
 // parent's first remaining vertex (pivot row/column 2 + a).  The new matrices
@@ -878,6 +946,17 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         if (twin)  // the leaves' parent has 2 kTreeLeaf + 4 rows
             expand_both_t<R, kTreeLeaf + 1>(level_smem(levels - 1), level_smem(levels), ws.sib,
                                             ws.detD + levels - 1, ws.detD + levels, ws.detD + levels + 1, lane);
+        if constexpr (twin_leaves<R>() && RFMAX >= kTreeLeaf) {
+            // both leaves at once, flat on all kTreeLeaf vertices: half-warp h resolves leaf h,
+            // two choice paths per lane (the last vertex's two indices)
+            if (twin && B == 0) {
+                const int h = lane >> 4;
+                const cx<R> *E = h ? ws.sib : level_smem(levels);
+                flat_pair<R, kTreeLeaf>(E, ws.detD[levels + h], __popc(b + h) & 1, lane & 15, ar, ai);
+                __syncwarp();
+                continue;
+            }
+        }
 #pragma unroll 1
         for (int h = 0; h <= twin; ++h) {
             const int tparity = __popc(b + h) & 1;
@@ -1913,9 +1992,9 @@ __device__ __forceinline__ unsigned unit_flag(double a, double b, double c, doub
 // Hot-path kernel: persistent warps pull chunks of 32 Sobol' indices.
 // ----------------------------------------------------------------------------
 template <class Tree, class R, int RFMAX, bool GS>
-__global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
-                              unsigned long long *counter, int n_max, int rf_min, cx<R> *gstack,
-                              unsigned long long *span) {
+__device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, int n_items, long long total_chunks,
+                                            unsigned long long *counter, int n_max, int rf_min, cx<R> *gstack,
+                                            unsigned long long *span) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -2001,6 +2080,27 @@ __global__ void detsum_kernel(const ItemDev *__restrict__ items, int n_items, lo
     }
     if (span && lane == 0) atomicMax(span + 1, gtimer());
 }
+
+#define QQMC_DETSUM_PARAMS                                                                                   \
+    const ItemDev *__restrict__ items, int n_items, long long total_chunks, unsigned long long *counter,   \
+        int n_max, int rf_min, cx<R> *gstack, unsigned long long *span
+#define QQMC_DETSUM_ARGS items, n_items, total_chunks, counter, n_max, rf_min, gstack, span
+
+template <class Tree, class R, int RFMAX, bool GS>
+__global__ void detsum_kernel(QQMC_DETSUM_PARAMS) {
+    detsum_body<Tree, R, RFMAX, GS>(QQMC_DETSUM_ARGS);
+}
+
+// The single-vertex tree's FP32 flat-5 kernel (paired flat phase) with a
+// register cap: left alone the compiler hoists the leaf gathers into ~240
+// registers; at the cap the SM still holds the warps its shared memory allows.
+constexpr int kFlat5Regs = 144;
+template <class Tree, class R, int RFMAX, bool GS>
+__global__ void __maxnreg__(kFlat5Regs) detsum_kernel_capped(QQMC_DETSUM_PARAMS) {
+    detsum_body<Tree, R, RFMAX, GS>(QQMC_DETSUM_ARGS);
+}
+#undef QQMC_DETSUM_PARAMS
+#undef QQMC_DETSUM_ARGS
 
 // ----------------------------------------------------------------------------
 // One-point-per-lane kernel for small orders (items whose tuning asks for it):
@@ -2567,6 +2667,16 @@ static bool stack_in_global(int n_max, int rf_min) {
            n_max >= g_gs_min_order[sizeof(R) == 8 ? 0 : 1].load();
 }
 
+// The kernel of one (tree, precision, flat depth, stack) shape: the register-capped
+// instance for the single-vertex tree's FP32 flat 5, the plain one otherwise.
+template <class Tree, class R, int F, bool GS>
+static auto detsum_entry() {
+    if constexpr (std::is_same<Tree, SingleTree>::value && sizeof(R) == 4 && F == 5)
+        return detsum_kernel_capped<Tree, R, F, GS>;
+    else
+        return detsum_kernel<Tree, R, F, GS>;
+}
+
 template <class Tree, class R, int F, bool GS>
 static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long long total_chunks,
                                    unsigned long long *d_counter, int n_max, int wpb, int rf_min, void *gstack,
@@ -2576,7 +2686,7 @@ static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long lon
     if (per_warp > kSmemMax) return cudaErrorInvalidConfiguration;
     while (wpb > 1 && per_warp * wpb > kSmemMax) --wpb;
     size_t smem = per_warp * wpb;
-    auto kern = detsum_kernel<Tree, R, F, GS>;
+    auto kern = detsum_entry<Tree, R, F, GS>();
     prefer_shared(kern);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

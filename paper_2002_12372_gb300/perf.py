@@ -1,6 +1,6 @@
 """Work accounting for the roofline of the determinant kernel.
 
-``flops_per_point(n, F, pairs)`` counts the real floating-point operations
+``flops_per_point(n, F, pairs, precision)`` counts the real floating-point operations
 the kernel executes for one in-domain point of order n (complex FMA c -/+ a*b
 = 8, complex product = 6, complex reciprocal = 6, the accumulation of a leaf
 term = 8), following the kernel's loops exactly, for either Keldysh-sum tree:
@@ -144,9 +144,24 @@ def _flat_lane_single(Rf: int) -> float:
     return fl + 2 * CMUL + 2 + ACC
 
 
-def _flops_single(n: int, RF: int) -> float:
+def _flat_pair_single(Rf: int) -> float:
+    """One lane resolving Rf vertices of a node along the two choice paths that differ only
+    in the last vertex: both of its rows and columns ride through the first Rf - 1
+    eliminations (the entries joining its two copies, like those joining the measurement
+    copies, are skipped), then one leaf term per path."""
+    M = Rf + 2
+    fl = CRCP + CMUL + M * CMUL + (M * M - 4) * CFMS
+    for q in range(1, Rf - 1):
+        rows = M - q
+        fl += CRCP + CMUL + rows * CMUL + (rows * rows - 4) * CFMS
+    return fl + 2 * (LEAF_TERM + 2 + ACC)
+
+
+def _flops_single(n: int, RF: int, paired: bool = False) -> float:
     """Single-vertex tree: level 0 (vertex 1 eliminated), the depth-first tree over a_2..,
-    the breadth-first levels below each leaf and the per-lane flat phase."""
+    the breadth-first levels below each leaf and the per-lane flat phase.  paired: the
+    FP32 kernel's sibling leaves at flat depth 5, resolved together by the two half-warps
+    with two choice paths per lane."""
     R0 = n - 1
     S0 = 2 * n
     fl = 0.0
@@ -172,14 +187,19 @@ def _flops_single(n: int, RF: int) -> float:
     for lb in range(B):
         S2 = 2 * (Rleaf - lb)
         leaf += 2 ** (lb + 1) * (CRCP + CMUL + S2 * CMUL + S2 * (S2 - 1) * CFMS)
-    leaf += 2 ** Rleaf * _flat_lane_single(Rf)
+    if paired and levels >= 1 and B == 0 and Rf == TREE_LEAF:
+        leaf += 2 ** (Rleaf - 1) * _flat_pair_single(Rf)
+    else:
+        leaf += 2 ** Rleaf * _flat_lane_single(Rf)
     return fl + 2 ** levels * leaf
 
 
-def flops_per_point(n: int, RF: int = 2, pairs: bool = False) -> float:
+def flops_per_point(n: int, RF: int = 2, pairs: bool = False, precision: str = "fp64") -> float:
     """Real flops per in-domain point of order n with tuned flat depth RF, on the
-    single-vertex tree or (pairs) the pair-block tree."""
-    return _flops_pairs(n, RF) if pairs else _flops_single(n, RF)
+    single-vertex tree or (pairs) the pair-block tree, in the given precision's kernel."""
+    if pairs:
+        return _flops_pairs(n, RF)
+    return _flops_single(n, RF, paired=precision != "fp64")
 
 
 def w_naive(n: int) -> float:

@@ -91,9 +91,11 @@ def test_integrand_fp64_matches_oracle(Q, W, oracle, order, count, elim):
 
 
 @pytest.mark.parametrize("elim", TREES)
-@pytest.mark.parametrize("order,count", [(2, 64), (5, 32), (8, 12), (10, 6)])
+@pytest.mark.parametrize("order,count", [(2, 64), (5, 32), (6, 16), (7, 16), (8, 12), (10, 6), (12, 2)])
 def test_integrand_mixed_within_fp32_bound(Q, W, oracle, order, count, elim):
-    """FP32 Schur updates: deviation bounded by 2^-20 (~1e-6) of the Keldysh-sum scale."""
+    """FP32 Schur updates: deviation bounded by 2^-20 (~1e-6) of the Keldysh-sum scale.  With the
+    single-vertex tree, orders >= 7 resolve their sibling leaves in one paired flat phase (two
+    choice paths per lane), order 6 its lone leaf one path per lane."""
     T = 10.0
     pr, tabs = _problem(Q, W, seed=300 + order, T=T, elim=elim)
     try:

@@ -190,6 +190,77 @@ def test_integrand_symmetric_in_vertex_labels(oracle):
     assert abs(a - b) < 1e-14
 
 
+def _wick_brute(n, u, t, alpha, vals, meas, meas_col):
+    """App. E Eq. (integral_gf) at 30 digits, assembled point by point on the Keldysh contour:
+    g[(x,u,a),(x',u',a')] is the 2x2 matrix (g^T, g^<; g^>, g^Tbar)_{a a'} at u - u', with
+    g^T = g^> for u > u' (g^< otherwise) and g^Tbar the reverse.  Vertex diagonals are the
+    equal-time lesser value shifted by -i alpha; the measurement entry is not shifted.
+    vals(x, tau) -> (g^<, g^>) between site 0 and site x; meas: g^<_{0x}(0); meas_col: x of
+    the measurement column (0: charge, 1: current)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+
+    def g(A, B):
+        (xa, ua, aa), (xb, ub, ab) = A, B
+        lt, gt = vals(xb, ua - ub)
+        if (aa, ab) == (0, 1):
+            return lt
+        if (aa, ab) == (1, 0):
+            return gt
+        later = ua > ub
+        return (gt if later else lt) if aa == 0 else (lt if later else gt)
+
+    total = mp.mpc(0)
+    for conf in range(1 << n):
+        a = [(conf >> k) & 1 for k in range(n)]
+        U = [(0, float(u[k]), a[k]) for k in range(n)]
+        rows = [(0, t, 0)] + U
+        cols = [(meas_col, t, 1)] + U
+        up = mp.matrix(n + 1, n + 1)
+        for r in range(n + 1):
+            for c in range(n + 1):
+                if r == 0 and c == 0:
+                    up[r, c] = meas
+                elif r == c:
+                    up[r, c] = vals(0, 0.0)[0] - 1j * alpha
+                else:
+                    up[r, c] = g(rows[r], cols[c])
+        dn = mp.matrix(n, n)
+        for r in range(n):
+            for c in range(n):
+                dn[r, c] = vals(0, 0.0)[0] - 1j * alpha if r == c else g(U[r], U[c])
+        total += (-1) ** sum(a) * mp.det(up) * mp.det(dn)
+    return complex(mp.mpc(1j) ** n * total)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+@pytest.mark.parametrize("current", [False, True])
+def test_integrand_assembly_against_30_digit_wick_sum(oracle, n, current):
+    """The oracle's integrand against the Wick-determinant sum of App. E assembled independently
+    (contour points, 2x2 Keldysh blocks, mpmath determinants), on the same table values: charge
+    and current, alpha != 0, vertices in any time order, one later than t."""
+    t, T, L, alpha = 6.0, 12.0, 512, 0.37
+    tabs = oracle.gf_tables(1.0, 0.4, T, L)
+    # any tables serve for the dot-lead column: the assembly is a polynomial in the entries
+    other = oracle.gf_tables(0.6, -0.9, T, L)
+    col = (0.3 * other[0], -0.2j * other[1], 0.3 * other[2]) if current else None
+
+    def vals(x, tau):
+        if tau == 0.0 and x == 0:
+            return complex(tabs[2]), None
+        src = col if x == 1 else tabs
+        return complex(oracle.table_at(src[0], T, tau)[0]), complex(oracle.table_at(src[1], T, tau)[0])
+
+    meas = complex(col[2]) if current else complex(tabs[2])
+    rng = np.random.default_rng(40 + n + 10 * current)
+    pts = [rng.uniform(0, t, n) for _ in range(3)]
+    pts[0][-1] = t + 1.3  # a vertex after the measurement time
+    for u in pts:
+        got, ab = oracle.integrand(n, u, t, tabs, T, return_abs=True, alpha=alpha, col=col)
+        ref = _wick_brute(n, u, t, alpha, vals, meas, 1 if current else 0)
+        assert abs(got[0] - ref) <= 1e-13 * ab[0] + 1e-300, (u, got[0], ref)
+
+
 # ------------------------------------------------------------ warp & estimate ---
 
 @pytest.mark.parametrize("n,tau", [(1, 1.0), (2, 0.6), (3, 1.0), (4, 0.95), (3, 1.7)])
