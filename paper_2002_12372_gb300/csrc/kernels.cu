@@ -2093,10 +2093,20 @@ __global__ void detsum_kernel(QQMC_DETSUM_PARAMS) {
 
 // The single-vertex tree's FP32 flat-5 kernel (paired flat phase) with a
 // register cap: left alone the compiler hoists the leaf gathers into ~240
-// registers; at the cap the SM still holds the warps its shared memory allows.
+// registers.  128 registers (10 values spilled) with the stack in shared
+// memory: up to 16 resident warps, and measured 1 % faster than the
+// spill-free cap even where shared memory holds the SM to 14 warps (order 10).
+// With the split stack (orders >= 11) the tight cap spills 18 values and costs
+// 4-5 %, so there the 144-register instance runs unless 128 registers buy
+// more resident warps.
 constexpr int kFlat5Regs = 144;
+constexpr int kFlat5RegsTight = 128;
 template <class Tree, class R, int RFMAX, bool GS>
 __global__ void __maxnreg__(kFlat5Regs) detsum_kernel_capped(QQMC_DETSUM_PARAMS) {
+    detsum_body<Tree, R, RFMAX, GS>(QQMC_DETSUM_ARGS);
+}
+template <class Tree, class R, int RFMAX, bool GS>
+__global__ void __maxnreg__(kFlat5RegsTight) detsum_kernel_tight(QQMC_DETSUM_PARAMS) {
     detsum_body<Tree, R, RFMAX, GS>(QQMC_DETSUM_ARGS);
 }
 #undef QQMC_DETSUM_PARAMS
@@ -2667,14 +2677,41 @@ static bool stack_in_global(int n_max, int rf_min) {
            n_max >= g_gs_min_order[sizeof(R) == 8 ? 0 : 1].load();
 }
 
-// The kernel of one (tree, precision, flat depth, stack) shape: the register-capped
-// instance for the single-vertex tree's FP32 flat 5, the plain one otherwise.
+template <class Tree, class R, int F>
+constexpr bool flat5_capped() {
+    return std::is_same<Tree, SingleTree>::value && sizeof(R) == 4 && F == 5;
+}
+
+// The kernel of one (tree, precision, flat depth, stack) shape: for the
+// single-vertex tree's FP32 flat 5 a register-capped instance (above), the
+// plain one otherwise.  Sets the kernel's shared-memory attributes.
 template <class Tree, class R, int F, bool GS>
-static auto detsum_entry() {
-    if constexpr (std::is_same<Tree, SingleTree>::value && sizeof(R) == 4 && F == 5)
-        return detsum_kernel_capped<Tree, R, F, GS>;
-    else
-        return detsum_kernel<Tree, R, F, GS>;
+static cudaError_t detsum_entry(int wpb, size_t smem, void (**out)(const ItemDev *, int, long long,
+                                                                    unsigned long long *, int, int, cx<R> *,
+                                                                    unsigned long long *)) {
+    auto prepare = [&](auto k, int *per_sm) {
+        prefer_shared(k);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, wpb * 32, smem);
+        return e;
+    };
+    int per_sm = 0;
+    if constexpr (flat5_capped<Tree, R, F>() && !GS) {
+        *out = detsum_kernel_tight<Tree, R, F, GS>;
+        return prepare(detsum_kernel_tight<Tree, R, F, GS>, &per_sm);
+    } else if constexpr (flat5_capped<Tree, R, F>()) {
+        cudaError_t e = prepare(detsum_kernel_capped<Tree, R, F, GS>, &per_sm);
+        if (e != cudaSuccess) return e;
+        *out = detsum_kernel_capped<Tree, R, F, GS>;
+        int per_sm_tight = 0;
+        e = prepare(detsum_kernel_tight<Tree, R, F, GS>, &per_sm_tight);
+        if (e != cudaSuccess) return e;
+        if (per_sm_tight > per_sm) *out = detsum_kernel_tight<Tree, R, F, GS>;
+        return cudaSuccess;
+    } else {
+        *out = detsum_kernel<Tree, R, F, GS>;
+        return prepare(detsum_kernel<Tree, R, F, GS>, &per_sm);
+    }
 }
 
 template <class Tree, class R, int F, bool GS>
@@ -2686,9 +2723,9 @@ static cudaError_t launch_detsum_t(const ItemDev *d_items, int n_items, long lon
     if (per_warp > kSmemMax) return cudaErrorInvalidConfiguration;
     while (wpb > 1 && per_warp * wpb > kSmemMax) --wpb;
     size_t smem = per_warp * wpb;
-    auto kern = detsum_entry<Tree, R, F, GS>();
-    prefer_shared(kern);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void (*kern)(const ItemDev *, int, long long, unsigned long long *, int, int, cx<R> *,
+                 unsigned long long *) = nullptr;
+    cudaError_t e = detsum_entry<Tree, R, F, GS>(wpb, smem, &kern);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
