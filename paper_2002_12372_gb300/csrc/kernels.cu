@@ -227,6 +227,76 @@ __device__ __forceinline__ void interp_col(const typename TabT<R>::V *col, doubl
     cg = mk<R>(fmaR(fr, b.z, g * a.z), fmaR(fr, b.w, g * a.w));
 }
 
+// Vertex times as the kernels keep them, one 8-byte slot per vertex (u_0 = t
+// first).  FP64: the time u itself.  Mixed: the mesh position x = u / h split
+// into its integer part and an FP32 fraction, so that a pair's position
+// s = x_j - x_k + T / h takes integer and FP32 operations only (the FP64 pipe
+// runs at 1/64 of the FP32 rate on this part).  With h = 2T / (L - 1), T / h
+// is (L - 1) / 2 exactly: integer part (L - 1) / 2, fraction 0 or 1/2.  The
+// fraction carries 24 bits, so the interpolation weight is exact to ~1e-7,
+// the rounding of the FP32 blend itself.
+struct VP32 {
+    int k;
+    float f;
+};
+
+template <class R>
+__device__ __forceinline__ void store_time(double *slot, double u, double inv_h) {
+    if constexpr (sizeof(R) == 8) {
+        *slot = u;
+    } else {
+        const double x = u * inv_h;
+        const double kx = floor(x);
+        VP32 v;
+        v.k = (int)kx;
+        v.f = (float)(x - kx);
+        *reinterpret_cast<VP32 *>(slot) = v;
+    }
+}
+
+// Node index and weight of position K + phi (phi in (-1, 2)) clamped to [kmin, kmax].
+__device__ __forceinline__ int mesh_node(int K, float phi, int kmin, int kmax, float &fr) {
+    int k = K + (phi >= 1.0f ? 1 : 0) - (phi < 0.0f ? 1 : 0);
+    k = k < kmin ? kmin : (k > kmax ? kmax : k);
+    fr = phi + (float)(K - k);
+    return k;
+}
+
+// Pair values of vertices j < k (u_j > u_k) from the stored times.
+template <class R>
+__device__ __forceinline__ void interp_pair_u(const typename TabT<R>::V *tab, double inv_h, double s0, int L,
+                                              const double *u, int j, int k, cx<R> &gl, cx<R> &gg) {
+    if constexpr (sizeof(R) == 8) {
+        interp_pair<R>(tab, inv_h, s0, L, u[j] - u[k], gl, gg);
+    } else {
+        const VP32 a = *reinterpret_cast<const VP32 *>(u + j), b = *reinterpret_cast<const VP32 *>(u + k);
+        const int kmin = L / 2 - 1;
+        float fr;
+        const int q = mesh_node(a.k - b.k + (L - 1) / 2, (a.f - b.f) + ((L - 1) & 1 ? 0.5f : 0.0f), kmin, L - 2, fr);
+        const float g = 1.0f - fr;
+        const float4 lo = tab[q - kmin], hi = tab[q - kmin + 1];
+        gl = mk<R>(fmaf(fr, hi.x, g * lo.x), fmaf(fr, hi.y, g * lo.y));
+        gg = mk<R>(fmaf(fr, hi.z, g * lo.z), fmaf(fr, hi.w, g * lo.w));
+    }
+}
+
+// Measurement-column values of vertex k from the stored times (tau = u_k - t).
+template <class R>
+__device__ __forceinline__ void interp_col_u(const typename TabT<R>::V *col, double inv_h, double s0, int L,
+                                             const double *u, int k, cx<R> &cl, cx<R> &cg) {
+    if constexpr (sizeof(R) == 8) {
+        interp_col<R>(col, inv_h, s0, L, u[k] - u[0], cl, cg);
+    } else {
+        const VP32 a = *reinterpret_cast<const VP32 *>(u + k), b = *reinterpret_cast<const VP32 *>(u);
+        float fr;
+        const int q = mesh_node(a.k - b.k + (L - 1) / 2, (a.f - b.f) + ((L - 1) & 1 ? 0.5f : 0.0f), 0, L / 2 - 1, fr);
+        const float g = 1.0f - fr;
+        const float4 lo = col[q], hi = col[q + 1];
+        cl = mk<R>(fmaf(fr, hi.x, g * lo.x), fmaf(fr, hi.y, g * lo.y));
+        cg = mk<R>(fmaf(fr, hi.z, g * lo.z), fmaf(fr, hi.w, g * lo.w));
+    }
+}
+
 // ----------------------------------------------------------------------------
 // Complex helpers and the leaf formula shared by both Keldysh-sum trees.
 // ----------------------------------------------------------------------------
@@ -319,7 +389,7 @@ struct WarpSmem {
     cx<R> *bfs;     // breadth-first levels (all nodes of one level contiguous)
     cx<R> *bdet;    // det M_down prefix per breadth-first node, two levels (2 x 32)
     cx<R> *bip;     // pivot reciprocal per child of the level being built (32)
-    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t); device memory with the split stack
+    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t; store_time form); device memory with the split stack
     int gs_level;   // split stack: levels with S > gs_level in device memory
 };
 
@@ -821,13 +891,13 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         while ((k + 1) * k / 2 <= p) ++k;
         int j = p - k * (k - 1) / 2;
         cx<R> gl, gg;
-        interp_pair<R>(tab, inv_h, s0, L, u[j] - u[k], gl, gg);
+        interp_pair_u<R>(tab, inv_h, s0, L, u, j, k, gl, gg);
         const int ok = p - j + k - 1;  // vertex k's block: (k-1)(k+2)/2
         ws.P[ok + j] = gg;
         ws.Rr[ok + j] = gl;
         if (j == 0) {  // measurement column of vertex k: g^<(u_k - t), g^>(u_k - t) for the charge
             cx<R> c0 = nconj(gl), c1 = nconj(gg);
-            if (col) interp_col<R>(col, inv_h, s0, L, u[k] - u[0], c0, c1);
+            if (col) interp_col_u<R>(col, inv_h, s0, L, u, k, c0, c1);
             ws.Rr[ok + k] = c0;
             ws.P[ok + k] = c1;
         }
@@ -1167,7 +1237,7 @@ struct WarpSmem {
     cx<R> *bip;     // general pair step: B^-1 per child
     cx<R> *bdet;    // det M_down per breadth-first node, two levels of `half` nodes
     int half;
-    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t); device memory with the split stack
+    double *upt;    // [32][n_max+1] point times of the chunk (u_0 = t; store_time form); device memory with the split stack
     int gs_level;   // split stack: levels with S > gs_level in device memory
 };
 
@@ -1642,13 +1712,13 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         while ((k + 1) * k / 2 <= p) ++k;
         int j = p - k * (k - 1) / 2;
         cx<R> gl, gg;
-        interp_pair<R>(tab, inv_h, s0, L, u[j] - u[k], gl, gg);
+        interp_pair_u<R>(tab, inv_h, s0, L, u, j, k, gl, gg);
         const int ok = p - j + k - 1;  // vertex k's block: (k-1)(k+2)/2
         ws.P[ok + j] = gg;
         ws.Rr[ok + j] = gl;
         if (j == 0) {  // measurement column of vertex k: g^<(u_k - t), g^>(u_k - t) for the charge
             cx<R> c0 = nconj(gl), c1 = nconj(gg);
-            if (col) interp_col<R>(col, inv_h, s0, L, u[k] - u[0], c0, c1);
+            if (col) interp_col_u<R>(col, inv_h, s0, L, u, k, c0, c1);
             ws.Rr[ok + k] = c0;
             ws.P[ok + k] = c1;
         }
@@ -2024,17 +2094,18 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
         // point generation and warp (Sobol' integers are exact)
         bool inside = false;
         double w = 0.0;
+        const double inv_h = 1.0 / I.h;
         if (valid) {
             const uint64_t i = (uint64_t)(I.first_index + idx);
             double uprev = I.t, prod = 1.0;
-            ws.upt[lane * NU] = I.t;
+            store_time<R>(ws.upt + lane * NU, I.t, inv_h);
             double jt = 1.0;
             for (int m = 0; m < n; ++m) {
                 uint32_t y = point_word(I.lat_z, I.lat_m, m, i, I.shifts[k * n + m]);
                 double v, omx, jac;
                 point_gap<R>(I, m, y, v, omx, jac);
                 uprev = uprev - v;
-                ws.upt[lane * NU + 1 + m] = uprev;
+                store_time<R>(ws.upt + lane * NU + 1 + m, uprev, inv_h);
                 prod *= omx;
                 jt *= jac;
             }
@@ -2049,7 +2120,6 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
         const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
         const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
         const typename TabT<R>::V *tab = item_table<R>(I);
-        const double inv_h = 1.0 / I.h;
         const double s0 = I.T * inv_h;
         unsigned mm = mask;
         while (mm) {
@@ -2304,7 +2374,7 @@ __global__ void integrand_kernel(ItemDev I, uint64_t count, const double *u, dou
     const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
     const double inv_h = 1.0 / I.h;
     for (uint64_t q = wid; q < count; q += (uint64_t)gridDim.x * (blockDim.x >> 5)) {
-        if (lane <= n) ws.upt[lane] = lane == 0 ? I.t : u[q * n + lane - 1];
+        if (lane <= n) store_time<R>(ws.upt + lane, lane == 0 ? I.t : u[q * n + lane - 1], inv_h);
         __syncwarp();
         cx<double> s = Tree::template sum<R, RF, GS>(ws, ws.upt, n, n_max, d, dv, item_table<R>(I), item_col<R>(I),
                                                      inv_h, I.T * inv_h, I.L, RF, lane);
