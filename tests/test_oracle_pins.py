@@ -191,14 +191,14 @@ def test_integrand_symmetric_in_vertex_labels(oracle):
 
 
 def _wick_brute(n, u, t, alpha, vals, meas, meas_col):
-    """App. E Eq. (integral_gf) at 30 digits, assembled point by point on the Keldysh contour:
+    """App. E Eq. (integral_gf) at 50 digits, assembled point by point on the Keldysh contour:
     g[(x,u,a),(x',u',a')] is the 2x2 matrix (g^T, g^<; g^>, g^Tbar)_{a a'} at u - u', with
     g^T = g^> for u > u' (g^< otherwise) and g^Tbar the reverse.  Vertex diagonals are the
     equal-time lesser value shifted by -i alpha; the measurement entry is not shifted.
     vals(x, tau) -> (g^<, g^>) between site 0 and site x; meas: g^<_{0x}(0); meas_col: x of
     the measurement column (0: charge, 1: current)."""
     mp = pytest.importorskip("mpmath")
-    mp.mp.dps = 30
+    mp.mp.dps = 50
 
     def g(A, B):
         (xa, ua, aa), (xb, ub, ab) = A, B
@@ -235,7 +235,7 @@ def _wick_brute(n, u, t, alpha, vals, meas, meas_col):
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
 @pytest.mark.parametrize("current", [False, True])
-def test_integrand_assembly_against_30_digit_wick_sum(oracle, n, current):
+def test_integrand_assembly_against_50_digit_wick_sum(oracle, n, current):
     """The oracle's integrand against the Wick-determinant sum of App. E assembled independently
     (contour points, 2x2 Keldysh blocks, mpmath determinants), on the same table values: charge
     and current, alpha != 0, vertices in any time order, one later than t."""
