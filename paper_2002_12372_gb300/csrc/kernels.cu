@@ -754,14 +754,24 @@ __device__ __forceinline__ void expand_level(const cx<R> *__restrict__ in, int S
 // the child and a fixed row offset, so the scaled pivot-row entry of its
 // column stays in a register and the pivot-column entry of a row is a
 // broadcast load.  A step is latency-bound (a few hundred flops per warp), so
-// every load of the step is issued before the pivot's reciprocal is formed,
-// and the lane mapping needs no division.
+// every load of the step is issued at once and the lane mapping needs no
+// division.  FP64 (pivot_slots<R>()): a depth-first node's two pivot
+// reciprocals (for a = 0, 1) are formed once, when the node is built, by the
+// lanes that compute the pivots, and kept in the cross slots (2, 3) and (3, 2),
+// which join the first vertex's two copies and are never read as entries; a
+// step loads its reciprocal with the rest, and both children of a node share
+// it (one reciprocal per node instead of one per child: FP64 benchmark step
+// 1.5 % faster, results bit-identical).  FP32 forms the reciprocal in the step:
+// the two-lane branch at the end of the step measured 5-10 % slower there.
 //
 // Children of 2T = 12, 14 or 16 rows (the deep, frequent steps): lanes 0-15
 // take the even rows, lanes 16-31 the odd rows, column c2 = lane & 15.
+template <class R>
+__host__ __device__ constexpr bool pivot_slots() { return sizeof(R) == 8; }
+
 template <class R, int T>
 __device__ __forceinline__ void expand_one_t(const cx<R> *__restrict__ in, int a, cx<R> *__restrict__ out,
-                                             const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+                                             const cx<R> *detD_in, cx<R> *detD_out, int lane, bool rcp_child) {
     constexpr int S2 = 2 * T, S = S2 + 2;
     const int pr = 2 + a;
     const int c2 = lane & 15, rsub = lane >> 4;
@@ -781,12 +791,24 @@ __device__ __forceinline__ void expand_one_t(const cx<R> *__restrict__ in, int a
             cv[t] = in[r * S + pr];
         }
     }
-    const cx<R> ip = crcp(piv);
+    // the pivot's reciprocal: from its row's cross slot, or formed here
+    const cx<R> ip = pivot_slots<R>() ? in[pr * S + 5 - pr] : crcp(piv);
     if (lane == 0) *detD_out = cmul(*detD_in, piv);
     if (act) {
         const cx<R> w = cmul(prc, ip);
 #pragma unroll
-        for (int t = 0; t < T; ++t) out[(rsub + 2 * t) * S2 + c2] = cfms(ev[t], cv[t], w);
+        for (int t = 0; t < T; ++t) {
+            const cx<R> v = cfms(ev[t], cv[t], w);
+            if constexpr (pivot_slots<R>()) {
+                // row 2 + rsub of the child: its cross entry (2 + rsub, 3 - rsub) is never read as
+                // an entry; for an inner node it holds the reciprocal of the diagonal entry instead
+                if (t == 1 && rcp_child && c2 == 3 - rsub) continue;
+                out[(rsub + 2 * t) * S2 + c2] = v;
+                if (t == 1 && rcp_child && c2 == 2 + rsub) out[(2 + rsub) * S2 + 3 - rsub] = crcp(v);
+            } else {
+                out[(rsub + 2 * t) * S2 + c2] = v;
+            }
+        }
     }
     __syncwarp();
 }
@@ -818,7 +840,8 @@ __device__ __forceinline__ void expand_both_t(const cx<R> *__restrict__ in, cx<R
             cv1[t] = in[r * S + 3];
         }
     }
-    const cx<R> ip0 = crcp(piv0), ip1 = crcp(piv1);
+    const cx<R> ip0 = pivot_slots<R>() ? in[2 * S + 3] : crcp(piv0);  // the pivots' reciprocals
+    const cx<R> ip1 = pivot_slots<R>() ? in[3 * S + 2] : crcp(piv1);
     if (lane == 0) *detD_out0 = cmul(*detD_in, piv0);
     if (lane == 1) *detD_out1 = cmul(*detD_in, piv1);
     if (act) {
@@ -836,12 +859,12 @@ __device__ __forceinline__ void expand_both_t(const cx<R> *__restrict__ in, cx<R
 // rows in batches (eight in FP32, four in FP64) with the batch's loads issued first.
 template <class R>
 __device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
-                                                const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+                                                const cx<R> *detD_in, cx<R> *detD_out, int lane, bool rcp_child) {
     constexpr int NB = sizeof(R) == 4 ? 8 : 4;  // rows per batch (FP64: register budget)
     const int S2 = S - 2;
     const int pr = 2 + a;
     const cx<R> piv = in[pr * S + pr];
-    const cx<R> ip = crcp(piv);
+    const cx<R> ip = pivot_slots<R>() ? in[pr * S + 5 - pr] : crcp(piv);
     if (lane == 0) *detD_out = cmul(*detD_in, piv);
     if (lane < S2) {
         const int c = lane < 2 ? lane : lane + 2;
@@ -856,8 +879,15 @@ __device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, in
                 cv[t] = in[r * S + pr];
             }
 #pragma unroll
-            for (int t = 0; t < NB; ++t)
-                if (r0 + t < S2) out[(r0 + t) * S2 + lane] = cfms(ev[t], cv[t], w);
+            for (int t = 0; t < NB; ++t) {
+                const int r2 = r0 + t;
+                if (r2 >= S2) continue;
+                const cx<R> v = cfms(ev[t], cv[t], w);
+                const bool slot = pivot_slots<R>() && rcp_child && (r2 == 2 || r2 == 3);
+                if (slot && lane == (r2 ^ 1)) continue;  // the cross slot, written below
+                out[r2 * S2 + lane] = v;
+                if (slot && lane == r2) out[r2 * S2 + (r2 ^ 1)] = crcp(v);
+            }
         }
     }
     __syncwarp();
@@ -865,13 +895,21 @@ __device__ __forceinline__ void expand_one_wide(const cx<R> *__restrict__ in, in
 
 template <class R>
 __device__ __forceinline__ void expand_one(const cx<R> *__restrict__ in, int S, int a, cx<R> *__restrict__ out,
-                                           const cx<R> *detD_in, cx<R> *detD_out, int lane) {
+                                           const cx<R> *detD_in, cx<R> *detD_out, int lane, bool rcp_child) {
     switch (S - 2) {
-        case 12: expand_one_t<R, 6>(in, a, out, detD_in, detD_out, lane); break;
-        case 14: expand_one_t<R, 7>(in, a, out, detD_in, detD_out, lane); break;
-        case 16: expand_one_t<R, 8>(in, a, out, detD_in, detD_out, lane); break;
-        default: expand_one_wide<R>(in, S, a, out, detD_in, detD_out, lane); break;
+        case 12: expand_one_t<R, 6>(in, a, out, detD_in, detD_out, lane, rcp_child); break;
+        case 14: expand_one_t<R, 7>(in, a, out, detD_in, detD_out, lane, rcp_child); break;
+        case 16: expand_one_t<R, 8>(in, a, out, detD_in, detD_out, lane, rcp_child); break;
+        default: expand_one_wide<R>(in, S, a, out, detD_in, detD_out, lane, rcp_child); break;
     }
+}
+
+// The pivot reciprocals of a depth-first node built by the general step, which
+// leaves the cross slots unbuilt: 1 / E(2,2) into E(2,3), 1 / E(3,3) into E(3,2).
+template <class R>
+__device__ __forceinline__ void fill_pivot_slots(cx<R> *E, int S, int lane) {
+    if (lane < 2) E[(2 + lane) * S + 3 - lane] = crcp(E[(2 + lane) * S + 2 + lane]);
+    __syncwarp();
 }
 
 // Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
@@ -973,10 +1011,16 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
             const cx<R> b00 = diag ? dd : (up ? vP : lo0), b01 = diag ? dd : (up ? vR : lo0);
             const cx<R> b10 = diag ? dd : (up ? vP : lo1), b11 = diag ? dd : (up ? vR : lo1);
             cx<R> *o = level(0) + (2 * bx) * S0 + 2 * by;
-            o[0] = cfms(b00, left0, right0);
-            o[1] = cfms(b01, left0, right1);
-            o[S0] = cfms(b10, left1, right0);
-            o[S0 + 1] = cfms(b11, left1, right1);
+            const cx<R> o00 = cfms(b00, left0, right0), o11 = cfms(b11, left1, right1);
+            o[0] = o00;
+            o[S0 + 1] = o11;
+            if (pivot_slots<R>() && levels >= 1 && bx == 1 && by == 1) {  // pivot reciprocals (expand_one_t)
+                o[1] = crcp(o00);
+                o[S0] = crcp(o11);
+            } else {
+                o[1] = cfms(b01, left0, right1);
+                o[S0] = cfms(b10, left1, right0);
+            }
             by += sr;
             bx += sq;
             if (by >= n) {
@@ -1007,11 +1051,14 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         for (int l = from; l < levels - twin; ++l) {
             const int a = (b >> (levels - 1 - l)) & 1;
             const int S = 2 * (R0 - l) + 2;
-            if (S - 2 <= 32)
-                expand_one<R>(level(l), S, a, level(l + 1), ws.detD + l, ws.detD + l + 1, lane);
-            else
+            const bool inner = l + 1 < levels;  // the child is a depth-first node in turn, not a leaf
+            if (S - 2 <= 32) {
+                expand_one<R>(level(l), S, a, level(l + 1), ws.detD + l, ws.detD + l + 1, lane, inner);
+            } else {
                 expand_level<R>(level(l), S, 1, a, level(l + 1), ws.detD + l, ws.detD + l + 1, ws.wrow, ws.bip,
                                 lane);
+                if (pivot_slots<R>() && inner) fill_pivot_slots<R>(level(l + 1), S - 2, lane);
+            }
         }
         if (twin)  // the leaves' parent has 2 kTreeLeaf + 4 rows
             expand_both_t<R, kTreeLeaf + 1>(level_smem(levels - 1), level_smem(levels), ws.sib,
