@@ -9,7 +9,8 @@ the oracle at the warped points.
 
 ``test_mixed_precision_table`` (opt-in: QQMC_PRECISION_TABLE=1) prints the
 per-order table of the precision configuration, orders 6..12 on the first 2^16
-Sobol' indices of two shifts; the default suite checks order 10 on 2^12.
+Sobol' indices of two shifts; the default suite checks order 10 on 2^12 points and
+order 12 on 2^9.
 """
 import os
 from concurrent.futures import ThreadPoolExecutor
@@ -60,6 +61,14 @@ def _compare(Q, oracle, order, N, K, T=10.0, tau=1.0, L=4096):
 
 def test_mixed_at_order_10_within_its_bound_of_the_oracle(Q, oracle):
     Sm, S0, bound, S64 = _compare(Q, oracle, 10, 4096, 2)
+    assert np.all(np.abs(S64 - S0) <= 1e-10 * np.abs(S0))
+    assert np.all(np.abs(Sm - S0) <= bound), (np.abs(Sm - S0), bound)
+
+
+def test_mixed_at_order_12_within_its_bound_of_the_oracle(Q, oracle):
+    """Order 12: the split tree stack (the wide levels in device memory) and the mixed flat-5 kernel
+    with its spill-free register cap, sibling leaves resolved together."""
+    Sm, S0, bound, S64 = _compare(Q, oracle, 12, 512, 2)
     assert np.all(np.abs(S64 - S0) <= 1e-10 * np.abs(S0))
     assert np.all(np.abs(Sm - S0) <= bound), (np.abs(Sm - S0), bound)
 
