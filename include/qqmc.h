@@ -184,7 +184,7 @@ int qqmc_set_lattice(qqmc_problem *pr, int log2_n, const uint32_t *z, int dims, 
 /*
  * Where the Schur-tree stack of the determinant kernel lives: from order
  * min_order on (per precision) its wide top levels (matrices of more than
- * S_g rows, 14 <= S_g <= 20 chosen so that an SM holds 7 FP64 or 12
+ * S_g rows, 14 <= S_g <= 20 chosen so that an SM holds up to 9 FP64 or 12
  * mixed-precision warps) and the chunk's point times move from shared memory to a per-warp
  * slice of device memory allocated with each plan, so that high orders keep
  * more warps per SM.  Orders whose stack does not fit in shared memory at all

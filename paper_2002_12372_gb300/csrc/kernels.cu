@@ -478,13 +478,14 @@ __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_l
 
 // Split-stack boundary: the widest levels go to device memory, two rows at a
 // time, until a warp's shared memory lets the SM hold the warps its bound pipe
-// needs (FP64: 32 KB, 7 warps per SM with the point times in device memory,
-// measured 6 % faster on the benchmark step than 36 KB and 6 warps; mixed: 12).
+// needs (FP64: 24 KB, 9 warps per SM at order 10 with the point times in
+// device memory; re-tuned benchmark step 2326 ms, against 2332 at 28 KB, 2362
+// at 32 KB and 2511 at 36 KB with the point times in shared memory; mixed: 12).
 // Never the tree leaf (S = 12) or its parent (S = 14): the last depth-first
 // step and the breadth-first and flat phases work in shared memory only.
 template <class R>
 __host__ __device__ inline int gs_level_of(int n_max, int RF) {
-    const size_t budget = sizeof(R) == 8 ? 32 * 1024 : 18 * 1024;
+    const size_t budget = sizeof(R) == 8 ? 24 * 1024 : 18 * 1024;
     int lev = 20;
     while (lev > 2 * kTreeLeaf + 4 && warp_smem_bytes_at<R>(n_max, RF, lev) > budget) lev -= 2;
     return lev;
@@ -2779,7 +2780,7 @@ int tree_leaf_bits(int order, bool pairs) { return pairs ? PairTree::leaf_bits(o
 // The tree stack is split (wide top levels in device memory) where it does not
 // fit in shared memory, and from the order set by qqmc_set_stack_policy
 // (default, measured fastest on GB300 with the single-vertex tree: FP64 from
-// order 5, so that the point times leave shared memory and 7 warps fit an SM;
+// order 5, so that the point times leave shared memory and 9 warps fit an SM;
 // mixed from order 11, whose latency-bound steps want every level close): a
 // large shared-memory stack limits the warps per SM, while the wide levels are
 // built only a few times per point.
