@@ -355,6 +355,24 @@ __device__ __forceinline__ double warp_total(Acc<R> acc) {
     return (double)s + (double)c;
 }
 
+// The same butterfly within each half-warp: lanes 0-15 and 16-31 get their
+// own half's total.
+template <class R>
+__device__ __forceinline__ double half_total(Acc<R> acc) {
+    R s = acc.s, c = acc.c;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        R s2 = __shfl_xor_sync(FULL, s, o);
+        R c2 = __shfl_xor_sync(FULL, c, o);
+        R t, e;
+        int lo = ((threadIdx.x & 31) & o) == 0;
+        if (lo) two_sum_r<R>(s, s2, t, e); else two_sum_r<R>(s2, s, t, e);
+        s = t;
+        c = lo ? (c + c2) + e : (c2 + c) + e;
+    }
+    return (double)s + (double)c;
+}
+
 // ----------------------------------------------------------------------------
 // Single-vertex Schur tree (the fast path): one vertex per tree level with
 // its 1x1 pivot.  Pivots are the ratios of consecutive leading minors of
@@ -442,9 +460,19 @@ __host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
     size_t m = 0;
     for (int Rl = 0; Rl <= kTreeLeaf && Rl <= n_max - 1; ++Rl) {
         size_t e = bfs_entries(Rl, RF);
+        if (Rl < kTreeLeaf && 2 * bfs_entries(Rl, RF) > e) e = 2 * bfs_entries(Rl, RF);  // two points
         m = e > m ? e : m;
     }
     return m;
+}
+
+// The shared-memory part of the tree stack: the levels that live there, and at
+// least the two level-0 matrices of a two-point pass (orders <= kTreeLeaf + 1).
+__host__ __device__ inline size_t stack_smem_entries(int n_max, int gs_level) {
+    const size_t lv = gs_level ? stack_entries_split(n_max, false, gs_level) : stack_entries(n_max);
+    const size_t n2 = n_max < kTreeLeaf + 1 ? n_max : kTreeLeaf + 1;
+    const size_t two = 2 * (2 * n2) * (2 * n2);
+    return lv > two ? lv : two;
 }
 
 // The mixed-precision path builds sibling leaves in pairs (one depth-first step
@@ -452,6 +480,16 @@ __host__ __device__ inline size_t bfs_max_entries(int n_max, int RF) {
 // FP64 pipe, gains nothing from it and keeps the shared memory for warps.
 template <class R>
 __host__ __device__ constexpr bool twin_leaves() { return sizeof(R) == 4; }
+
+// Orders whose tree has no depth-first level and whose choice paths fill at
+// most half a warp run two points per warp (keldysh_sum2): orders <= kTreeLeaf
+// (at most 16 paths, one per lane), and in FP32 with a flat depth of
+// kTreeLeaf also order kTreeLeaf + 1 (the paired flat phase: 16 lanes, two
+// paths each).  Both points' breadth-first levels are built together.
+template <class R, int RFMAX>
+__host__ __device__ inline bool two_point_order(int n) {
+    return n <= kTreeLeaf || (n == kTreeLeaf + 1 && twin_leaves<R>() && RFMAX >= kTreeLeaf);
+}
 
 // the sibling leaf buffer, used when the tree has depth-first levels
 template <class R>
@@ -469,7 +507,7 @@ __host__ __device__ inline size_t pair_entries(int n_max) { return (size_t)n_max
 template <class R>
 __host__ __device__ inline size_t warp_smem_bytes_at(int n_max, int RF, int gs_level) {
     size_t wide = needs_wide_buffers(n_max, RF) ? (2 * (size_t)n_max > 64 ? 2 * (size_t)n_max : 64) + 64 + 32 : 0;
-    size_t c = (gs_level ? stack_entries_split(n_max, false, gs_level) : stack_entries(n_max)) + pair_entries(n_max) +
+    size_t c = stack_smem_entries(n_max, gs_level) + pair_entries(n_max) +
                n_max + 1 + sib_entries<R>(n_max) + 4 * (size_t)n_max + bfs_max_entries(n_max, RF) + wide;
     size_t bytes = (c * sizeof(cx<R>) + 15) & ~(size_t)15;
     if (!gs_level) bytes += 32 * (size_t)(n_max + 1) * sizeof(double);
@@ -515,7 +553,7 @@ __device__ __forceinline__ WarpSmem<R> carve(unsigned char *base, int n_max, int
     w.gstack = gstack;
     w.gs_level = gstack ? gs_level_of<R>(n_max, RF) : 0;
     w.stack = p;
-    p += gstack ? stack_entries_split(n_max, false, w.gs_level) : stack_entries(n_max);
+    p += stack_smem_entries(n_max, w.gs_level);
     const int npair = n_max * (n_max + 3) / 2;
     w.P = p;
     p += npair;
@@ -914,15 +952,15 @@ __device__ __forceinline__ void fill_pivot_slots(cx<R> *E, int S, int lane) {
     __syncwarp();
 }
 
-// Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
-// Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
-// i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
-// The depth-first walk covers the subtree `sub` of 2^split: the first `split`
-// tree levels follow the bits of sub (split <= levels); split = 0: whole tree.
-template <class R, int RFMAX, bool GS>
-__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
-                                  const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
-                                  double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
+// Steps 1 and 2 of the Keldysh sum of one point whose times are in u[0..n]:
+// its pair values into P and Rr, then level 0 of the tree into `out`
+// (2n x 2n).  slots: also form vertex 2's two pivot reciprocals in level 0's
+// cross slots (FP64 trees with depth-first levels, see expand_one_t).
+template <class R>
+__device__ __forceinline__ void build_level0(const WarpSmem<R> &ws, const double *u, int n, cx<R> d, cx<R> dv,
+                                             const typename TabT<R>::V *tab, const typename TabT<R>::V *col,
+                                             double inv_h, double s0, int L, cx<R> *__restrict__ out, bool slots,
+                                             int lane) {
     // 1. pair interpolation, 0 <= j < k <= n
     const int npairs = n * (n + 1) / 2;
     for (int p = lane; p < npairs; p += 32) {
@@ -950,23 +988,6 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
     // right = M(vertex 1, .) / d.
     const int R0 = n - 1;
     const int S0 = 2 * R0 + 2;
-    // tree levels: offsets in shared memory, or (split stack) in device memory for the wide ones.
-    // Level l holds S_l^2 = 4 (R0 + 1 - l)^2 entries, so the offset of level l within its part is
-    // 4 (Q(R0 + 1 - l0) - Q(R0 + 1 - l)), Q(x) = x(x+1)(2x+1)/6, l0 = the part's first level.
-    const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
-    int lg = 0;  // levels [0, lg) in device memory: S_l > gs_level
-    if (GS) {
-        lg = R0 + 1 - ws.gs_level / 2;
-        lg = lg < 0 ? 0 : (lg > levels + 1 ? levels + 1 : lg);
-    }
-    auto sq_sum = [](int x) { return x * (x + 1) * (2 * x + 1) / 6; };
-    const int qtop = sq_sum(R0 + 1), qsplit = sq_sum(R0 + 1 - lg);
-    auto level = [&](int l) -> cx<R> * {
-        const int ql = sq_sum(R0 + 1 - l);
-        return (GS && l < lg) ? ws.gstack + 4 * (qtop - ql) : ws.stack + 4 * (qsplit - ql);
-    };
-    // the leaf and its parent are always in shared memory (gs_level >= 14)
-    auto level_smem = [&](int l) -> cx<R> * { return ws.stack + 4 * (qsplit - sq_sum(R0 + 1 - l)); };
     const cx<R> id = crcp(dv);  // pivot of vertex 1
     {
         // Block row b's left factors M(., vertex 1) and block column b's right factors
@@ -1012,11 +1033,11 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
             const cx<R> dd = bx == 0 ? d : dv;
             const cx<R> b00 = diag ? dd : (up ? vP : lo0), b01 = diag ? dd : (up ? vR : lo0);
             const cx<R> b10 = diag ? dd : (up ? vP : lo1), b11 = diag ? dd : (up ? vR : lo1);
-            cx<R> *o = level(0) + (2 * bx) * S0 + 2 * by;
+            cx<R> *o = out + (2 * bx) * S0 + 2 * by;
             const cx<R> o00 = cfms(b00, left0, right0), o11 = cfms(b11, left1, right1);
             o[0] = o00;
             o[S0 + 1] = o11;
-            if (pivot_slots<R>() && levels >= 1 && bx == 1 && by == 1) {  // pivot reciprocals (expand_one_t)
+            if (slots && bx == 1 && by == 1) {  // pivot reciprocals (expand_one_t)
                 o[1] = crcp(o00);
                 o[S0] = crcp(o11);
             } else {
@@ -1031,6 +1052,37 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
             }
         }
     }
+}
+
+// Keldysh sum for one point whose times are in u[0..n] (u_0 = t).
+// Returns sum_{a_2..a_n} (-1)^{a_2+..+a_n} det M_down^2 (S00(0) - S00(1)),
+// i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
+// The depth-first walk covers the subtree `sub` of 2^split: the first `split`
+// tree levels follow the bits of sub (split <= levels); split = 0: whole tree.
+template <class R, int RFMAX, bool GS>
+__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+                                  const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
+                                  double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
+    // 1. pair interpolation, 0 <= j < k <= n, and 2. level 0 (build_level0)
+    const int R0 = n - 1;
+    // tree levels: offsets in shared memory, or (split stack) in device memory for the wide ones.
+    // Level l holds S_l^2 = 4 (R0 + 1 - l)^2 entries, so the offset of level l within its part is
+    // 4 (Q(R0 + 1 - l0) - Q(R0 + 1 - l)), Q(x) = x(x+1)(2x+1)/6, l0 = the part's first level.
+    const int levels = R0 > kTreeLeaf ? R0 - kTreeLeaf : 0;
+    int lg = 0;  // levels [0, lg) in device memory: S_l > gs_level
+    if (GS) {
+        lg = R0 + 1 - ws.gs_level / 2;
+        lg = lg < 0 ? 0 : (lg > levels + 1 ? levels + 1 : lg);
+    }
+    auto sq_sum = [](int x) { return x * (x + 1) * (2 * x + 1) / 6; };
+    const int qtop = sq_sum(R0 + 1), qsplit = sq_sum(R0 + 1 - lg);
+    auto level = [&](int l) -> cx<R> * {
+        const int ql = sq_sum(R0 + 1 - l);
+        return (GS && l < lg) ? ws.gstack + 4 * (qtop - ql) : ws.stack + 4 * (qsplit - ql);
+    };
+    // the leaf and its parent are always in shared memory (gs_level >= 14)
+    auto level_smem = [&](int l) -> cx<R> * { return ws.stack + 4 * (qsplit - sq_sum(R0 + 1 - l)); };
+    build_level0<R>(ws, u, n, d, dv, tab, col, inv_h, s0, L, level(0), pivot_slots<R>() && levels >= 1, lane);
     if (lane == 0) ws.detD[0] = dv;
     __syncwarp();
     // 3. depth-first tree over a_2 .. a_{levels+1}
@@ -1105,6 +1157,68 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
         }
     }
     return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+}
+
+// Keldysh sums of two points at once (two_point_order(n)): the points whose
+// times are in ua and ub get level 0 side by side at the bottom of the stack,
+// and their trees run as one tree with a top bit h = the point.  Half-warp h
+// resolves point h: at order kTreeLeaf + 1 (FP32, flat kTreeLeaf) its leaf
+// with the paired flat phase; at lower orders the breadth-first levels build
+// both points' nodes together (2, 4, ... parents) and lane 16 h + (node, path)
+// takes one path (at most 16 per point).  Each point's sum is the total of its
+// half-warp; both are returned to every lane, as keldysh_sum's.
+template <class R, int RFMAX>
+__device__ void keldysh_sum2(const WarpSmem<R> &ws, const double *ua, const double *ub, int n, cx<R> d, cx<R> dv,
+                             const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h, double s0,
+                             int L, int RF, int lane, cx<double> &sa, cx<double> &sb) {
+    const int S0 = 2 * n;
+    build_level0<R>(ws, ua, n, d, dv, tab, col, inv_h, s0, L, ws.stack, false, lane);
+    __syncwarp();  // P, Rr and lr are rebuilt for the second point
+    build_level0<R>(ws, ub, n, d, dv, tab, col, inv_h, s0, L, ws.stack + S0 * S0, false, lane);
+    if (lane < 2) ws.detD[lane] = dv;
+    __syncwarp();
+    const int Rleaf = n - 1;
+    Acc<R> ar, ai;
+    ar.init();
+    ai.init();
+    bool paired = false;
+    if constexpr (twin_leaves<R>() && RFMAX >= kTreeLeaf) {
+        if (Rleaf == kTreeLeaf) {
+            const int h = lane >> 4;
+            flat_pair<R, kTreeLeaf>(ws.stack + h * S0 * S0, dv, 0, lane & 15, ar, ai);
+            paired = true;
+        }
+    }
+    if (!paired) {
+        const int B = Rleaf > RF ? Rleaf - RF : 0;
+        const int Rf = Rleaf - B;
+        const cx<R> *E = ws.stack;
+        int S = S0;
+        const cx<R> *ndet = ws.detD;
+        cx<R> *dbuf = ws.bdet;
+        size_t bo = 0;
+        for (int lb = 0; lb < B; ++lb) {
+            const int nparent = 2 << lb;
+            cx<R> *out = ws.bfs + bo;
+            expand_level<R>(E, S, 2 * nparent, 0, out, ndet, dbuf, ws.wrow, ws.bip, lane);
+            bo += (size_t)(2 * nparent) * (S - 2) * (S - 2);
+            E = out;
+            S -= 2;
+            ndet = dbuf;
+            dbuf = (dbuf == ws.bdet) ? ws.bdet + 32 : ws.bdet;
+        }
+        const int hl = lane & 15;  // half-warp h = lane >> 4 takes point h
+        if (hl < (1 << Rleaf)) {
+            const int nb = hl >> Rf;                  // the node's breadth-first choices
+            const int node = ((lane >> 4) << B) | nb;  // its index in the last level
+            flat_dispatch<R, RFMAX>(Rf, E + (size_t)node * S * S, ndet[node], __popc(nb) & 1, hl & ((1 << Rf) - 1),
+                                    ar, ai);
+        }
+    }
+    __syncwarp();
+    const double tr = half_total<R>(ar), ti = half_total<R>(ai);
+    sa = mk<double>(__shfl_sync(FULL, tr, 0), __shfl_sync(FULL, ti, 0));
+    sb = mk<double>(__shfl_sync(FULL, tr, 16), __shfl_sync(FULL, ti, 16));
 }
 
 }  // namespace single
@@ -2171,6 +2285,24 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
         const typename TabT<R>::V *tab = item_table<R>(I);
         const double s0 = I.T * inv_h;
         unsigned mm = mask;
+        if constexpr (std::is_same<Tree, SingleTree>::value) {
+            if (I.split == 0 && single::two_point_order<R, RFMAX>(n)) {
+                while (__popc(mm) >= 2) {  // two points per pass (keldysh_sum2), a lone last one below
+                    const int a = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const int b = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    cx<double> sa, sb;
+                    single::keldysh_sum2<R, RFMAX>(ws, ws.upt + a * NU, ws.upt + b * NU, n, d, dv, tab,
+                                                   item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sa, sb);
+                    if (lane == a || lane == b) {
+                        cx<double> cval = times_i_pow(lane == a ? sa : sb, n);
+                        myval = mk<double>(w * cval.re, w * cval.im);
+                    }
+                    __syncwarp();
+                }
+            }
+        }
         while (mm) {
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
