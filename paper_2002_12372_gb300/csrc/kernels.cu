@@ -129,6 +129,17 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
     e = (a - (s - z)) + (b - z);
 }
 
+// (s, c) += w z: the product's rounding error by FMA (error-free product), the
+// sum by two-sum, both errors into c.
+__device__ __forceinline__ void add_weighted(double w, double z, double &s, double &c) {
+    const double p = w * z;
+    const double e = fma(w, z, -p);
+    double t, f;
+    two_sum(s, p, t, f);
+    s = t;
+    c += f + e;
+}
+
 // Deterministic butterfly reduction of (s, c) pairs over the warp.
 __device__ __forceinline__ void warp_reduce_pair(double &s, double &c) {
 #pragma unroll
@@ -371,6 +382,13 @@ __device__ __forceinline__ double half_total(Acc<R> acc) {
         c = lo ? (c + c2) + e : (c2 + c) + e;
     }
     return (double)s + (double)c;
+}
+
+// A lane's own share of the Keldysh sum (the warp total is the sum of the
+// lanes' shares), for callers that weight and accumulate shares per lane.
+template <class R>
+__device__ __forceinline__ cx<double> lane_share(Acc<R> ar, Acc<R> ai) {
+    return mk<double>((double)ar.s + (double)ar.c, (double)ai.s + (double)ai.c);
 }
 
 // ----------------------------------------------------------------------------
@@ -1059,7 +1077,8 @@ __device__ __forceinline__ void build_level0(const WarpSmem<R> &ws, const double
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
 // The depth-first walk covers the subtree `sub` of 2^split: the first `split`
 // tree levels follow the bits of sub (split <= levels); split = 0: whole tree.
-template <class R, int RFMAX, bool GS>
+// SHARE: every lane returns its own share instead (their sum is the total).
+template <class R, int RFMAX, bool GS, bool SHARE = false>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                   double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
@@ -1156,7 +1175,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
             __syncwarp();
         }
     }
-    return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+    return SHARE ? lane_share<R>(ar, ai) : mk<double>(warp_total<R>(ar), warp_total<R>(ai));
 }
 
 // Keldysh sums of two points at once (two_point_order(n)): the points whose
@@ -1166,8 +1185,9 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
 // with the paired flat phase; at lower orders the breadth-first levels build
 // both points' nodes together (2, 4, ... parents) and lane 16 h + (node, path)
 // takes one path (at most 16 per point).  Each point's sum is the total of its
-// half-warp; both are returned to every lane, as keldysh_sum's.
-template <class R, int RFMAX>
+// half-warp; both are returned to every lane, as keldysh_sum's (SHARE: each
+// lane's own share of its half's point, in sa).
+template <class R, int RFMAX, bool SHARE = false>
 __device__ void keldysh_sum2(const WarpSmem<R> &ws, const double *ua, const double *ub, int n, cx<R> d, cx<R> dv,
                              const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h, double s0,
                              int L, int RF, int lane, cx<double> &sa, cx<double> &sb) {
@@ -1216,6 +1236,11 @@ __device__ void keldysh_sum2(const WarpSmem<R> &ws, const double *ua, const doub
         }
     }
     __syncwarp();
+    if constexpr (SHARE) {  // the lane's share of its half-warp's point, in sa
+        sa = lane_share<R>(ar, ai);
+        sb = mk<double>(0.0, 0.0);
+        return;
+    }
     const double tr = half_total<R>(ar), ti = half_total<R>(ai);
     sa = mk<double>(__shfl_sync(FULL, tr, 0), __shfl_sync(FULL, ti, 0));
     sb = mk<double>(__shfl_sync(FULL, tr, 16), __shfl_sync(FULL, ti, 16));
@@ -1863,7 +1888,7 @@ __device__ __forceinline__ void leaf_group(const WarpSmem<R> &ws, const cx<R> *E
 // The depth-first walk covers the subtree `sub` of 2^split: the first `split`
 // bits of the leaf index (a_2, then two per level) follow sub; split = 0: the
 // whole tree.
-template <class R, int RFMAX, bool GS>
+template <class R, int RFMAX, bool GS, bool SHARE = false>
 __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                   double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
@@ -1955,7 +1980,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
                                  ts.g ? 0 : __popc(b) & 1, ar, ai, lane);
         }
     }
-    return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+    return SHARE ? lane_share<R>(ar, ai) : mk<double>(warp_total<R>(ar), warp_total<R>(ai));
 }
 
 
@@ -1977,11 +2002,11 @@ struct SingleTree {
     __device__ static Smem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack) {
         return single::carve<R>(base, n_max, RF, gstack);
     }
-    template <class R, int RFMAX, bool GS>
+    template <class R, int RFMAX, bool GS, bool SHARE = false>
     __device__ static cx<double> sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                      const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                      double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
-        return single::keldysh_sum<R, RFMAX, GS>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
+        return single::keldysh_sum<R, RFMAX, GS, SHARE>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
                                                  split);
     }
     // depth-first levels above the tree leaf (5 vertices), one bit of the leaf index each
@@ -2003,11 +2028,11 @@ struct PairTree {
     __device__ static Smem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack) {
         return pairs::carve<R>(base, n_max, RF, gstack);
     }
-    template <class R, int RFMAX, bool GS>
+    template <class R, int RFMAX, bool GS, bool SHARE = false>
     __device__ static cx<double> sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                      const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                      double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
-        return pairs::keldysh_sum<R, RFMAX, GS>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
+        return pairs::keldysh_sum<R, RFMAX, GS, SHARE>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
                                                 split);
     }
     static int leaf_bits(int n) { return pairs::tree_shape(n).lbits; }
@@ -2279,7 +2304,12 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
         }
         unsigned mask = __ballot_sync(FULL, inside);
         __syncwarp();
+        // FP64: each lane adds w_i times its own share of every point's Keldysh sum (error-free
+        // product, two-sum) and the warp reduces once per unit, instead of a two-sum butterfly per
+        // point.  Mixed: the point's FP32 total is formed by the warp, then weighted in FP64.
+        constexpr bool kShare = sizeof(R) == 8;
         cx<double> myval = mk<double>(0.0, 0.0);
+        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
         const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
         const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
         const typename TabT<R>::V *tab = item_table<R>(I);
@@ -2293,9 +2323,14 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
                     const int b = __ffs(mm) - 1;
                     mm &= mm - 1;
                     cx<double> sa, sb;
-                    single::keldysh_sum2<R, RFMAX>(ws, ws.upt + a * NU, ws.upt + b * NU, n, d, dv, tab,
-                                                   item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sa, sb);
-                    if (lane == a || lane == b) {
+                    single::keldysh_sum2<R, RFMAX, kShare>(ws, ws.upt + a * NU, ws.upt + b * NU, n, d, dv, tab,
+                                                           item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sa, sb);
+                    if constexpr (kShare) {
+                        const double wp = __shfl_sync(FULL, w, (lane >> 4) ? b : a);
+                        const cx<double> sh = times_i_pow(sa, n);
+                        add_weighted(wp, sh.re, sr, cr);
+                        add_weighted(wp, sh.im, si, ci);
+                    } else if (lane == a || lane == b) {
                         cx<double> cval = times_i_pow(lane == a ? sa : sb, n);
                         myval = mk<double>(w * cval.re, w * cval.im);
                     }
@@ -2307,16 +2342,24 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
             // every warp-per-point item of a launch shares the launch's flat depth
-            cx<double> s = Tree::template sum<R, RFMAX, GS>(ws, ws.upt + src * NU, n, n_max, d, dv, tab,
-                                                            item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sub,
-                                                            I.split);
-            if (lane == src) {
+            cx<double> s = Tree::template sum<R, RFMAX, GS, kShare>(ws, ws.upt + src * NU, n, n_max, d, dv, tab,
+                                                                    item_col<R>(I), inv_h, s0, I.L, RFMAX, lane,
+                                                                    sub, I.split);
+            if constexpr (kShare) {
+                const double wp = __shfl_sync(FULL, w, src);
+                const cx<double> sh = times_i_pow(s, n);
+                add_weighted(wp, sh.re, sr, cr);
+                add_weighted(wp, sh.im, si, ci);
+            } else if (lane == src) {
                 cx<double> cval = times_i_pow(s, n);
                 myval = mk<double>(w * cval.re, w * cval.im);
             }
             __syncwarp();
         }
-        double sr = myval.re, cr = 0.0, si = myval.im, ci = 0.0;
+        if constexpr (!kShare) {
+            sr = myval.re;
+            si = myval.im;
+        }
         warp_reduce_pair(sr, cr);
         warp_reduce_pair(si, ci);
         if (lane == 0) {

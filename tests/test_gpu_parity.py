@@ -264,6 +264,41 @@ def test_mixed_every_flat_depth_within_bound_of_fp64(Q, W, oracle, flat):
         autotune.reset()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_points_per_warp_match_oracle(Q, W, oracle, precision):
+    """Orders whose single-vertex tree fills at most half a warp per point (n <= 5, and n = 6 in mixed
+    precision at flat 5) run two points per warp, one per half-warp, with both points' breadth-first
+    levels built together; an odd in-domain count leaves a lone last point on the one-point path.
+    Every order 1..6 at every flat depth, with 16384 and 8191 points x 4 shifts (work units of 4 and
+    2 points: the plan cuts small items into point groups, so a unit holds pairs, odd counts and lone
+    points): FP64 within 1e-10 of the oracle per shift; mixed within 1e-4 of the FP64 path's shift
+    scale."""
+    from paper_2002_12372_gb300 import autotune
+    T, K = 10.0, 4
+    pr, tabs = _problem(Q, W, seed=77, T=T, elim=2)
+    try:
+        for n in range(1, 7):
+            sw = W.shift_words(8000 + n, K, n)
+            for N in (16384, 8191):
+                ref = oracle.estimate(n, N, sw, T, 1.0, tabs, T) if precision == Q.QQMC_PREC_FP64 else None
+                for flat in (2, 3, 4, 5):
+                    Q.qqmc_set_tuning(precision, n, 2, flat)
+                    res, S = Q.qqmc_integrate(pr, n, N, K, precision, sw)
+                    if precision == Q.QQMC_PREC_FP64:
+                        S0, nin = ref
+                        assert res.n_in_domain == int(nin.sum())
+                        rel = np.abs(S - S0) / np.maximum(np.abs(S0), 1e-300)
+                        assert np.all(rel < 1e-10), (n, flat, N, rel)
+                    else:
+                        Q.qqmc_set_tuning(Q.QQMC_PREC_FP64, n, 2, 2)
+                        r64, S64 = Q.qqmc_integrate(pr, n, N, K, Q.QQMC_PREC_FP64, sw)
+                        assert res.n_in_domain == r64.n_in_domain
+                        assert np.all(np.abs(S - S64) <= 1e-4 * np.max(np.abs(S64))), (n, flat, N)
+    finally:
+        Q.qqmc_destroy_problem(pr)
+        autotune.reset()
+
+
 @pytest.mark.slow
 def test_full_size_bench_launch_sampled_chunks(Q, W, oracle):
     """The benchmark's launch shape at full size (three problems, n = 1..10, N = 2^20 x 32 shifts,
