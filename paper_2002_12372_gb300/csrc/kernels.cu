@@ -341,8 +341,6 @@ __device__ __forceinline__ cx<R> leaf_term(cx<R> m00, cx<R> m11, cx<R> m0p, cx<R
     return cmul(cmul(det, det), cmul(pv, cneg(r)));
 }
 
-// Float-float or double-double style butterfly of the lane accumulators:
-// combines (s, c) pairs with two-sum in R, then returns s + c in double.
 template <class R>
 __device__ __forceinline__ void two_sum_r(R a, R b, R &s, R &e) {
     s = a + b;
@@ -350,45 +348,70 @@ __device__ __forceinline__ void two_sum_r(R a, R b, R &s, R &e) {
     e = (a - (s - z)) + (b - z);
 }
 
+// Float-float or double-double style butterfly of the lane accumulators over
+// groups of W lanes (W = 32: the warp, 16: each half-warp): combines the
+// (s, c) pairs with two-sum in R; every lane gets its group's pair.
+template <class R, int W = 32>
+__device__ __forceinline__ Acc<R> group_pair(Acc<R> acc) {
+    R s = acc.s, c = acc.c;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+        R s2 = __shfl_xor_sync(FULL, s, o);
+        R c2 = __shfl_xor_sync(FULL, c, o);
+        R t, e;
+        int lo = ((threadIdx.x & 31) & o) == 0;
+        if (lo) two_sum_r<R>(s, s2, t, e); else two_sum_r<R>(s2, s, t, e);
+        s = t;
+        c = lo ? (c + c2) + e : (c2 + c) + e;
+    }
+    Acc<R> r;
+    r.s = s;
+    r.c = c;
+    return r;
+}
+
+// The pair's value s + c in double.
+template <class R>
+__device__ __forceinline__ double pair_value(Acc<R> a) {
+    return (double)a.s + (double)a.c;
+}
+
 template <class R>
 __device__ __forceinline__ double warp_total(Acc<R> acc) {
-    R s = acc.s, c = acc.c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        R s2 = __shfl_xor_sync(FULL, s, o);
-        R c2 = __shfl_xor_sync(FULL, c, o);
-        R t, e;
-        int lo = ((threadIdx.x & 31) & o) == 0;
-        if (lo) two_sum_r<R>(s, s2, t, e); else two_sum_r<R>(s2, s, t, e);
-        s = t;
-        c = lo ? (c + c2) + e : (c2 + c) + e;
-    }
-    return (double)s + (double)c;
+    return pair_value<R>(group_pair<R>(acc));
 }
 
-// The same butterfly within each half-warp: lanes 0-15 and 16-31 get their
-// own half's total.
-template <class R>
-__device__ __forceinline__ double half_total(Acc<R> acc) {
-    R s = acc.s, c = acc.c;
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-        R s2 = __shfl_xor_sync(FULL, s, o);
-        R c2 = __shfl_xor_sync(FULL, c, o);
-        R t, e;
-        int lo = ((threadIdx.x & 31) & o) == 0;
-        if (lo) two_sum_r<R>(s, s2, t, e); else two_sum_r<R>(s2, s, t, e);
-        s = t;
-        c = lo ? (c + c2) + e : (c2 + c) + e;
-    }
-    return (double)s + (double)c;
-}
+// What a Keldysh-sum tree returns: the warp total in double (kOutTotal), the
+// lane's own share in double (kOutShare: the shares sum to the total, for
+// callers that weight and accumulate shares per lane), or the warp total as
+// the unevaluated pairs in R (kOutPair: for callers that convert it later).
+constexpr int kOutTotal = 0, kOutShare = 1, kOutPair = 2;
 
-// A lane's own share of the Keldysh sum (the warp total is the sum of the
-// lanes' shares), for callers that weight and accumulate shares per lane.
 template <class R>
-__device__ __forceinline__ cx<double> lane_share(Acc<R> ar, Acc<R> ai) {
-    return mk<double>((double)ar.s + (double)ar.c, (double)ai.s + (double)ai.c);
+struct PairSum {
+    Acc<R> re, im;
+};
+template <class R, int OUT>
+struct SumOut {
+    using type = cx<double>;
+};
+template <class R>
+struct SumOut<R, kOutPair> {
+    using type = PairSum<R>;
+};
+
+template <class R, int OUT>
+__device__ __forceinline__ typename SumOut<R, OUT>::type tree_result(Acc<R> ar, Acc<R> ai) {
+    if constexpr (OUT == kOutPair) {
+        PairSum<R> r;
+        r.re = group_pair<R>(ar);
+        r.im = group_pair<R>(ai);
+        return r;
+    } else if constexpr (OUT == kOutShare) {
+        return mk<double>(pair_value<R>(ar), pair_value<R>(ai));
+    } else {
+        return mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -1077,9 +1100,10 @@ __device__ __forceinline__ void build_level0(const WarpSmem<R> &ws, const double
 // i.e. sum_a (-1)^{|a|} det M_up det M_down (without the i^n factor).
 // The depth-first walk covers the subtree `sub` of 2^split: the first `split`
 // tree levels follow the bits of sub (split <= levels); split = 0: whole tree.
-// SHARE: every lane returns its own share instead (their sum is the total).
-template <class R, int RFMAX, bool GS, bool SHARE = false>
-__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+// OUT: the form of the result (kOutTotal, kOutShare, kOutPair).
+template <class R, int RFMAX, bool GS, int OUT = kOutTotal>
+__device__ typename SumOut<R, OUT>::type keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max,
+                                                     cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                   double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
     // 1. pair interpolation, 0 <= j < k <= n, and 2. level 0 (build_level0)
@@ -1175,7 +1199,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
             __syncwarp();
         }
     }
-    return SHARE ? lane_share<R>(ar, ai) : mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+    return tree_result<R, OUT>(ar, ai);
 }
 
 // Keldysh sums of two points at once (two_point_order(n)): the points whose
@@ -1185,12 +1209,13 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
 // with the paired flat phase; at lower orders the breadth-first levels build
 // both points' nodes together (2, 4, ... parents) and lane 16 h + (node, path)
 // takes one path (at most 16 per point).  Each point's sum is the total of its
-// half-warp; both are returned to every lane, as keldysh_sum's (SHARE: each
-// lane's own share of its half's point, in sa).
-template <class R, int RFMAX, bool SHARE = false>
+// half-warp; both are returned to every lane in the form OUT, as keldysh_sum's
+// (kOutShare: each lane's own share of its half's point, in sa).
+template <class R, int RFMAX, int OUT = kOutTotal>
 __device__ void keldysh_sum2(const WarpSmem<R> &ws, const double *ua, const double *ub, int n, cx<R> d, cx<R> dv,
                              const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h, double s0,
-                             int L, int RF, int lane, cx<double> &sa, cx<double> &sb) {
+                             int L, int RF, int lane, typename SumOut<R, OUT>::type &sa,
+                             typename SumOut<R, OUT>::type &sb) {
     const int S0 = 2 * n;
     build_level0<R>(ws, ua, n, d, dv, tab, col, inv_h, s0, L, ws.stack, false, lane);
     __syncwarp();  // P, Rr and lr are rebuilt for the second point
@@ -1236,14 +1261,28 @@ __device__ void keldysh_sum2(const WarpSmem<R> &ws, const double *ua, const doub
         }
     }
     __syncwarp();
-    if constexpr (SHARE) {  // the lane's share of its half-warp's point, in sa
-        sa = lane_share<R>(ar, ai);
+    if constexpr (OUT == kOutShare) {  // the lane's share of its half-warp's point, in sa
+        sa = tree_result<R, kOutShare>(ar, ai);
         sb = mk<double>(0.0, 0.0);
-        return;
+    } else {
+        const Acc<R> hr = group_pair<R, 16>(ar), hi = group_pair<R, 16>(ai);
+        auto from = [&](int src) {  // half-warp src / 16's pair, from its first lane
+            PairSum<R> p;
+            p.re.s = __shfl_sync(FULL, hr.s, src);
+            p.re.c = __shfl_sync(FULL, hr.c, src);
+            p.im.s = __shfl_sync(FULL, hi.s, src);
+            p.im.c = __shfl_sync(FULL, hi.c, src);
+            return p;
+        };
+        const PairSum<R> pa = from(0), pb = from(16);
+        if constexpr (OUT == kOutPair) {
+            sa = pa;
+            sb = pb;
+        } else {
+            sa = mk<double>(pair_value<R>(pa.re), pair_value<R>(pa.im));
+            sb = mk<double>(pair_value<R>(pb.re), pair_value<R>(pb.im));
+        }
     }
-    const double tr = half_total<R>(ar), ti = half_total<R>(ai);
-    sa = mk<double>(__shfl_sync(FULL, tr, 0), __shfl_sync(FULL, ti, 0));
-    sb = mk<double>(__shfl_sync(FULL, tr, 16), __shfl_sync(FULL, ti, 16));
 }
 
 }  // namespace single
@@ -1888,8 +1927,9 @@ __device__ __forceinline__ void leaf_group(const WarpSmem<R> &ws, const cx<R> *E
 // The depth-first walk covers the subtree `sub` of 2^split: the first `split`
 // bits of the leaf index (a_2, then two per level) follow sub; split = 0: the
 // whole tree.
-template <class R, int RFMAX, bool GS, bool SHARE = false>
-__device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+template <class R, int RFMAX, bool GS, int OUT = kOutTotal>
+__device__ typename SumOut<R, OUT>::type keldysh_sum(const WarpSmem<R> &ws, const double *u, int n, int n_max,
+                                                     cx<R> d, cx<R> dv,
                                   const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                   double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
     // 1. pair interpolation, 0 <= j < k <= n
@@ -1980,7 +2020,7 @@ __device__ cx<double> keldysh_sum(const WarpSmem<R> &ws, const double *u, int n,
                                  ts.g ? 0 : __popc(b) & 1, ar, ai, lane);
         }
     }
-    return SHARE ? lane_share<R>(ar, ai) : mk<double>(warp_total<R>(ar), warp_total<R>(ai));
+    return tree_result<R, OUT>(ar, ai);
 }
 
 
@@ -2002,11 +2042,11 @@ struct SingleTree {
     __device__ static Smem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack) {
         return single::carve<R>(base, n_max, RF, gstack);
     }
-    template <class R, int RFMAX, bool GS, bool SHARE = false>
-    __device__ static cx<double> sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+    template <class R, int RFMAX, bool GS, int OUT = kOutTotal>
+    __device__ static typename SumOut<R, OUT>::type sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                      const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                      double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
-        return single::keldysh_sum<R, RFMAX, GS, SHARE>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
+        return single::keldysh_sum<R, RFMAX, GS, OUT>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
                                                  split);
     }
     // depth-first levels above the tree leaf (5 vertices), one bit of the leaf index each
@@ -2028,11 +2068,11 @@ struct PairTree {
     __device__ static Smem<R> carve(unsigned char *base, int n_max, int RF, cx<R> *gstack) {
         return pairs::carve<R>(base, n_max, RF, gstack);
     }
-    template <class R, int RFMAX, bool GS, bool SHARE = false>
-    __device__ static cx<double> sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
+    template <class R, int RFMAX, bool GS, int OUT = kOutTotal>
+    __device__ static typename SumOut<R, OUT>::type sum(const Smem<R> &ws, const double *u, int n, int n_max, cx<R> d, cx<R> dv,
                                      const typename TabT<R>::V *tab, const typename TabT<R>::V *col, double inv_h,
                                      double s0, int L, int RF, int lane, int sub = 0, int split = 0) {
-        return pairs::keldysh_sum<R, RFMAX, GS, SHARE>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
+        return pairs::keldysh_sum<R, RFMAX, GS, OUT>(ws, u, n, n_max, d, dv, tab, col, inv_h, s0, L, RF, lane, sub,
                                                 split);
     }
     static int leaf_bits(int n) { return pairs::tree_shape(n).lbits; }
@@ -2306,9 +2346,14 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
         __syncwarp();
         // FP64: each lane adds w_i times its own share of every point's Keldysh sum (error-free
         // product, two-sum) and the warp reduces once per unit, instead of a two-sum butterfly per
-        // point.  Mixed: the point's FP32 total is formed by the warp, then weighted in FP64.
-        constexpr bool kShare = sizeof(R) == 8;
-        cx<double> myval = mk<double>(0.0, 0.0);
+        // point.  Mixed: the warp forms each point's total as FP32 pairs, the point's own lane keeps
+        // it, and every lane converts and weights its point in FP64 once per unit (FP64 costs 64
+        // FP32 instructions here, so none runs per point).
+        constexpr int kOut = sizeof(R) == 8 ? kOutShare : kOutPair;
+        using Out = typename SumOut<R, kOut>::type;
+        PairSum<R> own;  // mixed: this lane's point total
+        own.re.init();
+        own.im.init();
         double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
         const cx<R> d = mk<R>((R)I.g0_re, (R)I.g0_im);
         const cx<R> dv = mk<R>((R)I.g0_re, (R)(I.g0_im - I.alpha));
@@ -2322,17 +2367,17 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
                     mm &= mm - 1;
                     const int b = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    cx<double> sa, sb;
-                    single::keldysh_sum2<R, RFMAX, kShare>(ws, ws.upt + a * NU, ws.upt + b * NU, n, d, dv, tab,
-                                                           item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sa, sb);
-                    if constexpr (kShare) {
+                    Out sa, sb;
+                    single::keldysh_sum2<R, RFMAX, kOut>(ws, ws.upt + a * NU, ws.upt + b * NU, n, d, dv, tab,
+                                                         item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sa, sb);
+                    if constexpr (kOut == kOutShare) {
                         const double wp = __shfl_sync(FULL, w, (lane >> 4) ? b : a);
                         const cx<double> sh = times_i_pow(sa, n);
                         add_weighted(wp, sh.re, sr, cr);
                         add_weighted(wp, sh.im, si, ci);
-                    } else if (lane == a || lane == b) {
-                        cx<double> cval = times_i_pow(lane == a ? sa : sb, n);
-                        myval = mk<double>(w * cval.re, w * cval.im);
+                    } else {
+                        if (lane == a) own = sa;
+                        if (lane == b) own = sb;
                     }
                     __syncwarp();
                 }
@@ -2342,23 +2387,25 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
             // every warp-per-point item of a launch shares the launch's flat depth
-            cx<double> s = Tree::template sum<R, RFMAX, GS, kShare>(ws, ws.upt + src * NU, n, n_max, d, dv, tab,
-                                                                    item_col<R>(I), inv_h, s0, I.L, RFMAX, lane,
-                                                                    sub, I.split);
-            if constexpr (kShare) {
+            const Out s = Tree::template sum<R, RFMAX, GS, kOut>(ws, ws.upt + src * NU, n, n_max, d, dv, tab,
+                                                                 item_col<R>(I), inv_h, s0, I.L, RFMAX, lane, sub,
+                                                                 I.split);
+            if constexpr (kOut == kOutShare) {
                 const double wp = __shfl_sync(FULL, w, src);
                 const cx<double> sh = times_i_pow(s, n);
                 add_weighted(wp, sh.re, sr, cr);
                 add_weighted(wp, sh.im, si, ci);
             } else if (lane == src) {
-                cx<double> cval = times_i_pow(s, n);
-                myval = mk<double>(w * cval.re, w * cval.im);
+                own = s;
             }
             __syncwarp();
         }
-        if constexpr (!kShare) {
-            sr = myval.re;
-            si = myval.im;
+        if constexpr (kOut == kOutPair) {
+            if ((mask >> lane) & 1u) {  // the lane's point was in the domain
+                const cx<double> cval = times_i_pow(mk<double>(pair_value<R>(own.re), pair_value<R>(own.im)), n);
+                sr = w * cval.re;
+                si = w * cval.im;
+            }
         }
         warp_reduce_pair(sr, cr);
         warp_reduce_pair(si, ci);
