@@ -414,6 +414,34 @@ __device__ __forceinline__ typename SumOut<R, OUT>::type tree_result(Acc<R> ar, 
     }
 }
 
+// Mixed path: a work unit's sum of the lanes' FP64 values (re, im) as an FP64
+// (sum, compensation) pair per part, with the butterfly on the FP32 pipe.  The
+// values are scaled by one power of two (the largest magnitude in the warp then
+// lies in [2^63, 2^64), so 32 of them stay far from the FP32 limit and the
+// smallest that matter far above its underflow), split into float-float pairs
+// (about 48 bits), combined with group_pair and scaled back.  FP64 instructions
+// cost 64 FP32 instructions' issue here: this takes 18 of them per unit where
+// the FP64 butterfly takes 80.  A NaN or infinity stays one.
+__device__ __forceinline__ void unit_pairs_ff(double re, double im, double &sr, double &cr, double &si, double &ci) {
+    const int er = (__double2hiint(re) >> 20) & 0x7ff, ei = (__double2hiint(im) >> 20) & 0x7ff;
+    const int e = (int)__reduce_max_sync(FULL, (unsigned)(er > ei ? er : ei));
+    int k = e == 0x7ff ? 0 : 1023 + 63 - e;  // scale by 2^k, |k| <= 1022
+    k = k > 1022 ? 1022 : k;
+    const double up = __hiloint2double((k + 1023) << 20, 0), down = __hiloint2double((1023 - k) << 20, 0);
+    auto split = [&](double x) {
+        const double xs = x * up;
+        Acc<float> a;
+        a.s = (float)xs;
+        a.c = (float)(xs - (double)a.s);
+        return group_pair<float>(a);
+    };
+    const Acc<float> pr = split(re), pi = split(im);
+    sr = (double)pr.s * down;
+    cr = (double)pr.c * down;
+    si = (double)pi.s * down;
+    ci = (double)pi.c * down;
+}
+
 // ----------------------------------------------------------------------------
 // Single-vertex Schur tree (the fast path): one vertex per tree level with
 // its 1x1 pivot.  Pivots are the ratios of consecutive leading minors of
@@ -2406,9 +2434,11 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
                 sr = w * cval.re;
                 si = w * cval.im;
             }
+            unit_pairs_ff(sr, si, sr, cr, si, ci);
+        } else {
+            warp_reduce_pair(sr, cr);
+            warp_reduce_pair(si, ci);
         }
-        warp_reduce_pair(sr, cr);
-        warp_reduce_pair(si, ci);
         if (lane == 0) {
             double *pp = I.partials + 4 * (size_t)local;
             pp[0] = sr;
@@ -2514,8 +2544,12 @@ __global__ void __launch_bounds__(128) lane_kernel(const ItemDev *__restrict__ i
         }
         const unsigned mask = __ballot_sync(FULL, inside);
         double sr = v.re, cr = 0.0, si = v.im, ci = 0.0;
-        warp_reduce_pair(sr, cr);
-        warp_reduce_pair(si, ci);
+        if constexpr (sizeof(R) == 4) {
+            unit_pairs_ff(v.re, v.im, sr, cr, si, ci);
+        } else {
+            warp_reduce_pair(sr, cr);
+            warp_reduce_pair(si, ci);
+        }
         if (lane == 0) {
             double *pp = I.partials + 4 * (size_t)local;
             pp[0] = sr;
