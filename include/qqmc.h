@@ -73,8 +73,10 @@ extern "C" {
 
 /* Arithmetic of the determinant stage. */
 #define QQMC_PREC_FP64 0  /* tables, Schur updates and sums in FP64 */
-#define QQMC_PREC_MIXED 1 /* tables and Schur updates in FP32, leaf sums two-sum
-                             compensated, point and shift sums in FP64 */
+#define QQMC_PREC_MIXED 1 /* tables and Schur updates in FP32; leaf sums and a
+                             work unit's 32 weighted point values as two-sum
+                             float-float pairs (48 bits); weights, sums over
+                             units and shift sums in FP64 two-sum */
 
 /* Elimination order of the Keldysh sum (qqmc_set_elimination).  Every vertex
  * diagonal of M_down is g^<(0) - i alpha (App. E), which is zero at the
