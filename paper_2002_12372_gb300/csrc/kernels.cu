@@ -2375,8 +2375,9 @@ __device__ __forceinline__ void detsum_body(const ItemDev *__restrict__ items, i
         // FP64: each lane adds w_i times its own share of every point's Keldysh sum (error-free
         // product, two-sum) and the warp reduces once per unit, instead of a two-sum butterfly per
         // point.  Mixed: the warp forms each point's total as FP32 pairs, the point's own lane keeps
-        // it, and every lane converts and weights its point in FP64 once per unit (FP64 costs 64
-        // FP32 instructions here, so none runs per point).
+        // it, every lane converts and weights its point in FP64 once per unit, and the unit's values
+        // are summed as float-float pairs (unit_pairs_ff): an FP64 instruction costs 64 FP32
+        // instructions' issue here, so none runs per point.
         constexpr int kOut = sizeof(R) == 8 ? kOutShare : kOutPair;
         using Out = typename SumOut<R, kOut>::type;
         PairSum<R> own;  // mixed: this lane's point total
