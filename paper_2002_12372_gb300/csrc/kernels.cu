@@ -107,8 +107,9 @@ __device__ __forceinline__ cx<R> nconj(cx<R> a) {  // -conj(a)
 // Lane accumulator of the Keldysh leaf terms, value = s + c.  FP32 leaves:
 // Knuth two-sum (float-float), since the alternating-sign sum cancels by up to
 // 1e5.  FP64 leaves: plain sum; a lane adds at most 2^(n-1)/32 terms, so its
-// rounding stays below 1e-14 of the Keldysh-sum scale, and the lanes are
-// combined with two-sum in warp_total.
+// rounding stays below 1e-14 of the Keldysh-sum scale, and the lanes' shares
+// are combined with two-sum (per point in warp_total, or weighted and summed
+// over a work unit's points with add_weighted in the integration kernel).
 template <class R>
 struct Acc {
     R s, c;
